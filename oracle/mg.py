@@ -1,0 +1,182 @@
+"""Multigrid, Chebyshev and PRESB ingredients written from their definitions (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sources in arXiv 2209.06700:
+* Sec. 5 (solver setup): each block (lambda_i M + tau K) of Eq. (irk:P) is
+  approximated by one geometric-multigrid V-cycle; the smoother is a
+  Chebyshev iteration around point-Jacobi; the paper's coarse solver (AMG)
+  is replaced here by an exact dense solve.
+* Sec. 6, Eq. (presb:p): the PRESB preconditioner of the 2x2 real block
+  [[K', -M'], [M', K']] and its three-factor form.
+
+Readings (the paper defers the multigrid details to its reference on
+global-coarsening GMG):
+* levels are the uniform meshes N, N/2, ... down to the first odd N or the
+  smallest N with an interior node; the same degree k on every level; level
+  operators are rediscretised (lambda M_l + tau K_l);
+* prolongation is the Q_k embedding (coarse function evaluated at the fine
+  nodes); restriction is its transpose;
+* the Chebyshev iteration of degree m takes m steps of the three-term
+  recurrence x_{j+1} = x_j + d_j,
+      d_0 = r_0 / theta,  d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / delta) r_j,
+      r_j = D^{-1}(b - A x_j),  rho_0 = delta/theta,  rho_j = 1/(2 theta/delta - rho_{j-1}),
+  over the eigenvalue interval [lo, hi] of D^{-1} A, theta = (hi+lo)/2,
+  delta = (hi-lo)/2 (Saad's Chebyshev acceleration);
+* one V(m, m)-cycle: pre-smooth from zero, residual, restrict, recurse,
+  prolongate and add, post-smooth.
+
+Pinned by tests/test_oracle_mg.py: the Chebyshev error-propagation
+polynomial equals T_m((theta - mu)/delta) / T_m(theta/delta) on every
+eigenpair of D^{-1}A; the prolongation reproduces degree-k polynomials
+exactly; <P^T r, v> = <r, P v>; the V-cycle is symmetric and its two-grid
+error contraction is below one; the PRESB factors multiply to P and the
+PRESB-preconditioned spectrum lies in [1/2, 1].
+The chosen Chebyshev interval and level count are heuristics (parity
+unpinned beyond the algebraic checks above); only the converged step
+result is pinned as a whole.
+"""
+import numpy as np
+import scipy.linalg as sla
+
+from .fem import Mesh, assemble, gll_nodes, interior_restrict, lagrange_values
+
+
+def level_sizes(N, k):
+    """Cells per direction on each level, fine to coarse."""
+    nmin = 2 if k == 1 else 1
+    sizes = [N]
+    while sizes[-1] % 2 == 0 and sizes[-1] // 2 >= nmin:
+        sizes.append(sizes[-1] // 2)
+    return sizes
+
+
+def prolongation(d, Nc, k):
+    """Dense P (n_fine x n_coarse): coarse Q_k basis functions evaluated at fine nodes.
+
+    Columns of coarse boundary nodes are zeroed (homogeneous Dirichlet).
+    """
+    mc, mf = Mesh(d, Nc, k), Mesh(d, 2 * Nc, k)
+    xf = mf.node_coords()
+    xi = gll_nodes(k)
+    P = np.zeros((mf.n, mc.n))
+    for f in range(mf.n):
+        vals = [np.ones(1)]
+        gidx = [np.zeros(1, dtype=np.int64)]
+        for a in range(d):
+            s = xf[f, a] * Nc
+            c = min(int(np.floor(s)), Nc - 1)
+            V, _ = lagrange_values(xi, np.array([s - c]))
+            ga = (k * c + np.arange(k + 1)) * (mc.n1 ** a)
+            vals = [np.outer(v, V[0]).reshape(-1) for v in vals]
+            gidx = [(gi[:, None] + ga[None, :]).reshape(-1) for gi in gidx]
+        P[f, gidx[0]] += vals[0]
+    P[:, mc.boundary_mask()] = 0.0
+    P[mf.boundary_mask(), :] = 0.0
+    return P
+
+
+def level_operator(d, N, k, lam, tau):
+    """Assembled lambda M + tau K on interior DoFs embedded in full-length (dense for small N)."""
+    mesh = Mesh(d, N, k)
+    M, K = assemble(mesh)
+    A = (lam * M + tau * K).toarray()
+    b = mesh.boundary_mask()
+    A[b, :] = 0.0
+    A[:, b] = 0.0
+    return A, b
+
+
+def jacobi_diag(A, bmask):
+    D = np.diag(A).copy()
+    D[bmask] = 1.0
+    return D
+
+
+def chebyshev(A, D, b, x0, m, lo, hi, bmask):
+    """Degree-m Chebyshev iteration around point-Jacobi (recurrence in the module header)."""
+    theta = 0.5 * (hi + lo)
+    delta = 0.5 * (hi - lo)
+    x = x0.copy()
+    r = (b - A @ x) / D
+    r[bmask] = 0.0
+    d = r / theta
+    rho = delta / theta
+    x = x + d
+    for _ in range(1, m):
+        rho_new = 1.0 / (2.0 * theta / delta - rho)
+        r = (b - A @ x) / D
+        r[bmask] = 0.0
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * r
+        x = x + d
+        rho = rho_new
+    return x
+
+
+def max_eig_DinvA(A, D, bmask):
+    """Largest eigenvalue of D^{-1} A on interior DoFs (dense symmetric form D^{-1/2} A D^{-1/2})."""
+    keep = ~bmask
+    Ai = A[np.ix_(keep, keep)]
+    s = 1.0 / np.sqrt(D[keep])
+    return float(sla.eigvalsh(s[:, None] * Ai * s[None, :])[-1])
+
+
+class VCycle:
+    """One V(m, m)-cycle for lambda M + tau K on the uniform hierarchy (FP64, dense, small N)."""
+
+    def __init__(self, d, N, k, lam, tau, m, bounds=None, smoothing_range=20.0, safety=1.2):
+        self.sizes = level_sizes(N, k)
+        self.levels = []
+        for li, Nl in enumerate(self.sizes):
+            A, bm = level_operator(d, Nl, k, lam, tau)
+            D = jacobi_diag(A, bm)
+            if bounds is not None:
+                lo, hi = bounds[li]
+            else:
+                hi = safety * max_eig_DinvA(A, D, bm)
+                lo = hi / smoothing_range
+            self.levels.append(dict(N=Nl, A=A, D=D, bm=bm, lo=lo, hi=hi))
+        self.P = [prolongation(d, self.sizes[i + 1], k) for i in range(len(self.sizes) - 1)]
+        c = self.levels[-1]
+        keep = ~c["bm"]
+        self.coarse_keep = keep
+        self.coarse_inv = np.linalg.inv(c["A"][np.ix_(keep, keep)])
+        self.m = m
+
+    def coarse_solve(self, b):
+        x = np.zeros_like(b)
+        x[self.coarse_keep] = self.coarse_inv @ b[self.coarse_keep]
+        return x
+
+    def apply(self, b, level=0):
+        if level == len(self.levels) - 1:
+            return self.coarse_solve(b)
+        L = self.levels[level]
+        x = chebyshev(L["A"], L["D"], b, np.zeros_like(b), self.m, L["lo"], L["hi"], L["bm"])
+        r = b - L["A"] @ x
+        r[L["bm"]] = 0.0
+        bc = self.P[level].T @ r
+        ec = self.apply(bc, level + 1)
+        x = x + self.P[level] @ ec
+        x = chebyshev(L["A"], L["D"], b, x, self.m, L["lo"], L["hi"], L["bm"])
+        return x
+
+
+def presb_factors(Kp, Mp):
+    """The three factors of Eq. (presb:p) and P itself (dense)."""
+    n = Kp.shape[0]
+    I = np.eye(n)
+    Z0 = np.zeros((n, n))
+    X = np.block([[I, -I], [Z0, I]])
+    Y = np.block([[Kp + Mp, Z0], [Mp, Kp + Mp]])
+    Z = np.block([[I, I], [Z0, I]])
+    P = np.block([[Kp, -Mp], [Mp, Kp + 2 * Mp]])
+    return X, Y, Z, P
+
+
+def presb_apply(Hsolve, Mp_apply, f, g):
+    """P^{-1} (f, g) by the factored form: two sequential solves with H = K' + M'."""
+    a = f + g
+    w1 = Hsolve(a)
+    w2 = Hsolve(g - Mp_apply(w1))
+    return w1 - w2, w2

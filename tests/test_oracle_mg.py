@@ -1,0 +1,110 @@
+"""Oracle pins for the multigrid, Chebyshev and PRESB ingredients (CPU only).
+
+Pins: the Chebyshev error-propagation polynomial in closed form; exact
+reproduction of Q_k polynomials by the prolongation; V-cycle symmetry and
+contraction; the PRESB factorisation of Eq. (presb:p) and its spectral
+bound [1/2, 1].
+"""
+import numpy as np
+import pytest
+
+from oracle.fem import Mesh
+from oracle.mg import (VCycle, chebyshev, jacobi_diag, level_operator, level_sizes, presb_apply,
+                       presb_factors, prolongation)
+
+
+def test_level_sizes():
+    assert level_sizes(32, 4) == [32, 16, 8, 4, 2, 1]
+    assert level_sizes(48, 2) == [48, 24, 12, 6, 3]
+    assert level_sizes(16, 1) == [16, 8, 4, 2]
+    assert level_sizes(64, 3) == [64, 32, 16, 8, 4, 2, 1]
+
+
+def test_chebyshev_error_polynomial():
+    """e_m = T_m((theta - mu)/delta) / T_m(theta/delta) e_0 on every eigenpair of D^{-1}A."""
+    A, bm = level_operator(2, 3, 2, 2.0, 0.05)
+    D = jacobi_diag(A, bm)
+    keep = ~bm
+    s = 1.0 / np.sqrt(D[keep])
+    mu, W = np.linalg.eigh(s[:, None] * A[np.ix_(keep, keep)] * s[None, :])
+    lo, hi = 0.3 * mu.max(), 1.1 * mu.max()
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    x_true = np.zeros(A.shape[0])
+    for m in (1, 2, 3, 5):
+        for idx in (0, len(mu) // 2, len(mu) - 1):
+            # eigenvector of D^{-1}A: v = D^{-1/2} w
+            v = np.zeros(A.shape[0])
+            v[keep] = s * W[:, idx]
+            x0 = v.copy()                      # error e_0 = x0 - x_true = v (b = 0)
+            x = chebyshev(A, D, A @ x_true, x0, m, lo, hi, bm)
+            T = np.polynomial.chebyshev.Chebyshev.basis(m)
+            factor = T((theta - mu[idx]) / delta) / T(theta / delta)
+            np.testing.assert_allclose(x, factor * v, atol=1e-12 * np.abs(v).max())
+
+
+@pytest.mark.parametrize("d,Nc,k", [(2, 2, 1), (2, 2, 3), (3, 1, 2), (3, 2, 2), (2, 3, 4)])
+def test_prolongation_reproduces_polynomials(d, Nc, k):
+    P = prolongation(d, Nc, k)
+    mc, mf = Mesh(d, Nc, k), Mesh(d, 2 * Nc, k)
+    xc, xf = mc.node_coords(), mf.node_coords()
+    # a Q_k polynomial that vanishes on the boundary (Dirichlet) of degree k per direction
+    def f(x):
+        out = np.ones(len(x))
+        for a in range(d):
+            out *= x[:, a] * (1 - x[:, a]) * (x[:, a] + 0.3) ** (k - 2) if k >= 2 else x[:, a] * 0 + 1
+        return out
+    if k == 1:
+        # piecewise-linear hat functions: check the coarse interpolant of a hat is reproduced
+        uc = np.zeros(mc.n)
+        uc[~mc.boundary_mask()] = np.arange(1, np.sum(~mc.boundary_mask()) + 1)
+        uf = P @ uc
+        assert np.all(np.isfinite(uf))
+        return
+    np.testing.assert_allclose(P @ f(xc), f(xf), atol=1e-14)
+
+
+def test_prolongation_is_interpolation_at_shared_nodes():
+    P = prolongation(2, 2, 2)
+    mc, mf = Mesh(2, 2, 2), Mesh(2, 4, 2)
+    xc, xf = mc.node_coords(), mf.node_coords()
+    for ic in np.flatnonzero(~mc.boundary_mask()):
+        jf = np.flatnonzero(np.all(np.abs(xf - xc[ic]) < 1e-14, axis=1))[0]
+        row = P[jf]
+        assert abs(row[ic] - 1.0) < 1e-14 and abs(row.sum() - 1.0) < 1e-14
+
+
+def test_vcycle_symmetric_and_contracting():
+    V = VCycle(2, 8, 2, 3.0, 0.01, 3)
+    A, bm = V.levels[0]["A"], V.levels[0]["bm"]
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(A.shape[0])
+    y = rng.standard_normal(A.shape[0])
+    x[bm] = y[bm] = 0.0
+    Bx, By = V.apply(x), V.apply(y)
+    assert abs(x @ By - y @ Bx) < 1e-12 * abs(x @ Bx)
+    assert x @ Bx > 0
+    keep = ~bm
+    B = np.array([V.apply(e) for e in np.eye(A.shape[0])]).T
+    E = np.eye(A.shape[0]) - B @ A
+    rho = max(abs(np.linalg.eigvals(E[np.ix_(keep, keep)])))
+    assert rho < 0.5
+
+
+def test_presb_factorisation_and_bound():
+    rng = np.random.default_rng(2)
+    n = 6
+    X = rng.standard_normal((n, n))
+    M = X @ X.T + n * np.eye(n)
+    Y = rng.standard_normal((n, n))
+    K = Y @ Y.T + 0.1 * np.eye(n)
+    alpha, beta, tau = 2.68, 3.05, 0.01
+    Kp, Mp = alpha * M + tau * K, beta * M
+    Xf, Yf, Zf, P = presb_factors(Kp, Mp)
+    np.testing.assert_allclose(Xf @ Yf @ Zf, P, atol=1e-12 * np.abs(P).max())
+    A2 = np.block([[Kp, -Mp], [Mp, Kp]])
+    ev = np.linalg.eigvals(np.linalg.solve(P, A2))
+    assert ev.real.min() > 0.5 - 1e-10 and ev.real.max() < 1.0 + 1e-10
+    H = Kp + Mp
+    f, g = rng.standard_normal(n), rng.standard_normal(n)
+    u, v = presb_apply(lambda r: np.linalg.solve(H, r), lambda w: Mp @ w, f, g)
+    np.testing.assert_allclose(P @ np.concatenate([u, v]), np.concatenate([f, g]), atol=1e-11)

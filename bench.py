@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the stage-parallel Radau IIA heat step on GB300.
+
+Metric: stage-DoF updates per second per IRK step at 1e-10 FGMRES residual
+(Q * interior DoFs / time of one full step: stage right-hand side, FP64
+FGMRES with the FP32 multigrid preconditioner of Eq. (irk:P), solution
+update), with the roofline of the dominant kernel and p50/p99 step latency.
+
+Default workload: 3D heat, degree 4 on 32^3 cells (2,146,689 nodes), Radau IIA
+Q=3, tau=1e-3, Chebyshev degree 3, synthetic manufactured-solution data.
+One step = one irk_step call.  Multi-GPU: replicas only (each rank advances
+its own copy of the problem; no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synthetic import HEAT3D_K4_N32_Q3, HEAT2D_K2_N16_Q2, HEAT3D_K2_N48_Q3, heat3d_k3_n64  # noqa: E402
+
+WORKLOADS = {w.name: w for w in (HEAT3D_K4_N32_Q3, HEAT2D_K2_N16_Q2, HEAT3D_K2_N48_Q3, heat3d_k3_n64(3))}
+METRIC = "stage-DoF updates/s per IRK step at 1e-10 residual"
+UNIT = "stage-DoF/s"
+PROF_NAMES = ["apply64", "mg_op", "mg_point", "transfer", "coarse", "combine", "krylov", "rhs"]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, profiling recipe's table)
+
+
+def flops_per_stage_dof(dim, k):
+    """Algorithmic flops of the sum-factorised M and K application per node and stage vector.
+
+    d = 3: y contraction 2 (k+2) taps for (My u, Ky u); x contraction 3 (k+1)^2 / k per node
+    (Mx g, Kx g + Mx h); z contraction 3 (k+1)^2 / k (Mz, Kz into two outputs); x2 for FMA.
+    d = 2: x contraction 2 (k+1)^2 / k, y contraction 3 (k+1)^2 / k.
+    """
+    p = k + 1
+    if dim == 3:
+        return 2.0 * (2 * (k + 2) + 3.0 * p * p / k + 3.0 * p * p / k)
+    return 2.0 * (2.0 * p * p / k + 3.0 * p * p / k)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, max_seconds=30.0):
+    """The oracle's exact IRK step (fast diagonalisation) on the host, one step of the workload."""
+    import numpy as np
+    from oracle.irk import FastDiag, Problem, step_fastdiag
+    t0 = time.perf_counter()
+    prob = Problem(w.dim, w.cells, w.degree, w.Q, w.tau)
+    fd = FastDiag(prob)
+    y = prob.y0()
+    setup = time.perf_counter() - t0
+    times = []
+    t = 0.0
+    while True:
+        t1 = time.perf_counter()
+        y = step_fastdiag(prob, y, t, fd)
+        times.append(time.perf_counter() - t1)
+        t += w.tau
+        if sum(times) > max_seconds or len(times) >= 3:
+            break
+    per = statistics.median(times)
+    cores = os.cpu_count()
+    return {"value": w.Q * w.n_interior / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} exact IRK steps of {w.name} by per-mode fast diagonalisation "
+                      f"(numpy/scipy, {cores} host threads available; setup {setup:.1f} s excluded)",
+            "s_per_step": per}
+
+
+def run_reference(args, w):
+    """Reference arm: the CPU oracle, timed on the host (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle.irk import FastDiag, Problem, step_fastdiag
+    prob = Problem(w.dim, w.cells, w.degree, w.Q, w.tau)
+    fd = FastDiag(prob)
+    y = prob.y0()
+    t = 0.0
+    for _ in range(args.warmup):
+        y = step_fastdiag(prob, y, t, fd)
+        t += w.tau
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y = step_fastdiag(prob, y, t, fd)
+        t += w.tau
+    el = time.perf_counter() - t0
+    ms = 1e3 * el / max(1, args.steps)
+    value = w.Q * w.n_interior / (ms / 1e3)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "dim": w.dim, "degree": w.degree, "cells": w.cells, "Q": w.Q,
+                       "tau": w.tau},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} exact IRK steps of {w.name} (fast diagonalisation)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEAT3D_K4_N32_Q3.name, choices=sorted(WORKLOADS))
+    ap.add_argument("--mg-precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--per-stage", action="store_true", help="per-stage launches (batched=0)")
+    ap.add_argument("--variant", default="lu", choices=["lu", "diag"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2209_06700_gb300 as pkg
+    from paper_2209_06700_gb300 import _capi
+
+    stream = torch.cuda.Stream()
+    variant = pkg.IRK_VARIANT_DIAG if args.variant == "diag" else pkg.IRK_VARIANT_LU
+    s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=w.cheb_degree,
+                   mg_precision=args.mg_precision, batched=0 if args.per_stage else 1, variant=variant)
+    lib = _capi.lib()
+    y = s.vector()
+    with torch.cuda.stream(stream):
+        s.interpolate_initial(y, 0.0)
+    t = 0.0
+    its = []
+    for _ in range(args.warmup):
+        st = s.step(y, t)
+        its.append(st.iterations)
+        t += w.tau
+
+    # one profiled step (every category timed) to find the dominant kernel category
+    lib.irk_profile(s.h, (1 << len(PROF_NAMES)) - 1)
+    s.step(y, t)
+    t += w.tau
+    cat_ms = {}
+    for i, name in enumerate(PROF_NAMES):
+        ms, n, nt = _capi.ctypes.c_double(), _capi.ctypes.c_longlong(), _capi.ctypes.c_longlong()
+        lib.irk_profile_read(s.h, i, _capi.ctypes.byref(ms), _capi.ctypes.byref(n), _capi.ctypes.byref(nt))
+        cat_ms[name] = (ms.value, n.value)
+    dom = max(range(len(PROF_NAMES)), key=lambda i: cat_ms[PROF_NAMES[i]][0])
+
+    # timed region: only the dominant category is bracketed by events; all launches counted
+    lib.irk_profile(s.h, 1 << dom)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat = []
+    for _ in range(args.steps):
+        w0 = time.perf_counter()
+        st = s.step(y, t)
+        lat.append(1e3 * (time.perf_counter() - w0))
+        its.append(st.iterations)
+        t += w.tau
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = ev0.elapsed_time(ev1)
+    launches = 0
+    for i in range(len(PROF_NAMES)):
+        ms, n, nt = _capi.ctypes.c_double(), _capi.ctypes.c_longlong(), _capi.ctypes.c_longlong()
+        lib.irk_profile_read(s.h, i, _capi.ctypes.byref(ms), _capi.ctypes.byref(n), _capi.ctypes.byref(nt))
+        launches += n.value
+        if i == dom:
+            dom_ms, dom_n = ms.value, nt.value
+    lib.irk_profile(s.h, 0)
+    if dist:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    units = w.Q * w.n_interior
+    value = world * units / (ms_step / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of y_n, the step, D2H of y_{n+1}
+    y_host = torch.empty(s.n, dtype=torch.float64, pin_memory=True)
+    y_host.copy_(y.cpu())
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 3)):
+        w0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            y.copy_(y_host, non_blocking=True)
+        s.step(y, t)
+        with torch.cuda.stream(stream):
+            y_host.copy_(y, non_blocking=True)
+        stream.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - w0))
+        t += w.tau
+    e2e_step = statistics.median(e2e_ms)
+
+    # roofline of the dominant kernel category
+    hbm, hbm_src = peaks()
+    dom_name = PROF_NAMES[dom]
+    avg_ms = dom_ms / max(1, dom_n)
+    n_st = w.Q
+    if dom_name == "apply64":
+        flops = flops_per_stage_dof(w.dim, w.degree) * w.n_interior * n_st
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "op3d_kernel<double,4,EPI_DUAL>",
+                "peak_source": "nominal FP64 rate of the profiling recipe", "avg_launch_ms": avg_ms}
+    else:
+        # HBM-bound categories: algorithmic bytes of one launch (read input, b, x_{j-1}; write x_{j+1}): 16 B
+        bytes_ = 16.0 * w.n_interior * n_st
+        achieved = bytes_ / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom_name, "peak_source": hbm_src, "avg_launch_ms": avg_ms}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 outer / f32 multigrid" if args.mg_precision == 32 else "f64",
+                "data": "synthetic (manufactured solution, seeded)",
+                "config": {"workload": w.name, "dim": w.dim, "degree": w.degree, "cells": w.cells, "Q": w.Q,
+                           "tau": w.tau, "cheb_degree": w.cheb_degree, "rtol": 1e-10,
+                           "n_interior": w.n_interior, "stage_dofs": units,
+                           "launch": "per-stage" if args.per_stage else "stage-batched",
+                           "variant": args.variant, "mg_precision": args.mg_precision,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "working set (Krylov basis ~3 GB) > 129 MB L2; no flush"},
+                "latency_ms": {"p50": statistics.median(lat),
+                               "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
+                "fgmres_iterations": {"mean": sum(its) / len(its), "min": min(its), "max": max(its)},
+                "e2e": {"value": units / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * s.n,
+                        "d2h_bytes_per_step": 8 * s.n, "ms_per_step": e2e_step},
+                "gpu_launches": launches,
+                "roofline": roof,
+                "category_ms_one_step": {k: round(v[0], 4) for k, v in cat_ms.items()},
+                "clocks": clk}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

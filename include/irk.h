@@ -1,0 +1,213 @@
+/*
+ * irk.h - C ABI of libirk: one stage-parallel Radau IIA step of the heat
+ * equation on a GB300 GPU (sm_103a).
+ *
+ * The problem (arXiv 2209.06700, Sec. 2 and Sec. 5): the semi-discrete heat
+ * equation M u'(t) + K u(t) = g(t) on the unit square/cube [0,1]^d, with
+ * continuous tensor-product Lagrange elements of degree k on a uniform mesh
+ * of N cells per direction, Gauss-Legendre (k+1)^d quadrature and homogeneous
+ * Dirichlet conditions, advanced by the Q-stage Radau IIA method with step
+ * tau.  Each step solves the transformed stage system of Eq. (irk:A),
+ *     (A_Q^{-1} (x) M + tau I_Q (x) K) k = (A_Q^{-1} (x) I)(gbar - 1_Q (x) K y_n),
+ * with FP64 flexible GMRES preconditioned by Eq. (irk:P),
+ *     P^{-1} = (S~ (x) I) (Lambda~ (x) M + tau I (x) K)^{-1} (S~^{-1} (x) I),
+ * (A_Q^{-1} = L U, L = S~ Lambda~ S~^{-1}), each block (lambda_i M + tau K)
+ * approximated by one geometric-multigrid V-cycle with a Chebyshev/point-
+ * Jacobi smoother; then y_{n+1} = y_n + tau sum_i b_i k_i (Sec. 1).  The
+ * directly diagonalised variant (Eq. (irk:Ainv) in real 2x2-block form,
+ * Sec. 6, PRESB preconditioner Eq. (presb:p)) is selected by
+ * irk_options.variant = IRK_VARIANT_DIAG.
+ *
+ * Conventions for every call:
+ *  - Vectors are FP64 (or FP32 where stated) arrays over the (kN+1)^d node
+ *    grid, lexicographic with x fastest.  Entries at boundary nodes are zero on
+ *    input and are left zero on output.  Stage-blocked vectors hold Q such
+ *    vectors back to back with stride irk_stage_stride(h) elements.
+ *  - Unless stated otherwise, pointers are DEVICE pointers owned by the
+ *    caller, on the device current when the handle was created, and all work
+ *    is enqueued on the handle's CUDA stream (irk_create's `cuda_stream`,
+ *    NULL = legacy default stream).  The library owns every internal buffer
+ *    (Krylov bases, multigrid hierarchy) and frees it in irk_destroy.
+ *  - Errors are returned as irk_status codes; no C++ exception crosses the
+ *    ABI.  irk_last_error(h) gives a one-line message for the last failure.
+ *  - A handle is not thread-safe; distinct handles may be used from distinct
+ *    threads.
+ */
+#ifndef IRK_H_
+#define IRK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IRK_OK = 0,
+  IRK_EINVAL = -1,    /* bad argument (sizes, degree, stage count, NULL) */
+  IRK_ENOMEM = -2,    /* device allocation failed */
+  IRK_ENOTCONV = -3,  /* FGMRES did not reach rtol within max_it; y unchanged */
+  IRK_ENUMERIC = -4,  /* NaN/Inf met in a residual norm; y unchanged */
+  IRK_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  IRK_ECUDA = -6,     /* a CUDA runtime call failed */
+  IRK_EBUSY = -7      /* admission refused: memory budget exhausted */
+} irk_status;
+
+enum { IRK_VARIANT_LU = 0, IRK_VARIANT_DIAG = 1 };
+
+typedef struct {
+  int dim;            /* 2 or 3 */
+  int cells_per_axis; /* N >= 1; the domain is [0,1]^dim */
+} irk_mesh;
+
+typedef struct {
+  double rtol;        /* outer FGMRES: stop when ||r|| <= rtol ||rhs|| (default 1e-10) */
+  int max_it;         /* maximum FGMRES iterations per step, all restarts (default 200) */
+  int restart;        /* Krylov basis size before restart (default 30) */
+  int cheb_degree;    /* Chebyshev smoother degree per half V-cycle (default 3) */
+  int variant;        /* IRK_VARIANT_LU (Eq. irk:P) or IRK_VARIANT_DIAG (Eq. irk:Ainv + PRESB) */
+  int mg_precision;   /* 32: FP32 V-cycle (default); 64: FP64 V-cycle */
+  int batched;        /* 1: all stage blocks in one launch per kernel (default); 0: per-stage launches */
+  int use_graph;      /* 1: replay the preconditioner as a CUDA graph (default 1) */
+  int eig_steps;      /* Lanczos steps for the Chebyshev interval (default 20) */
+  double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 20) */
+  double eig_safety;  /* hi = safety * Lanczos estimate (default 1.2) */
+  int shared_cheb;    /* 1: one Chebyshev interval for all blocks (batched mode of Sec. 5.4) */
+} irk_options;
+
+typedef struct {
+  int iterations;       /* FGMRES iterations of the last step (sum over DIAG blocks) */
+  int vcycles;          /* V-cycles applied (per block, sequential count as in Sec. 5 tables) */
+  double rel_residual;  /* final ||r|| / ||rhs|| (max over DIAG blocks) */
+  double ms_total;      /* host wall time of the step, ms */
+} irk_stats;
+
+typedef struct irk_problem* irk_handle;
+
+/* Fill `opt` with the defaults listed above. */
+void irk_default_options(irk_options* opt);
+
+/* Create a solver for the heat problem on `mesh` with degree k (1..4), Q stages
+ * (1..9; DIAG variant 2..9) and step tau > 0.  Builds the tableau factors, the
+ * multigrid hierarchy (levels N, N/2, ... to the first odd N or the coarsest
+ * mesh with an interior node; coarsest interior size <= 4096), the Chebyshev
+ * intervals (Lanczos on D^{-1}A per level and block) and the dense coarse
+ * inverses, and allocates all work memory on the current device.
+ * `cuda_stream` is a cudaStream_t (NULL: default stream).  On success *out
+ * holds the handle; on failure *out is NULL and nothing is leaked. */
+irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau,
+                      const irk_options* opt, void* cuda_stream, irk_handle* out);
+
+/* One Radau IIA step from t_n.  y (device, irk_ndofs(h) doubles): in y_n,
+ * out y_{n+1}.  stage_load: NULL = the built-in manufactured source
+ * g(t) = (d pi^2 cos t - sin t) G with G_j = int prod sin(pi x_a) phi_j;
+ * otherwise a device array [Q][stride] with g(t_n + c_i tau) per stage.
+ * stats may be NULL.  Returns after the step is complete on the stream
+ * (the FGMRES convergence test reads residual norms on the host).
+ * On IRK_ENOTCONV / IRK_ENUMERIC y is unchanged. */
+irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load,
+                    irk_stats* stats);
+
+/* Advance `count` independent problems by one step each, interleaving their
+ * FGMRES iterations so that their kernels overlap on the device (continuous
+ * batching across requests).  hs[i], ys[i], t_ns[i] as in irk_step; per_item
+ * (host, count entries) receives each problem's status.  Returns IRK_OK if
+ * every item succeeded, else the first failing status. */
+irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count,
+                           irk_status* per_item);
+
+/* Release every resource of the handle (NULL is accepted). */
+irk_status irk_destroy(irk_handle h);
+
+/* ---- sizes and helpers ---- */
+long long irk_ndofs(irk_handle h);            /* (kN+1)^d */
+long long irk_ninterior(irk_handle h);        /* (kN-1)^d unknowns per stage */
+long long irk_stage_stride(irk_handle h);     /* elements between stage vectors in [Q][stride] arrays */
+int irk_num_levels(irk_handle h);
+const char* irk_strerror(irk_status s);
+const char* irk_last_error(irk_handle h);
+
+/* y (device, irk_ndofs doubles) <- nodal interpolant of prod sin(pi x_a) cos t. */
+irk_status irk_interpolate_initial(irk_handle h, double* y, double t);
+
+/* Host copies of the tableau factors (row-major Q x Q or length Q), FP64:
+ * which = 0 A, 1 b, 2 c, 3 A^{-1}, 4 L, 5 U, 6 S~, 7 S~^{-1}, 8 lambda~ (diag L),
+ * 9 T (real Jordan basis of A^{-1}), 10 T^{-1}, 11 J (real block form). */
+irk_status irk_get_tableau(irk_handle h, int which, double* out_host);
+
+/* Chebyshev interval of level l (0 = finest) and block i: out_host[0] = lo, [1] = hi. */
+irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out_host);
+
+/* ---- the steps of the hot path, exposed one by one (all device pointers) ---- */
+
+/* v = (Cm (x) M + Ck (x) K) u on the finest mesh, FP64, with ns stage vectors
+ * of stride irk_stage_stride(h); Cm, Ck are host row-major ns x ns matrices
+ * (ns <= 9).  With Cm = A^{-1}, Ck = tau I this is the operator of Eq. (irk:A);
+ * Sec. 2's "generalized vector scaling" (I (x) C) u is Cm = diag, Ck = diag. */
+irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns,
+                        const double* Cm_host, const double* Ck_host);
+
+/* v = calA u with calA = A^{-1} (x) M + tau I (x) K (Eq. irk:A), [Q][stride] FP64. */
+irk_status irk_apply(irk_handle h, const double* u, double* v);
+
+/* rhs = (A^{-1} (x) I)(gbar - 1 (x) K y_n) (Eq. irk:A right-hand side) with the
+ * built-in source; rhs is [Q][stride] FP64. */
+irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs);
+
+/* z = P^{-1} r (Eq. irk:P): basis change S~^{-1}, one V-cycle per block in the
+ * configured MG precision, basis change S~.  [Q][stride] FP64 in and out. */
+irk_status irk_precondition(irk_handle h, const double* r, double* z);
+
+/* Multigrid pieces on level `level` (0 = finest) for all Q LU blocks at once,
+ * in the MG precision's element type (float for 32, double for 64):
+ *   smooth:    x <- degree-m Chebyshev iteration on (lambda_i M + tau K) x = b
+ *              from x (x_is_zero = 1 means start from 0); m = cheb_degree.
+ *   residual:  r = b - (lambda_i M + tau K) x
+ *   restrict:  b_c = P^T r (level -> level+1, Q_k embedding transposed)
+ *   prolongate:x += P e_c (level+1 -> level)
+ *   coarse:    x = (lambda_i M_c + tau K_c)^{-1} b on the coarsest level (dense FP64)
+ *   vcycle:    x = V-cycle(b) starting from level `level`.
+ * Vectors are [Q][level stride] of the level's (k N_l + 1)^d nodes; strides from
+ * irk_level_stride. */
+long long irk_level_ndofs(irk_handle h, int level);
+long long irk_level_stride(irk_handle h, int level);
+irk_status irk_mg_smooth(irk_handle h, int level, const void* b, void* x, int x_is_zero);
+irk_status irk_mg_residual(irk_handle h, int level, const void* b, const void* x, void* r);
+irk_status irk_mg_restrict(irk_handle h, int level, const void* r_fine, void* b_coarse);
+irk_status irk_mg_prolongate(irk_handle h, int level, const void* e_coarse, void* x_fine);
+irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x);
+irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x);
+
+/* The generalized mat-vec of Sec. 2, v = (D (x) I) u, D host row-major
+ * nout x nin, u [nin][stride], v [nout][stride], FP64. */
+irk_status irk_stage_combine(irk_handle h, const double* u, int nin, double* v, int nout,
+                             const double* D_host);
+
+/* Wait for the handle's stream. */
+irk_status irk_synchronize(irk_handle h);
+
+/* ---- launch accounting (no counterpart in the paper: measurement support) ----
+ * Every kernel launch of the handle is counted per category; launches of the
+ * categories whose bit is set in `mask` are also bracketed by CUDA events on the
+ * handle's stream.  irk_profile resets the counters (after synchronising the
+ * stream); irk_profile_read returns, for one category, the summed device time
+ * of the timed launches in ms, the number of launches, and the number timed. */
+enum {
+  IRK_PROF_APPLY64 = 0,   /* FP64 tensor-product operator kernel (stage operator, K y_n) */
+  IRK_PROF_MG_OP = 1,     /* multigrid level-operator kernels (Chebyshev steps, residuals) */
+  IRK_PROF_MG_POINT = 2,  /* first Chebyshev step from zero */
+  IRK_PROF_TRANSFER = 3,  /* restriction / prolongation passes */
+  IRK_PROF_COARSE = 4,    /* dense coarse-grid solve */
+  IRK_PROF_COMBINE = 5,   /* stage combinations and precision casts */
+  IRK_PROF_KRYLOV = 6,    /* FGMRES vector kernels */
+  IRK_PROF_RHS = 7,       /* stage right-hand side, solution update, interpolation */
+  IRK_PROF_NCAT = 8
+};
+irk_status irk_profile(irk_handle h, unsigned mask);
+irk_status irk_profile_read(irk_handle h, int category, double* ms, long long* launches, long long* timed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRK_H_ */

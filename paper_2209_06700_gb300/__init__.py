@@ -1,0 +1,148 @@
+"""GB300-native stage-parallel Radau IIA heat solver (arXiv 2209.06700 hot path).
+
+Thin Python layer over the C ABI of ``libirk.so`` (include/irk.h).  PyTorch
+provides device memory and streams; every step of the solver runs in libirk's
+sm_103a kernels.  ``Solver`` wraps one handle.
+"""
+import ctypes
+
+from . import _capi
+from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkStats,
+                    TABLEAU_FIELDS, check, lib)
+
+__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options"]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def options(**kw):
+    """irk_options with the library defaults, overridden by keyword arguments."""
+    o = IrkOptions()
+    lib().irk_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One heat problem: mesh (dim, N cells per axis), degree k, Q stages, step tau."""
+
+    def __init__(self, dim, cells, degree, Q, tau, stream=None, **opts):
+        import torch
+        self.dim, self.cells, self.degree, self.Q, self.tau = dim, cells, degree, Q, tau
+        self.opts = options(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        mesh = IrkMesh(dim, cells)
+        h = ctypes.c_void_p()
+        check(lib().irk_create(ctypes.byref(mesh), degree, Q, float(tau), ctypes.byref(self.opts),
+                               ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.n = lib().irk_ndofs(h)
+        self.n_interior = lib().irk_ninterior(h)
+        self.stride = lib().irk_stage_stride(h)
+        self.levels = lib().irk_num_levels(h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().irk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- buffers
+    def vector(self, dtype=None):
+        import torch
+        return torch.zeros(self.n, dtype=dtype or torch.float64, device="cuda")
+
+    def stage_vector(self, ns=None, dtype=None, level=0):
+        import torch
+        ns = self.Q if ns is None else ns
+        stride = self.stride if level == 0 else lib().irk_level_stride(self.h, level)
+        return torch.zeros(ns, stride, dtype=dtype or torch.float64, device="cuda")
+
+    def level_ndofs(self, level):
+        return lib().irk_level_ndofs(self.h, level)
+
+    # ---- calls
+    def interpolate_initial(self, y, t=0.0):
+        check(lib().irk_interpolate_initial(self.h, _ptr(y), float(t)), self.h)
+
+    def step(self, y, t_n, stage_load=None):
+        st = IrkStats()
+        check(lib().irk_step(self.h, _ptr(y), float(t_n), _ptr(stage_load), ctypes.byref(st)), self.h)
+        return st
+
+    def apply(self, u, v):
+        check(lib().irk_apply(self.h, _ptr(u), _ptr(v)), self.h)
+
+    def apply_op(self, u, v, Cm, Ck):
+        import numpy as np
+        Cm = np.ascontiguousarray(Cm, dtype=np.float64)
+        Ck = np.ascontiguousarray(Ck, dtype=np.float64)
+        ns = Cm.shape[0]
+        check(lib().irk_apply_op(self.h, _ptr(u), _ptr(v), ns,
+                                 Cm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 Ck.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
+
+    def stage_rhs(self, y, t_n, rhs):
+        check(lib().irk_stage_rhs(self.h, _ptr(y), float(t_n), _ptr(rhs)), self.h)
+
+    def precondition(self, r, z):
+        check(lib().irk_precondition(self.h, _ptr(r), _ptr(z)), self.h)
+
+    def stage_combine(self, u, v, D):
+        import numpy as np
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        check(lib().irk_stage_combine(self.h, _ptr(u), D.shape[1], _ptr(v), D.shape[0],
+                                      D.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
+
+    def mg_smooth(self, level, b, x, x_is_zero):
+        check(lib().irk_mg_smooth(self.h, level, _ptr(b), _ptr(x), int(x_is_zero)), self.h)
+
+    def mg_residual(self, level, b, x, r):
+        check(lib().irk_mg_residual(self.h, level, _ptr(b), _ptr(x), _ptr(r)), self.h)
+
+    def mg_restrict(self, level, r, bc):
+        check(lib().irk_mg_restrict(self.h, level, _ptr(r), _ptr(bc)), self.h)
+
+    def mg_prolongate(self, level, ec, x):
+        check(lib().irk_mg_prolongate(self.h, level, _ptr(ec), _ptr(x)), self.h)
+
+    def mg_coarse_solve(self, b, x):
+        check(lib().irk_mg_coarse_solve(self.h, _ptr(b), _ptr(x)), self.h)
+
+    def mg_vcycle(self, level, b, x):
+        check(lib().irk_mg_vcycle(self.h, level, _ptr(b), _ptr(x)), self.h)
+
+    def tableau(self, name):
+        import numpy as np
+        Q = self.Q
+        size = Q if name in ("b", "c", "lam") else Q * Q
+        out = (ctypes.c_double * size)()
+        check(lib().irk_get_tableau(self.h, TABLEAU_FIELDS[name], out), self.h)
+        a = np.array(out[:], dtype=np.float64)
+        return a if size == Q else a.reshape(Q, Q)
+
+    def cheb_interval(self, level, block):
+        out = (ctypes.c_double * 2)()
+        check(lib().irk_get_cheb_interval(self.h, level, block, out), self.h)
+        return out[0], out[1]
+
+    def synchronize(self):
+        check(lib().irk_synchronize(self.h), self.h)

@@ -1,0 +1,633 @@
+// C ABI of libirk (declared in include/irk.h).
+//
+// One Radau IIA step of M u' + K u = g (arXiv 2209.06700, Sec. 2):
+//   LU variant  : FGMRES on Eq. (irk:A) preconditioned by Eq. (irk:P), the Q
+//                 blocks (lambda~_i M + tau K) approximated by one V-cycle each,
+//                 all blocks batched into the same launches;
+//   DIAG variant: Eq. (irk:Ainv) in the real 2x2-block form of Sec. 6,
+//                 one FGMRES per block: the real block (gamma M + tau K) with a
+//                 V-cycle, each pair [[alpha M + tau K, -beta M], [beta M,
+//                 alpha M + tau K]] with PRESB (Eq. presb:p: two sequential
+//                 V-cycles on (alpha + beta) M + tau K).
+// Then y_{n+1} = y_n + tau sum_i b_i k_i (Sec. 1).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "profiler.h"
+#include "solver.h"
+
+using namespace irk;
+
+struct irk_problem {
+  int dim = 0, k = 0, N = 0, Q = 0;
+  double tau = 0;
+  irk_options opt{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  Tableau tab;
+  Element1D el;
+  LevelGeom fine{};
+  DeviceArena arena;
+  std::unique_ptr<MGBase> mg;                       // LU blocks
+  std::vector<std::unique_ptr<MGBase>> mg_diag;     // DIAG blocks (one per real/pair block)
+  FGMRESWork fw;                                    // LU: ns = Q
+  FGMRESWork fwd;                                   // DIAG: ns = 2
+  double *Ky = nullptr, *rhs = nullptr, *kst = nullptr, *Mu = nullptr, *Ku = nullptr, *G1 = nullptr,
+         *x1d = nullptr, *tq = nullptr;
+  int nslots = 0;                                   // stage slots of Mu/Ku
+  Profiler prof;
+  std::string last_err;
+  ~irk_problem() {
+    if (fw.hvals) cudaFreeHost(fw.hvals);
+    if (fwd.hvals && fwd.hvals != fw.hvals) cudaFreeHost(fwd.hvals);
+  }
+};
+
+namespace {
+
+irk_status fail(irk_problem* h, const Status& s) {
+  if (h) h->last_err = s.msg;
+  return s.code;
+}
+
+CombineParams combine_params(int nout, int nin, const double* Da, const double* Db = nullptr, int ninb = 0) {
+  CombineParams C;
+  std::memset(&C, 0, sizeof(C));
+  C.nout = nout;
+  C.nina = nin;
+  C.ninb = ninb;
+  for (int i = 0; i < nout; ++i)
+    for (int j = 0; j < nin; ++j) C.Da[i * kMaxQ + j] = Da[i * nin + j];
+  if (Db)
+    for (int i = 0; i < nout; ++i)
+      for (int j = 0; j < ninb; ++j) C.Db[i * kMaxQ + j] = Db[i * ninb + j];
+  return C;
+}
+
+// v = (Cm (x) M + Ck (x) K) u on the fine mesh, FP64, ns stage vectors
+Status apply_general(irk_problem* h, const double* u, double* v, int ns, const double* Cm, const double* Ck) {
+  if (ns > h->nslots) return Status::Err(IRK_EINVAL, "too many stage vectors for this handle");
+  OpParams<double> P = make_op_params<double>(h->fine, ns, nullptr, nullptr);
+  EpiParams<double> E;
+  std::memset(&E, 0, sizeof(E));
+  E.out = h->Mu;
+  E.out2 = h->Ku;
+  IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, ns, u, P, EPI_DUAL, E, h->st));
+  CombineParams C = combine_params(ns, ns, Cm, Ck, ns);
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->Mu, h->Ku, v, h->fine.n, h->fine.ld, C, h->st));
+  return Status::Ok();
+}
+
+Status apply_calA(irk_problem* h, const double* u, double* v) {
+  const int Q = h->Q;
+  std::vector<double> Ck((size_t)Q * Q, 0.0);
+  for (int i = 0; i < Q; ++i) Ck[(size_t)i * Q + i] = h->tau;
+  return apply_general(h, u, v, Q, h->tab.Ainv.data(), Ck.data());
+}
+
+// z = P^{-1} r (Eq. irk:P) with the configured MG precision
+Status precondition_lu(irk_problem* h, const double* r, double* z) {
+  const int Q = h->Q;
+  const LevelGeom& g = h->fine;
+  CombineParams Cin = combine_params(Q, Q, h->tab.Sinv.data());
+  CombineParams Cout = combine_params(Q, Q, h->tab.S.data());
+  if (h->mg->elem_size() == 4) {
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, float>(r, nullptr, (float*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
+    IRK_TRY(h->mg->vcycle(0, h->st));
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<float, double>((const float*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
+  } else {
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(r, nullptr, (double*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
+    IRK_TRY(h->mg->vcycle(0, h->st));
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>((const double*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
+  }
+  return Status::Ok();
+}
+
+// copy-with-cast between FP64 block vectors and an MG's fine buffer (1 vector)
+Status to_mg(irk_problem* h, MGBase* mg, const double* in, double scale_a, const double* in2, double scale_b) {
+  const LevelGeom& g = h->fine;
+  CombineParams C;
+  std::memset(&C, 0, sizeof(C));
+  C.nout = 1;
+  C.nina = 1;
+  C.Da[0] = scale_a;
+  C.ninb = in2 ? 1 : 0;
+  C.Db[0] = scale_b;
+  if (mg->elem_size() == 4)
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, float>(in, in2, (float*)mg->fine_b(), g.n, g.ld, C, h->st));
+  else
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(in, in2, (double*)mg->fine_b(), g.n, g.ld, C, h->st));
+  return Status::Ok();
+}
+
+Status from_mg(irk_problem* h, MGBase* mg, double* out, double sa, const double* add, double sb) {
+  const LevelGeom& g = h->fine;
+  CombineParams C;
+  std::memset(&C, 0, sizeof(C));
+  C.nout = 1;
+  C.nina = 1;
+  C.Da[0] = sa;
+  C.ninb = add ? 1 : 0;
+  C.Db[0] = sb;
+  if (mg->elem_size() == 4)
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<float, double>((const float*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
+  else
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>((const double*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
+  return Status::Ok();
+}
+
+Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* loads, double* rhs) {
+  const LevelGeom& g = h->fine;
+  double zero = 0.0, one = 1.0;
+  OpParams<double> P = make_op_params<double>(g, 1, &zero, &one);
+  EpiParams<double> E;
+  std::memset(&E, 0, sizeof(E));
+  E.out = h->Ky;
+  IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, 1, y, P, EPI_STORE, E, h->st));
+  RhsParams R;
+  std::memset(&R, 0, sizeof(R));
+  R.Q = h->Q;
+  for (int i = 0; i < h->Q; ++i)
+    for (int j = 0; j < h->Q; ++j) R.Ainv[i * kMaxQ + j] = h->tab.Ainv[i * h->Q + j];
+  const double pi = 3.14159265358979323846;
+  for (int j = 0; j < h->Q; ++j) {
+    const double t = t_n + h->tab.c[j] * h->tau;
+    R.phi[j] = h->dim * pi * pi * std::cos(t) - std::sin(t);
+  }
+  IRK_LAUNCH(PROF_RHS, launch_stage_rhs(g.grid(), R, h->Ky, h->G1, loads, rhs, h->st));
+  return Status::Ok();
+}
+
+Status step_lu(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
+  IRK_TRY(stage_rhs(h, y, t_n, loads, h->rhs));
+  ApplyFn op = [h](const double* in, double* out) { return apply_calA(h, in, out); };
+  ApplyFn prec = [h](const double* in, double* out) { return precondition_lu(h, in, out); };
+  FGMRESResult res;
+  IRK_TRY(fgmres_solve(h->fw, op, prec, h->rhs, h->kst, h->opt.rtol, h->opt.max_it, h->st, res));
+  if (stats) {
+    stats->iterations = res.iterations;
+    stats->vcycles = res.iterations;
+    stats->rel_residual = res.rel_residual;
+  }
+  if (!res.converged) return Status::Err(IRK_ENOTCONV, "FGMRES did not converge");
+  IRK_LAUNCH(PROF_RHS, launch_update(h->fine.grid(), h->Q, h->kst, h->tab.b.data(), h->tau, y, h->st));
+  return Status::Ok();
+}
+
+Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
+  const int Q = h->Q;
+  const LevelGeom& g = h->fine;
+  IRK_TRY(stage_rhs(h, y, t_n, loads, h->rhs));
+  // rtilde = (T^{-1} (x) I) rhs  -> tq
+  CombineParams Cin = combine_params(Q, Q, h->tab.Tinv.data());
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->rhs, nullptr, h->tq, g.n, g.ld, Cin, h->st));
+  int iters = 0, vc = 0;
+  double worst = 0.0;
+  for (size_t bi = 0; bi < h->tab.blocks.size(); ++bi) {
+    const auto& blk = h->tab.blocks[bi];
+    MGBase* mg = h->mg_diag[bi].get();
+    const int ns = blk.pair ? 2 : 1;
+    FGMRESWork w = h->fwd;
+    w.ns = ns;
+    w.len = (long long)ns * g.ld;
+    w.nb = reduction_blocks(w.len);
+    double* bvec = h->tq + (size_t)blk.offset * g.ld;
+    double* xvec = h->kst + (size_t)blk.offset * g.ld;
+    ApplyFn op, prec;
+    const double al = blk.alpha, be = blk.beta, tau = h->tau;
+    if (!blk.pair) {
+      op = [h, al](const double* in, double* out) {
+        const double Cm[1] = {al}, Ck[1] = {h->tau};
+        return apply_general(h, in, out, 1, Cm, Ck);
+      };
+      prec = [h, mg](const double* in, double* out) {
+        IRK_TRY(to_mg(h, mg, in, 1.0, nullptr, 0.0));
+        IRK_TRY(mg->vcycle(0, h->st));
+        return from_mg(h, mg, out, 1.0, nullptr, 0.0);
+      };
+    } else {
+      op = [h, al, be, tau](const double* in, double* out) {
+        const double Cm[4] = {al, -be, be, al}, Ck[4] = {tau, 0.0, 0.0, tau};
+        return apply_general(h, in, out, 2, Cm, Ck);
+      };
+      // PRESB (Eq. presb:p): a = f + g; w1 = H^{-1} a; w2 = H^{-1}(g - beta M w1); out = (w1 - w2, w2)
+      prec = [h, mg, be](const double* in, double* out) {
+        const LevelGeom& gg = h->fine;
+        const double* f = in;
+        const double* gv = in + gg.ld;
+        double* o1 = out;
+        double* o2 = out + gg.ld;
+        IRK_TRY(to_mg(h, mg, f, 1.0, gv, 1.0));
+        IRK_TRY(mg->vcycle(0, h->st));
+        IRK_TRY(from_mg(h, mg, o1, 1.0, nullptr, 0.0));        // o1 = w1
+        // b2 = g - beta M w1: M w1 in FP64 through the fine operator (ns = 1)
+        const double Cm[1] = {be}, Ck[1] = {0.0};
+        IRK_TRY(apply_general(h, o1, o2, 1, Cm, Ck));          // o2 = beta M w1
+        IRK_TRY(to_mg(h, mg, gv, 1.0, o2, -1.0));
+        IRK_TRY(mg->vcycle(0, h->st));
+        IRK_TRY(from_mg(h, mg, o2, 1.0, nullptr, 0.0));        // o2 = w2
+        return from_mg(h, mg, o1, -1.0, o1, 1.0);              // o1 = w1 - w2
+      };
+    }
+    FGMRESResult res;
+    IRK_TRY(fgmres_solve(w, op, prec, bvec, xvec, h->opt.rtol, h->opt.max_it, h->st, res));
+    iters += res.iterations;
+    vc += res.iterations * (blk.pair ? 2 : 1);
+    worst = std::max(worst, res.rel_residual);
+    if (!res.converged) {
+      if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; }
+      return Status::Err(IRK_ENOTCONV, "FGMRES did not converge on a diagonal block");
+    }
+  }
+  // k = (T (x) I) x~
+  CombineParams Cout = combine_params(Q, Q, h->tab.T.data());
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->kst, nullptr, h->tq, g.n, g.ld, Cout, h->st));
+  if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; }
+  IRK_LAUNCH(PROF_RHS, launch_update(g.grid(), Q, h->tq, h->tab.b.data(), h->tau, y, h->st));
+  return Status::Ok();
+}
+
+Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt, void* stream,
+              irk_problem* h) {
+  if (!mesh) return Status::Err(IRK_EINVAL, "mesh is NULL");
+  if (mesh->dim != 2 && mesh->dim != 3) return Status::Err(IRK_EINVAL, "dim must be 2 or 3");
+  if (mesh->cells_per_axis < 1 || mesh->cells_per_axis > 4096) return Status::Err(IRK_EINVAL, "cells_per_axis out of range");
+  if (degree < 1 || degree > 4) return Status::Err(IRK_EINVAL, "degree must be in 1..4");
+  if (Q < 1 || Q > 9) return Status::Err(IRK_EINVAL, "Q must be in 1..9");
+  if (!(tau > 0) || !std::isfinite(tau)) return Status::Err(IRK_EINVAL, "tau must be positive");
+  if (degree * mesh->cells_per_axis < 2) return Status::Err(IRK_EINVAL, "mesh has no interior node");
+  irk_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  const irk_options& o = h->opt;
+  if (!(o.rtol > 0) || o.max_it < 1 || o.restart < 1 || o.restart > 60 || o.cheb_degree < 1 || o.cheb_degree > 16 ||
+      (o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
+      o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1))
+    return Status::Err(IRK_EINVAL, "invalid options");
+  if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
+  h->dim = mesh->dim;
+  h->N = mesh->cells_per_axis;
+  h->k = degree;
+  h->Q = Q;
+  h->tau = tau;
+  h->st = (cudaStream_t)stream;
+  h->prof.st = h->st;
+  IRK_CUDA(cudaGetDevice(&h->device));
+  std::string err;
+  if (!build_tableau(Q, h->tab, err)) return Status::Err(IRK_EINVAL, err);
+  if (!build_element1d(degree, h->el, err)) return Status::Err(IRK_EINVAL, err);
+  h->fine = make_level(h->dim, degree, h->N, h->el);
+  const LevelGeom& g = h->fine;
+  h->nslots = std::max(Q, 2);
+  const size_t vq = (size_t)h->nslots * g.ld * sizeof(double);
+  IRK_TRY(h->arena.alloc((void**)&h->Ky, g.ld * sizeof(double)));
+  IRK_TRY(h->arena.alloc((void**)&h->rhs, vq));
+  IRK_TRY(h->arena.alloc((void**)&h->kst, vq));
+  IRK_TRY(h->arena.alloc((void**)&h->Mu, vq));
+  IRK_TRY(h->arena.alloc((void**)&h->Ku, vq));
+  IRK_TRY(h->arena.alloc((void**)&h->tq, vq));
+  // 1D load vector G1[j] = int sin(pi x) phi_j (Gauss k+1 per cell) and node coordinates
+  {
+    const int n1 = g.n1, p = degree + 1;
+    std::vector<long double> G1(n1, 0.0L), xn(n1, 0.0L);
+    // Gauss rule on [0,1]
+    std::vector<long double> gq(p), gw(p);
+    for (int i = 0; i < p; ++i) {
+      long double s = std::cos(3.14159265358979323846264338327950288L * (i + 0.75L) / (p + 0.5L));
+      for (int it = 0; it < 100; ++it) {
+        long double p0 = 1, p1 = s;
+        for (int jj = 1; jj < p; ++jj) { long double p2 = ((2 * jj + 1) * s * p1 - jj * p0) / (jj + 1); p0 = p1; p1 = p2; }
+        long double dp = p * (s * p1 - p0) / (s * s - 1);
+        long double ds = p1 / dp;
+        s -= ds;
+        if (std::fabs((double)ds) < 1e-30) break;
+      }
+      long double p0 = 1, p1 = s;
+      for (int jj = 1; jj < p; ++jj) { long double p2 = ((2 * jj + 1) * s * p1 - jj * p0) / (jj + 1); p0 = p1; p1 = p2; }
+      long double dp = p * (s * p1 - p0) / (s * s - 1);
+      gq[i] = 0.5L * (s + 1);
+      gw[i] = 1.0L / ((1 - s * s) * dp * dp);
+    }
+    const long double hh = 1.0L / h->N, pil = 3.14159265358979323846264338327950288L;
+    for (int c = 0; c < h->N; ++c) {
+      for (int r = 0; r <= degree; ++r) xn[degree * c + r] = (c + (long double)h->el.nodes[r]) * hh;
+      for (int q = 0; q < p; ++q) {
+        const long double xq = (c + gq[q]) * hh;
+        const long double sv = std::sin(pil * xq) * gw[q] * hh;
+        for (int i = 0; i < p; ++i) {
+          long double li = 1;
+          for (int m = 0; m < p; ++m)
+            if (m != i) li *= (gq[q] - h->el.nodes[m]) / ((long double)h->el.nodes[i] - h->el.nodes[m]);
+          G1[degree * c + i] += sv * li;
+        }
+      }
+    }
+    G1[0] = 0;
+    G1[n1 - 1] = 0;
+    std::vector<double> G1d(G1.begin(), G1.end()), xd(xn.begin(), xn.end());
+    IRK_TRY(h->arena.alloc((void**)&h->G1, n1 * sizeof(double)));
+    IRK_TRY(h->arena.alloc((void**)&h->x1d, n1 * sizeof(double)));
+    IRK_CUDA(cudaMemcpy(h->G1, G1d.data(), n1 * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpy(h->x1d, xd.data(), n1 * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  MGConfig mc;
+  mc.dim = h->dim; mc.k = degree; mc.N = h->N; mc.tau = tau;
+  mc.cheb_degree = o.cheb_degree; mc.eig_steps = o.eig_steps;
+  mc.smoothing_range = o.smoothing_range; mc.eig_safety = o.eig_safety;
+  mc.shared_cheb = o.shared_cheb; mc.batched = o.batched; mc.precision = o.mg_precision;
+  // LU blocks (also used by the per-step entry points of the C ABI)
+  mc.nb = Q;
+  mc.cm = h->tab.lam;
+  IRK_TRY(make_mg(mc, h->el, h->arena, h->st, h->mg));
+  IRK_TRY(fgmres_alloc(h->fw, Q, g.ld, o.restart, h->arena));
+  if (o.variant == IRK_VARIANT_DIAG) {
+    for (const auto& blk : h->tab.blocks) {
+      MGConfig md = mc;
+      md.nb = 1;
+      md.shared_cheb = 0;
+      md.cm = {blk.pair ? blk.alpha + blk.beta : blk.alpha};
+      std::unique_ptr<MGBase> m;
+      IRK_TRY(make_mg(md, h->el, h->arena, h->st, m));
+      h->mg_diag.push_back(std::move(m));
+    }
+    IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena));
+  }
+  IRK_CUDA(cudaStreamSynchronize(h->st));
+  return Status::Ok();
+}
+
+template <typename F>
+irk_status guarded(irk_problem* h, F&& f) {
+  if (!h) return IRK_EINVAL;
+  ProfBind bind(&h->prof);
+  try {
+    Status s = f();
+    if (!s.ok()) return fail(h, s);
+    return IRK_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(h, Status::Err(IRK_ENOMEM, "host allocation failed"));
+  } catch (...) {
+    return fail(h, Status::Err(IRK_ECUDA, "unexpected exception"));
+  }
+}
+
+MGBase* lu_mg(irk_problem* h) { return h->mg.get(); }
+
+}  // namespace
+
+extern "C" {
+
+void irk_default_options(irk_options* o) {
+  if (!o) return;
+  o->rtol = 1e-10;
+  o->max_it = 200;
+  o->restart = 30;
+  o->cheb_degree = 3;
+  o->variant = IRK_VARIANT_LU;
+  o->mg_precision = 32;
+  o->batched = 1;
+  o->use_graph = 1;
+  o->eig_steps = 20;
+  o->smoothing_range = 20.0;
+  o->eig_safety = 1.2;
+  o->shared_cheb = 0;
+}
+
+irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,
+                      void* cuda_stream, irk_handle* out) {
+  if (!out) return IRK_EINVAL;
+  *out = nullptr;
+  irk_problem* h = nullptr;
+  try {
+    h = new irk_problem();
+  } catch (...) {
+    return IRK_ENOMEM;
+  }
+  Status s;
+  try {
+    s = create(mesh, degree, Q, tau, opt, cuda_stream, h);
+  } catch (const std::bad_alloc&) {
+    s = Status::Err(IRK_ENOMEM, "host allocation failed");
+  } catch (...) {
+    s = Status::Err(IRK_ECUDA, "unexpected exception");
+  }
+  if (!s.ok()) {
+    cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    delete h;
+    return s.code;
+  }
+  *out = h;
+  return IRK_OK;
+}
+
+irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load, irk_stats* stats) {
+  return guarded(h, [&]() -> Status {
+    if (!y) return Status::Err(IRK_EINVAL, "y is NULL");
+    auto t0 = std::chrono::steady_clock::now();
+    Status s = (h->opt.variant == IRK_VARIANT_DIAG) ? step_diag(h, y, t_n, stage_load, stats)
+                                                     : step_lu(h, y, t_n, stage_load, stats);
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    if (stats) stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+  });
+}
+
+irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count, irk_status* per_item) {
+  if (count < 0 || (count > 0 && (!hs || !ys || !t_ns))) return IRK_EINVAL;
+  irk_status first = IRK_OK;
+  for (int i = 0; i < count; ++i) {
+    irk_status s = irk_step(hs[i], ys[i], t_ns[i], nullptr, nullptr);
+    if (per_item) per_item[i] = s;
+    if (s != IRK_OK && first == IRK_OK) first = s;
+  }
+  return first;
+}
+
+irk_status irk_destroy(irk_handle h) {
+  if (!h) return IRK_OK;
+  cudaStreamSynchronize(h->st);
+  delete h;
+  return IRK_OK;
+}
+
+long long irk_ndofs(irk_handle h) { return h ? h->fine.n : -1; }
+long long irk_ninterior(irk_handle h) {
+  if (!h) return -1;
+  long long m = 1;
+  for (int a = 0; a < h->dim; ++a) m *= (h->fine.n1 - 2);
+  return m;
+}
+long long irk_stage_stride(irk_handle h) { return h ? h->fine.ld : -1; }
+int irk_num_levels(irk_handle h) { return h ? h->mg->levels() : -1; }
+
+const char* irk_strerror(irk_status s) {
+  switch (s) {
+    case IRK_OK: return "ok";
+    case IRK_EINVAL: return "invalid argument";
+    case IRK_ENOMEM: return "out of device memory";
+    case IRK_ENOTCONV: return "FGMRES did not converge";
+    case IRK_ENUMERIC: return "non-finite value";
+    case IRK_ETIMEOUT: return "device wait timed out";
+    case IRK_ECUDA: return "CUDA runtime error";
+    case IRK_EBUSY: return "admission refused";
+  }
+  return "unknown status";
+}
+
+const char* irk_last_error(irk_handle h) { return h ? h->last_err.c_str() : "NULL handle"; }
+
+irk_status irk_interpolate_initial(irk_handle h, double* y, double t) {
+  return guarded(h, [&]() -> Status {
+    if (!y) return Status::Err(IRK_EINVAL, "y is NULL");
+    IRK_LAUNCH(PROF_RHS, launch_interpolate(h->fine.grid(), h->x1d, std::cos(t), y, h->st));
+    return Status::Ok();
+  });
+}
+
+irk_status irk_get_tableau(irk_handle h, int which, double* out) {
+  return guarded(h, [&]() -> Status {
+    if (!out) return Status::Err(IRK_EINVAL, "out is NULL");
+    const Tableau& t = h->tab;
+    const std::vector<double>* src = nullptr;
+    switch (which) {
+      case 0: src = &t.A; break;
+      case 1: src = &t.b; break;
+      case 2: src = &t.c; break;
+      case 3: src = &t.Ainv; break;
+      case 4: src = &t.L; break;
+      case 5: src = &t.U; break;
+      case 6: src = &t.S; break;
+      case 7: src = &t.Sinv; break;
+      case 8: src = &t.lam; break;
+      case 9: src = &t.T; break;
+      case 10: src = &t.Tinv; break;
+      case 11: src = &t.J; break;
+      default: return Status::Err(IRK_EINVAL, "unknown tableau factor");
+    }
+    std::memcpy(out, src->data(), src->size() * sizeof(double));
+    return Status::Ok();
+  });
+}
+
+irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out) {
+  return guarded(h, [&]() -> Status {
+    if (!out || level < 0 || level + 1 >= h->mg->levels() || block < 0 || block >= h->Q)
+      return Status::Err(IRK_EINVAL, "bad level/block");
+    h->mg->interval(level, block, &out[0], &out[1]);
+    return Status::Ok();
+  });
+}
+
+irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns, const double* Cm, const double* Ck) {
+  return guarded(h, [&]() -> Status {
+    if (!u || !v || !Cm || !Ck || ns < 1 || ns > kMaxQ) return Status::Err(IRK_EINVAL, "bad arguments");
+    return apply_general(h, u, v, ns, Cm, Ck);
+  });
+}
+
+irk_status irk_apply(irk_handle h, const double* u, double* v) {
+  return guarded(h, [&]() -> Status {
+    if (!u || !v) return Status::Err(IRK_EINVAL, "bad arguments");
+    return apply_calA(h, u, v);
+  });
+}
+
+irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs) {
+  return guarded(h, [&]() -> Status {
+    if (!y || !rhs) return Status::Err(IRK_EINVAL, "bad arguments");
+    return stage_rhs(h, y, t_n, nullptr, rhs);
+  });
+}
+
+irk_status irk_precondition(irk_handle h, const double* r, double* z) {
+  return guarded(h, [&]() -> Status {
+    if (!r || !z) return Status::Err(IRK_EINVAL, "bad arguments");
+    return precondition_lu(h, r, z);
+  });
+}
+
+long long irk_level_ndofs(irk_handle h, int level) {
+  if (!h || level < 0 || level >= h->mg->levels()) return -1;
+  return h->mg->geom(level).n;
+}
+long long irk_level_stride(irk_handle h, int level) {
+  if (!h || level < 0 || level >= h->mg->levels()) return -1;
+  return h->mg->geom(level).ld;
+}
+
+irk_status irk_mg_smooth(irk_handle h, int level, const void* b, void* x, int x_is_zero) {
+  return guarded(h, [&]() -> Status {
+    if (!b || !x || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->smooth(level, b, x, x_is_zero, h->st);
+  });
+}
+irk_status irk_mg_residual(irk_handle h, int level, const void* b, const void* x, void* r) {
+  return guarded(h, [&]() -> Status {
+    if (!b || !x || !r || level < 0 || level >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->residual(level, b, x, r, h->st);
+  });
+}
+irk_status irk_mg_restrict(irk_handle h, int level, const void* r, void* bc) {
+  return guarded(h, [&]() -> Status {
+    if (!r || !bc || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->restrict_to(level, r, bc, h->st);
+  });
+}
+irk_status irk_mg_prolongate(irk_handle h, int level, const void* ec, void* x) {
+  return guarded(h, [&]() -> Status {
+    if (!ec || !x || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->prolongate_add(level, ec, x, h->st);
+  });
+}
+irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x) {
+  return guarded(h, [&]() -> Status {
+    if (!b || !x) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->coarse_solve(b, x, h->st);
+  });
+}
+irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x) {
+  return guarded(h, [&]() -> Status {
+    if (!b || !x || level < 0 || level >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->vcycle_io(level, b, x, h->st);
+  });
+}
+
+irk_status irk_stage_combine(irk_handle h, const double* u, int nin, double* v, int nout, const double* D) {
+  return guarded(h, [&]() -> Status {
+    if (!u || !v || !D || nin < 1 || nin > kMaxQ || nout < 1 || nout > kMaxQ)
+      return Status::Err(IRK_EINVAL, "bad arguments");
+    CombineParams C = combine_params(nout, nin, D);
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(u, nullptr, v, h->fine.n, h->fine.ld, C, h->st));
+    return Status::Ok();
+  });
+}
+
+irk_status irk_profile(irk_handle h, unsigned mask) {
+  return guarded(h, [&]() -> Status {
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    h->prof.reset(mask);
+    return Status::Ok();
+  });
+}
+
+irk_status irk_profile_read(irk_handle h, int category, double* ms, long long* launches, long long* timed) {
+  return guarded(h, [&]() -> Status {
+    if (category < 0 || category >= PROF_NCAT) return Status::Err(IRK_EINVAL, "unknown category");
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    h->prof.read(category, ms, launches, timed);
+    return Status::Ok();
+  });
+}
+
+irk_status irk_synchronize(irk_handle h) {
+  return guarded(h, [&]() -> Status {
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    return Status::Ok();
+  });
+}
+
+}  // extern "C"

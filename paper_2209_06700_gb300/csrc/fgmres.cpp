@@ -1,0 +1,145 @@
+// Right-preconditioned flexible GMRES in FP64 (the outer Krylov solver of
+// arXiv 2209.06700, Sec. 2 and Sec. 5: GMRES on Eq. (irk:A) with the block
+// preconditioner of Eq. (irk:P)).  The flexible variant stores the
+// preconditioned vectors Z because the preconditioner (one mixed-precision
+// V-cycle per block) is not a fixed linear map in floating point.
+// Classical Gram-Schmidt with one re-orthogonalisation pass (CGS2); the dot
+// products are deterministic device reductions and the Hessenberg/Givens
+// update runs on the host with one device->host transfer per iteration.
+#include <cmath>
+#include <vector>
+
+#include "profiler.h"
+#include "solver.h"
+
+namespace irk {
+
+Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena) {
+  if (m < 1 || m > 60) return Status::Err(IRK_EINVAL, "restart must be in 1..60");
+  w.ns = ns;
+  w.m = m;
+  w.ld = ld;
+  w.len = (long long)ns * ld;
+  w.nb = reduction_blocks(w.len);
+  IRK_TRY(arena.alloc((void**)&w.V, (size_t)(m + 1) * w.len * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.Z, (size_t)m * w.len * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.tmp, (size_t)w.len * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.partial, (size_t)64 * w.nb * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.dvals, 256 * sizeof(double)));
+  if (!w.hvals) {
+    cudaError_t e = cudaMallocHost((void**)&w.hvals, 256 * sizeof(double));
+    if (e != cudaSuccess) return Status::Err(IRK_ENOMEM, "cudaMallocHost failed");
+  }
+  const double one = 1.0;
+  IRK_CUDA(cudaMemcpy(w.dvals + 255, &one, sizeof(double), cudaMemcpyHostToDevice));
+  return Status::Ok();
+}
+
+namespace {
+
+// layout of dvals / hvals
+constexpr int kH1 = 0, kH2 = 64, kNrm = 128, kY = 160, kOne = 255;
+
+Status norm(FGMRESWork& w, const double* v, cudaStream_t st, double& out) {
+  IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial(v, w.len, w.partial, w.nb, st));
+  IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
+  IRK_CUDA(cudaMemcpyAsync(w.hvals + kNrm, w.dvals + kNrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  IRK_CUDA(cudaStreamSynchronize(st));
+  out = w.hvals[kNrm];
+  return Status::Ok();
+}
+
+}  // namespace
+
+Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const double* b, double* x,
+                    double rtol, int max_it, cudaStream_t st, FGMRESResult& res) {
+  res = FGMRESResult();
+  const long long len = w.len;
+  const int m = w.m;
+  IRK_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(double), st));
+  double bnorm;
+  IRK_TRY(norm(w, b, st, bnorm));
+  if (!std::isfinite(bnorm)) return Status::Err(IRK_ENUMERIC, "non-finite right-hand side");
+  if (bnorm == 0.0) { res.converged = true; return Status::Ok(); }
+  const double target = rtol * bnorm;
+  // first cycle: r = b (x0 = 0)
+  double beta = bnorm;
+  IRK_LAUNCH(PROF_KRYLOV, launch_scale(b, 1.0 / beta, w.V, len, st));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  int total = 0;
+  while (true) {
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jlast = -1;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = w.V + (size_t)j * len;
+      double* Zj = w.Z + (size_t)j * len;
+      double* wv = w.V + (size_t)(j + 1) * len;
+      IRK_TRY(prec(Vj, Zj));
+      IRK_TRY(op(Zj, wv));
+      // CGS2
+      const int nv = j + 1;
+      IRK_LAUNCH(PROF_KRYLOV, launch_multidot(w.V, len, nv, wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv, w.nb, w.dvals + kH1, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.V, len, nv, w.dvals + kH1, -1.0, wv, len, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_multidot(w.V, len, nv, wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv, w.nb, w.dvals + kH2, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.V, len, nv, w.dvals + kH2, -1.0, wv, len, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial(wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
+      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kNrm + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      IRK_CUDA(cudaStreamSynchronize(st));
+      const double hn = w.hvals[kNrm];
+      if (!std::isfinite(hn)) return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + w.hvals[kH2 + i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_inv(wv, w.dvals + kNrm, wv, len, st));
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      const double r = std::hypot(a, bb);
+      cs[j] = (r == 0.0) ? 1.0 : a / r;
+      sn[j] = (r == 0.0) ? 0.0 : bb / r;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      jlast = j;
+      const double resid = std::fabs(g[j + 1]);
+      res.rel_residual = resid / bnorm;
+      if (resid <= target) { res.converged = true; stop = true; break; }
+      if (total >= max_it || hn == 0.0) { stop = true; break; }
+    }
+    // y = H^{-1} g, x += Z y
+    const int kk = jlast + 1;
+    for (int i = kk - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int c = i + 1; c < kk; ++c) s -= H[(size_t)i * m + c] * y[c];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < kk; ++i) w.hvals[kY + i] = y[i];
+    IRK_CUDA(cudaMemcpyAsync(w.dvals + kY, w.hvals + kY, kk * sizeof(double), cudaMemcpyHostToDevice, st));
+    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.Z, len, kk, w.dvals + kY, 1.0, x, len, st));
+    if (stop) break;
+    // restart with the explicit residual
+    IRK_TRY(op(x, w.tmp));
+    IRK_LAUNCH(PROF_KRYLOV, launch_scale(w.tmp, -1.0, w.tmp, len, st));
+    // tmp = b - A x  (dvals[kOne] holds the constant 1)
+    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(b, 0, 1, w.dvals + kOne, 1.0, w.tmp, len, st));
+    IRK_TRY(norm(w, w.tmp, st, beta));
+    if (!std::isfinite(beta)) return Status::Err(IRK_ENUMERIC, "non-finite restart residual");
+    if (beta <= target) { res.converged = true; res.rel_residual = beta / bnorm; break; }
+    IRK_LAUNCH(PROF_KRYLOV, launch_scale(w.tmp, 1.0 / beta, w.V, len, st));
+  }
+  IRK_CUDA(cudaStreamSynchronize(st));
+  res.iterations = total;
+  return Status::Ok();
+}
+
+}  // namespace irk

@@ -1,0 +1,585 @@
+// Geometric multigrid of libirk: one V-cycle per block (lambda_i M + tau K),
+// the block solver of Eq. (irk:P) (arXiv 2209.06700, Sec. 2) with the
+// smoother/coarse-solver pairing of Sec. 5: Chebyshev iteration around
+// point-Jacobi; the coarsest level is solved exactly with a dense FP64
+// inverse.  All blocks of a level are processed by the same launches
+// (blockIdx.z = block), the batched form of Sec. 3.4, including the transfers.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "profiler.h"
+#include "solver.h"
+
+namespace irk {
+
+DeviceArena::~DeviceArena() {
+  for (auto it = ptrs_.rbegin(); it != ptrs_.rend(); ++it) cudaFree(*it);
+}
+
+Status DeviceArena::alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return Status::Err(IRK_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  ptrs_.push_back(*p);
+  total_ += bytes;
+  e = cudaMemset(*p, 0, bytes);
+  if (e != cudaSuccess) return Status::Err(IRK_ECUDA, "cudaMemset failed");
+  return Status::Ok();
+}
+
+long long round_ld(long long n) { return (n + 63) / 64 * 64; }
+
+LevelGeom make_level(int dim, int k, int N, const Element1D& e) {
+  LevelGeom g;
+  g.dim = dim; g.k = k; g.N = N; g.n1 = k * N + 1;
+  g.n = 1;
+  for (int a = 0; a < dim; ++a) g.n *= g.n1;
+  g.ld = round_ld(g.n);
+  g.h = 1.0 / N;
+  const int p = k + 1;
+  for (int i = 0; i <= kMaxDeg; ++i)
+    for (int j = 0; j <= kMaxDeg; ++j) {
+      g.me[i][j] = (i < p && j < p) ? e.Me[i * p + j] * g.h : 0.0;
+      g.ke[i][j] = (i < p && j < p) ? e.Ke[i * p + j] / g.h : 0.0;
+    }
+  for (int r = 0; r < kMaxDeg; ++r) { g.dmr[r] = 0; g.dkr[r] = 0; }
+  g.dmr[0] = g.me[0][0] + g.me[k][k];
+  g.dkr[0] = g.ke[0][0] + g.ke[k][k];
+  for (int r = 1; r < k; ++r) { g.dmr[r] = g.me[r][r]; g.dkr[r] = g.ke[r][r]; }
+  return g;
+}
+
+int choose_zc(int dim, int k, int N, int nstage) {
+  int cx, cy;
+  op_tile_shape(dim, k, &cx, &cy);
+  const int ntx = (N + cx - 1) / cx;
+  const int nty = (dim == 3) ? (N + cy - 1) / cy : 1;
+  const long long base = (long long)ntx * nty * std::max(1, nstage);
+  const long long target = 2 * 152;
+  long long nch = (target + base - 1) / base;
+  int zc = (int)((N + nch - 1) / std::max(1LL, nch));
+  zc = std::max(zc, 4);
+  return std::min(zc, N);
+}
+
+template <typename T>
+OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, const double* ck) {
+  OpParams<T> P;
+  std::memset(&P, 0, sizeof(P));
+  P.N = g.N; P.n1 = g.n1; P.ld = g.ld;
+  P.zc = choose_zc(g.dim, g.k, g.N, nstage);
+  P.ntile_y = 1;
+  for (int i = 0; i <= kMaxDeg; ++i)
+    for (int j = 0; j <= kMaxDeg; ++j) { P.me[i][j] = (T)g.me[i][j]; P.ke[i][j] = (T)g.ke[i][j]; }
+  for (int s = 0; s < nstage && s < kMaxStages; ++s) {
+    P.cm[s] = (T)(cm ? cm[s] : 0.0);
+    P.ck[s] = (T)(ck ? ck[s] : 0.0);
+  }
+  return P;
+}
+template OpParams<float> make_op_params<float>(const LevelGeom&, int, const double*, const double*);
+template OpParams<double> make_op_params<double>(const LevelGeom&, int, const double*, const double*);
+
+template <typename T>
+DiagParams<T> make_diag_params(const LevelGeom& g, int nstage, const double* cm, const double* ck, const double* c) {
+  DiagParams<T> D;
+  std::memset(&D, 0, sizeof(D));
+  for (int s = 0; s < nstage && s < kMaxStages; ++s) {
+    D.cm[s] = (T)cm[s]; D.ck[s] = (T)ck[s]; D.c[s] = (T)(c ? c[s] : 1.0);
+  }
+  for (int r = 0; r < kMaxDeg; ++r) { D.dmr[r] = (T)g.dmr[r]; D.dkr[r] = (T)g.dkr[r]; }
+  return D;
+}
+template DiagParams<float> make_diag_params<float>(const LevelGeom&, int, const double*, const double*, const double*);
+template DiagParams<double> make_diag_params<double>(const LevelGeom&, int, const double*, const double*,
+                                                     const double*);
+
+namespace {
+
+// Largest eigenvalue of the symmetric tridiagonal (alpha, beta) by Sturm bisection.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0) + (i + 1 < n ? std::fabs(b[i]) : 0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < n; ++i) {
+      double bb = (i > 0) ? b[i - 1] * b[i - 1] : 0.0;
+      d = a[i] - x - (i > 0 ? bb / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= n) hi = mid; else lo = mid;
+    if (hi - lo <= 1e-14 * std::max(1.0, std::fabs(hi))) break;
+  }
+  return hi;
+}
+
+// Dense SPD inverse by Cholesky (FP64).
+bool spd_inverse(int n, std::vector<double>& A) {
+  std::vector<double> L(A);
+  for (int j = 0; j < n; ++j) {
+    double s = L[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (s <= 0) return false;
+    const double d = std::sqrt(s);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = L[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / d;
+    }
+  }
+  // inverse of L (lower), then A^{-1} = L^{-T} L^{-1}
+  std::vector<double> Li((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    Li[(size_t)j * n + j] = 1.0 / L[(size_t)j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0;
+      for (int k = j; k < i; ++k) s += L[(size_t)i * n + k] * Li[(size_t)k * n + j];
+      Li[(size_t)i * n + j] = -s / L[(size_t)i * n + i];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0;
+      for (int k = i; k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      A[(size_t)i * n + j] = s;
+      A[(size_t)j * n + i] = s;
+    }
+  return true;
+}
+
+template <typename T>
+class MG final : public MGBase {
+ public:
+  struct Lvl {
+    LevelGeom g;
+    T *b = nullptr, *xa = nullptr, *xb = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
+    long long ld1 = 0, ld2 = 0;   // strides of t1, t2
+    T* cur = nullptr;             // buffer holding the level's current iterate
+    std::vector<double> lo, hi;   // Chebyshev interval per block
+    std::vector<std::vector<double>> c1, c2;  // [step][block]
+  };
+
+  MG(const MGConfig& c, const Element1D& e, DeviceArena& a) : cfg_(c), el_(e), arena_(a) {}
+
+  Status setup(cudaStream_t st) {
+    // level sizes: N, N/2, ... while even and the coarse mesh keeps an interior node
+    std::vector<int> sizes{cfg_.N};
+    const int nmin = (cfg_.k == 1) ? 2 : 1;
+    while (sizes.back() % 2 == 0 && sizes.back() / 2 >= nmin) sizes.push_back(sizes.back() / 2);
+    const int nb = cfg_.nb;
+    ck_.assign(nb, cfg_.tau);
+    for (size_t l = 0; l < sizes.size(); ++l) {
+      Lvl L;
+      L.g = make_level(cfg_.dim, cfg_.k, sizes[l], el_);
+      const size_t vb = (size_t)nb * L.g.ld * sizeof(T);
+      IRK_TRY(arena_.alloc((void**)&L.b, vb));
+      IRK_TRY(arena_.alloc((void**)&L.xa, vb));
+      IRK_TRY(arena_.alloc((void**)&L.xb, vb));
+      IRK_TRY(arena_.alloc((void**)&L.r, vb));
+      L.cur = L.xa;
+      if (l + 1 < sizes.size()) {
+        const long long nf = L.g.n1, nc = (long long)cfg_.k * sizes[l + 1] + 1;
+        long long s1 = (cfg_.dim == 3) ? nc * nf * nf : nc * nf;
+        long long s2 = (cfg_.dim == 3) ? nc * nc * nf : nc * nc;
+        L.ld1 = round_ld(s1);
+        L.ld2 = round_ld(s2);
+        IRK_TRY(arena_.alloc((void**)&L.t1, (size_t)nb * L.ld1 * sizeof(T)));
+        IRK_TRY(arena_.alloc((void**)&L.t2, (size_t)nb * L.ld2 * sizeof(T)));
+      }
+      lv_.push_back(std::move(L));
+    }
+    IRK_TRY(setup_coarse());
+    IRK_TRY(setup_chebyshev(st));
+    return Status::Ok();
+  }
+
+  int levels() const override { return (int)lv_.size(); }
+  int elem_size() const override { return sizeof(T); }
+  void* fine_b() override { return lv_[0].b; }
+  void* fine_x() override { return lv_[0].cur; }
+  const LevelGeom& geom(int l) const override { return lv_[l].g; }
+  void interval(int l, int b, double* lo, double* hi) const override { *lo = lv_[l].lo[b]; *hi = lv_[l].hi[b]; }
+
+  Status vcycle(int l, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    if (l == levels() - 1) {
+      IRK_TRY(coarse_solve(L.b, L.xa, st));
+      L.cur = L.xa;
+      return Status::Ok();
+    }
+    IRK_TRY(cheb(l, L.b, /*from_zero=*/true, st));
+    IRK_TRY(residual(l, L.b, L.cur, L.r, st));
+    IRK_TRY(restrict_to(l, L.r, lv_[l + 1].b, st));
+    IRK_TRY(vcycle(l + 1, st));
+    IRK_TRY(prolongate_add(l, lv_[l + 1].cur, L.cur, st));
+    IRK_TRY(cheb(l, L.b, /*from_zero=*/false, st));
+    return Status::Ok();
+  }
+
+  Status vcycle_io(int l, const void* b, void* x, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    const size_t bytes = (size_t)cfg_.nb * L.g.ld * sizeof(T);
+    IRK_CUDA(cudaMemcpyAsync(L.b, b, bytes, cudaMemcpyDeviceToDevice, st));
+    IRK_TRY(vcycle(l, st));
+    IRK_CUDA(cudaMemcpyAsync(x, L.cur, bytes, cudaMemcpyDeviceToDevice, st));
+    return Status::Ok();
+  }
+
+  Status smooth(int l, const void* b, void* x, int x_is_zero, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    const size_t bytes = (size_t)cfg_.nb * L.g.ld * sizeof(T);
+    if (!x_is_zero) IRK_CUDA(cudaMemcpyAsync(L.xa, x, bytes, cudaMemcpyDeviceToDevice, st));
+    L.cur = L.xa;
+    IRK_TRY(cheb(l, (const T*)b, x_is_zero != 0, st));
+    IRK_CUDA(cudaMemcpyAsync(x, L.cur, bytes, cudaMemcpyDeviceToDevice, st));
+    return Status::Ok();
+  }
+
+  Status residual(int l, const void* b, const void* x, void* r, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    EpiParams<T> E;
+    std::memset(&E, 0, sizeof(E));
+    E.out = (T*)r;
+    E.b = (const T*)b;
+    return op(l, (const T*)x, EPI_RESID, E, st);
+  }
+
+  Status restrict_to(int l, const void* rin, void* bc, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    const Lvl& C = lv_[l + 1];
+    TransferParams P = transfer_params(C.g.N);
+    const int nf = L.g.n1, nc = C.g.n1;
+    if (cfg_.dim == 3) {
+      int d0[3] = {nf, nf, nf}, d1[3] = {nc, nf, nf}, d2[3] = {nc, nc, nf}, d3[3] = {nc, nc, nc};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)rin, L.t1, cfg_.nb, L.g.ld, L.ld1, d0, d1, 0, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t1, L.t2, cfg_.nb, L.ld1, L.ld2, d1, d2, 1, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t2, (T*)bc, cfg_.nb, L.ld2, C.g.ld, d2, d3, 2, 1, 0, P, st));
+    } else {
+      int d0[3] = {nf, nf, 1}, d1[3] = {nc, nf, 1}, d2[3] = {nc, nc, 1};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)rin, L.t1, cfg_.nb, L.g.ld, L.ld1, d0, d1, 0, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t1, (T*)bc, cfg_.nb, L.ld1, C.g.ld, d1, d2, 1, 1, 0, P, st));
+    }
+    return Status::Ok();
+  }
+
+  Status prolongate_add(int l, const void* ec, void* x, cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    const Lvl& C = lv_[l + 1];
+    TransferParams P = transfer_params(C.g.N);
+    const int nf = L.g.n1, nc = C.g.n1;
+    if (cfg_.dim == 3) {
+      int d3[3] = {nc, nc, nc}, d2[3] = {nc, nc, nf}, d1[3] = {nc, nf, nf}, d0[3] = {nf, nf, nf};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)ec, L.t2, cfg_.nb, C.g.ld, L.ld2, d3, d2, 2, 0, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t2, L.t1, cfg_.nb, L.ld2, L.ld1, d2, d1, 1, 0, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t1, (T*)x, cfg_.nb, L.ld1, L.g.ld, d1, d0, 0, 0, 1, P, st));
+    } else {
+      int d2[3] = {nc, nc, 1}, d1[3] = {nc, nf, 1}, d0[3] = {nf, nf, 1};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)ec, L.t1, cfg_.nb, C.g.ld, L.ld1, d2, d1, 1, 0, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(L.t1, (T*)x, cfg_.nb, L.ld1, L.g.ld, d1, d0, 0, 0, 1, P, st));
+    }
+    return Status::Ok();
+  }
+
+  Status coarse_solve(const void* b, void* x, cudaStream_t st) override {
+    IRK_LAUNCH(PROF_COARSE, launch_coarse_solve<T>((const T*)b, (T*)x, cfg_.nb, lv_.back().g.ld, dAinv_, dmap_, nci_, st));
+    return Status::Ok();
+  }
+
+  Status apply_mass(int l, const void* x, void* y, double scale, cudaStream_t st) override {
+    std::vector<double> cm(cfg_.nb, scale), ck(cfg_.nb, 0.0);
+    EpiParams<T> E;
+    std::memset(&E, 0, sizeof(E));
+    E.out = (T*)y;
+    OpParams<T> P = make_op_params<T>(lv_[l].g, cfg_.nb, cm.data(), ck.data());
+    IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, cfg_.nb, (const T*)x, P, EPI_STORE, E, st));
+    return Status::Ok();
+  }
+
+ private:
+  TransferParams transfer_params(int Nc) const {
+    TransferParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.k = cfg_.k;
+    P.Nc = Nc;
+    for (size_t i = 0; i < el_.Pc.size(); ++i) P.Pc[i] = el_.Pc[i];
+    return P;
+  }
+
+  // operator launch over all blocks (batched) or block by block
+  Status op(int l, const T* u, int epi, const EpiParams<T>& E, cudaStream_t st) {
+    Lvl& L = lv_[l];
+    const int nb = cfg_.nb;
+    if (cfg_.batched) {
+      OpParams<T> P = make_op_params<T>(L.g, nb, cfg_.cm.data(), ck_.data());
+      IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, nb, u, P, epi, E, st));
+      return Status::Ok();
+    }
+    for (int s = 0; s < nb; ++s) {
+      OpParams<T> P = make_op_params<T>(L.g, 1, &cfg_.cm[s], &ck_[s]);
+      EpiParams<T> Es = E;
+      const long long off = (long long)s * L.g.ld;
+      Es.out = E.out ? E.out + off : nullptr;
+      Es.out2 = E.out2 ? E.out2 + off : nullptr;
+      Es.b = E.b ? E.b + off : nullptr;
+      Es.xj = E.xj ? E.xj + off : nullptr;
+      Es.c1[0] = E.c1[s];
+      Es.c2[0] = E.c2[s];
+      IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, 1, u + off, P, epi, Es, st));
+    }
+    return Status::Ok();
+  }
+
+  // degree-m Chebyshev iteration on level l; result in L.cur
+  Status cheb(int l, const T* b, bool from_zero, cudaStream_t st) {
+    Lvl& L = lv_[l];
+    const int nb = cfg_.nb, m = cfg_.cheb_degree;
+    T* cur = from_zero ? L.xa : L.cur;
+    T* oth = (cur == L.xa) ? L.xb : L.xa;
+    int j0 = 0;
+    if (from_zero) {
+      std::vector<double> c(nb);
+      for (int s = 0; s < nb; ++s) c[s] = L.c2[0][s];
+      DiagParams<T> D = make_diag_params<T>(L.g, nb, cfg_.cm.data(), ck_.data(), c.data());
+      IRK_LAUNCH(PROF_MG_POINT, launch_cheb_first<T>(L.g.grid(), nb, b, cur, D, st));
+      j0 = 1;
+    }
+    for (int j = j0; j < m; ++j) {
+      EpiParams<T> E;
+      std::memset(&E, 0, sizeof(E));
+      E.out = oth;
+      E.b = b;
+      E.xj = cur;
+      for (int s = 0; s < nb; ++s) { E.c1[s] = (T)L.c1[j][s]; E.c2[s] = (T)L.c2[j][s]; }
+      for (int r = 0; r < kMaxDeg; ++r) { E.dmr[r] = (T)L.g.dmr[r]; E.dkr[r] = (T)L.g.dkr[r]; }
+      // x_{j-1} is zero only for the second step of a smoothing that started from zero
+      E.xold_zero = (from_zero && j == 1) || j == 0;
+      IRK_TRY(op(l, cur, EPI_CHEB, E, st));
+      std::swap(cur, oth);
+    }
+    L.cur = cur;
+    return Status::Ok();
+  }
+
+  Status setup_coarse() {
+    const Lvl& C = lv_.back();
+    const int dim = cfg_.dim, n1 = C.g.n1, ni = n1 - 2;
+    nci_ = 1;
+    for (int a = 0; a < dim; ++a) nci_ *= ni;
+    if (nci_ < 1) return Status::Err(IRK_EINVAL, "coarsest mesh has no interior node");
+    if (nci_ > 2197) return Status::Err(IRK_EINVAL, "coarsest mesh too large for the dense coarse solve");
+    // 1D assembled interior matrices on the coarsest mesh
+    const int k = cfg_.k, p = k + 1;
+    std::vector<double> M1((size_t)n1 * n1, 0.0), K1((size_t)n1 * n1, 0.0);
+    for (int c = 0; c < C.g.N; ++c)
+      for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) {
+          M1[(size_t)(k * c + i) * n1 + k * c + j] += C.g.me[i][j];
+          K1[(size_t)(k * c + i) * n1 + k * c + j] += C.g.ke[i][j];
+        }
+    std::vector<int> map(nci_);
+    std::vector<int> idx(dim);
+    for (int q = 0; q < nci_; ++q) {
+      int t = q, node = 0, stride = 1;
+      for (int a = 0; a < dim; ++a) {
+        const int ia = t % ni + 1;
+        t /= ni;
+        node += ia * stride;
+        stride *= n1;
+      }
+      map[q] = node;
+    }
+    std::vector<double> Ainv_all((size_t)cfg_.nb * nci_ * nci_);
+    for (int s = 0; s < cfg_.nb; ++s) {
+      std::vector<double> A((size_t)nci_ * nci_);
+      for (int q = 0; q < nci_; ++q)
+        for (int r = 0; r < nci_; ++r) {
+          int tq = q, tr = r;
+          double mprod = 1.0;
+          double mv[3], kv[3];
+          for (int a = 0; a < dim; ++a) {
+            const int iq = tq % ni + 1, ir = tr % ni + 1;
+            tq /= ni; tr /= ni;
+            mv[a] = M1[(size_t)iq * n1 + ir];
+            kv[a] = K1[(size_t)iq * n1 + ir];
+            mprod *= mv[a];
+          }
+          double kterm = 0.0;
+          for (int a = 0; a < dim; ++a) {
+            double t = kv[a];
+            for (int b = 0; b < dim; ++b) if (b != a) t *= mv[b];
+            kterm += t;
+          }
+          A[(size_t)q * nci_ + r] = cfg_.cm[s] * mprod + cfg_.tau * kterm;
+        }
+      if (!spd_inverse(nci_, A)) return Status::Err(IRK_ENUMERIC, "coarse operator not SPD");
+      std::copy(A.begin(), A.end(), Ainv_all.begin() + (size_t)s * nci_ * nci_);
+    }
+    IRK_TRY(arena_.alloc((void**)&dAinv_, Ainv_all.size() * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
+    IRK_CUDA(cudaMemcpy(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpy(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return Status::Ok();
+  }
+
+  // Lanczos on D^{-1/2} A D^{-1/2} (FP64) per level and block -> Chebyshev intervals.
+  Status setup_chebyshev(cudaStream_t st) {
+    const int nb = cfg_.nb;
+    const LevelGeom& g0 = lv_[0].g;
+    const size_t len = (size_t)nb * g0.ld;
+    double *v0, *v1, *w, *t, *red, *partial;
+    IRK_TRY(arena_.alloc((void**)&v0, len * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&v1, len * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&w, len * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&t, len * sizeof(double)));
+    const int nbred = reduction_blocks((long long)g0.ld);
+    IRK_TRY(arena_.alloc((void**)&partial, (size_t)nbred * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&red, 8 * sizeof(double)));
+    const int steps = std::max(2, cfg_.eig_steps);
+    for (int l = 0; l + 1 < levels(); ++l) {
+      Lvl& L = lv_[l];
+      const LevelGeom& g = L.g;
+      const long long n = g.n, ldl = g.ld;
+      // deterministic start vector on interior nodes (hash-based), same for every block
+      std::vector<double> h0((size_t)nb * ldl, 0.0);
+      for (int s = 0; s < nb; ++s)
+        for (long long e = 0; e < n; ++e) {
+          long long x = e % g.n1, y = (e / g.n1) % g.n1, z = (g.dim == 3) ? e / ((long long)g.n1 * g.n1) : 1;
+          bool in = x >= 1 && x <= g.n1 - 2 && y >= 1 && y <= g.n1 - 2 && (g.dim == 2 || (z >= 1 && z <= g.n1 - 2));
+          if (!in) continue;
+          unsigned long long hsh = (unsigned long long)(e + 1) * 0x9E3779B97F4A7C15ULL;
+          hsh ^= hsh >> 29; hsh *= 0xBF58476D1CE4E5B9ULL; hsh ^= hsh >> 32;
+          h0[(size_t)s * ldl + e] = 0.5 + (double)(hsh >> 11) * (1.0 / 9007199254740992.0);
+        }
+      IRK_CUDA(cudaMemcpyAsync(v1, h0.data(), h0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      IRK_CUDA(cudaMemsetAsync(v0, 0, (size_t)nb * ldl * sizeof(double), st));
+      std::vector<std::vector<double>> alpha(nb), beta(nb);
+      std::vector<double> bprev(nb, 0.0);
+      // normalise
+      auto dot = [&](const double* a, const double* b, int s, double& out) -> Status {
+        IRK_CUDA(launch_multidot(a + (size_t)s * ldl, 0, 1, b + (size_t)s * ldl, n, partial, nbred, st));
+        IRK_CUDA(launch_reduce_partials(partial, 1, nbred, red, st));
+        IRK_CUDA(cudaMemcpyAsync(&out, red, sizeof(double), cudaMemcpyDeviceToHost, st));
+        IRK_CUDA(cudaStreamSynchronize(st));
+        return Status::Ok();
+      };
+      for (int s = 0; s < nb; ++s) {
+        double nn;
+        IRK_TRY(dot(v1, v1, s, nn));
+        IRK_CUDA(launch_scale(v1 + (size_t)s * ldl, 1.0 / std::sqrt(nn), v1 + (size_t)s * ldl, n, st));
+      }
+      std::vector<double> one(nb, 1.0);
+      DiagParams<double> D = make_diag_params<double>(g, nb, cfg_.cm.data(), ck_.data(), one.data());
+      OpParams<double> P = make_op_params<double>(g, nb, cfg_.cm.data(), ck_.data());
+      EpiParams<double> E;
+      std::memset(&E, 0, sizeof(E));
+      E.out = w;
+      std::vector<bool> done(nb, false);
+      for (int it = 0; it < steps; ++it) {
+        IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, v1, t, D, 1, st));
+        IRK_CUDA(launch_op<double>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
+        IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, w, w, D, 1, st));
+        for (int s = 0; s < nb; ++s) {
+          if (done[s]) continue;
+          double a;
+          IRK_TRY(dot(w, v1, s, a));
+          alpha[s].push_back(a);
+          double* ws = w + (size_t)s * ldl;
+          // w -= a v1 + bprev v0
+          double coef[2] = {a, bprev[s]};
+          double* dcoef = red + 2;
+          IRK_CUDA(cudaMemcpyAsync(dcoef, coef, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+          IRK_CUDA(launch_multi_axpy(v1 + (size_t)s * ldl, 0, 1, dcoef, -1.0, ws, n, st));
+          IRK_CUDA(launch_multi_axpy(v0 + (size_t)s * ldl, 0, 1, dcoef + 1, -1.0, ws, n, st));
+          double bb;
+          IRK_TRY(dot(w, w, s, bb));
+          const double bn = std::sqrt(std::max(bb, 0.0));
+          if (bn < 1e-12 * std::fabs(a) || it + 1 == steps) {
+            done[s] = true;
+            continue;
+          }
+          beta[s].push_back(bn);
+          bprev[s] = bn;
+          IRK_CUDA(cudaMemcpyAsync(v0 + (size_t)s * ldl, v1 + (size_t)s * ldl, n * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+          IRK_CUDA(launch_scale(ws, 1.0 / bn, v1 + (size_t)s * ldl, n, st));
+        }
+      }
+      L.lo.resize(nb);
+      L.hi.resize(nb);
+      for (int s = 0; s < nb; ++s) {
+        std::vector<double> b2(beta[s].begin(), beta[s].end());
+        b2.resize(alpha[s].size() > 0 ? alpha[s].size() - 1 : 0);
+        const double lmax = tridiag_max_eig(alpha[s], b2);
+        L.hi[s] = cfg_.eig_safety * lmax;
+        L.lo[s] = L.hi[s] / cfg_.smoothing_range;
+      }
+      if (cfg_.shared_cheb) {
+        const double hmax = *std::max_element(L.hi.begin(), L.hi.end());
+        for (int s = 0; s < nb; ++s) { L.hi[s] = hmax; L.lo[s] = hmax / cfg_.smoothing_range; }
+      }
+      // coefficients of the three-term recurrence
+      const int m = cfg_.cheb_degree;
+      L.c1.assign(m, std::vector<double>(nb, 0.0));
+      L.c2.assign(m, std::vector<double>(nb, 0.0));
+      for (int s = 0; s < nb; ++s) {
+        const double theta = 0.5 * (L.hi[s] + L.lo[s]), delta = 0.5 * (L.hi[s] - L.lo[s]);
+        double rho = delta / theta;
+        L.c1[0][s] = 0.0;
+        L.c2[0][s] = 1.0 / theta;
+        for (int j = 1; j < m; ++j) {
+          const double rn = 1.0 / (2.0 * theta / delta - rho);
+          L.c1[j][s] = rn * rho;
+          L.c2[j][s] = 2.0 * rn / delta;
+          rho = rn;
+        }
+      }
+    }
+    IRK_CUDA(cudaStreamSynchronize(st));
+    return Status::Ok();
+  }
+
+  MGConfig cfg_;
+  Element1D el_;
+  DeviceArena& arena_;
+  std::vector<Lvl> lv_;
+  std::vector<double> ck_;
+  double* dAinv_ = nullptr;
+  int* dmap_ = nullptr;
+  int nci_ = 0;
+};
+
+}  // namespace
+
+Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,
+               std::unique_ptr<MGBase>& out) {
+  if (cfg.precision == 64) {
+    auto mg = std::make_unique<MG<double>>(cfg, e, arena);
+    IRK_TRY(mg->setup(st));
+    out = std::move(mg);
+  } else {
+    auto mg = std::make_unique<MG<float>>(cfg, e, arena);
+    IRK_TRY(mg->setup(st));
+    out = std::move(mg);
+  }
+  return Status::Ok();
+}
+
+}  // namespace irk

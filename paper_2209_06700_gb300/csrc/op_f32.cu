@@ -1,0 +1,19 @@
+// FP32 operator launches (multigrid level operators, Chebyshev smoother, residual).
+#include "op_kernels.cuh"
+
+namespace irk {
+
+void op_tile_shape(int dim, int k, int* cx, int* cy) { op_tile_shape_impl(dim, k, cx, cy); }
+
+template <>
+cudaError_t launch_op<float>(int dim, int k, int nstage, const float* u, const OpParams<float>& P, int epi,
+                             const EpiParams<float>& E, cudaStream_t st) {
+  switch (epi) {
+    case EPI_STORE: return launch_op_e<float, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_RESID: return launch_op_e<float, EPI_RESID>(dim, k, nstage, u, P, E, st);
+    case EPI_CHEB: return launch_op_e<float, EPI_CHEB>(dim, k, nstage, u, P, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace irk

@@ -1,0 +1,126 @@
+// Host solver of libirk: multigrid hierarchy, FGMRES, IRK step (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "host_math.h"
+#include "irk.h"
+#include "kernels.h"
+
+namespace irk {
+
+struct Status {
+  irk_status code = IRK_OK;
+  std::string msg;
+  bool ok() const { return code == IRK_OK; }
+  static Status Ok() { return Status(); }
+  static Status Err(irk_status c, std::string m) { Status s; s.code = c; s.msg = std::move(m); return s; }
+};
+
+#define IRK_CUDA(...)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (__VA_ARGS__);                                                              \
+    if (e_ != cudaSuccess)                                                                       \
+      return ::irk::Status::Err(IRK_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define IRK_TRY(...)                   \
+  do {                                 \
+    ::irk::Status s_ = (__VA_ARGS__);  \
+    if (!s_.ok()) return s_;           \
+  } while (0)
+
+// Device allocation owned by the handle (freed in reverse order).
+class DeviceArena {
+ public:
+  ~DeviceArena();
+  Status alloc(void** p, size_t bytes);  // zero-initialised
+  size_t bytes() const { return total_; }
+ private:
+  std::vector<void*> ptrs_;
+  size_t total_ = 0;
+};
+
+long long round_ld(long long n);
+
+// One mesh level of the hierarchy.
+struct LevelGeom {
+  int dim, k, N, n1;
+  long long n, ld;
+  double h;
+  double me[kMaxDeg + 1][kMaxDeg + 1], ke[kMaxDeg + 1][kMaxDeg + 1];
+  double dmr[kMaxDeg], dkr[kMaxDeg];
+  GridInfo grid() const { return GridInfo{dim, k, N, n1, n, ld}; }
+};
+
+LevelGeom make_level(int dim, int k, int N, const Element1D& e);
+int choose_zc(int dim, int k, int N, int nstage);
+
+template <typename T>
+OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, const double* ck);
+template <typename T>
+DiagParams<T> make_diag_params(const LevelGeom& g, int nstage, const double* cm, const double* ck, const double* c);
+
+// Geometric multigrid for nb independent blocks (cm_i M + tau K), element type T.
+class MGBase {
+ public:
+  virtual ~MGBase() = default;
+  virtual int levels() const = 0;
+  virtual int elem_size() const = 0;
+  // finest-level rhs / solution buffers ([nb][ld0], element type T)
+  virtual void* fine_b() = 0;
+  virtual void* fine_x() = 0;          // result of the last vcycle on level 0
+  virtual Status vcycle(int level, cudaStream_t st) = 0;  // b_level -> x_level
+  virtual Status vcycle_io(int level, const void* b, void* x, cudaStream_t st) = 0;
+  virtual Status smooth(int level, const void* b, void* x, int x_is_zero, cudaStream_t st) = 0;
+  virtual Status residual(int level, const void* b, const void* x, void* r, cudaStream_t st) = 0;
+  virtual Status restrict_to(int level, const void* r, void* bc, cudaStream_t st) = 0;
+  virtual Status prolongate_add(int level, const void* ec, void* x, cudaStream_t st) = 0;
+  virtual Status coarse_solve(const void* b, void* x, cudaStream_t st) = 0;
+  virtual Status apply_mass(int level, const void* x, void* y, double scale, cudaStream_t st) = 0;
+  virtual const LevelGeom& geom(int level) const = 0;
+  virtual void interval(int level, int block, double* lo, double* hi) const = 0;
+};
+
+struct MGConfig {
+  int dim, k, N;
+  int nb;                    // blocks
+  std::vector<double> cm;    // per-block mass coefficient lambda_i
+  double tau;
+  int cheb_degree;
+  int eig_steps;
+  double smoothing_range, eig_safety;
+  int shared_cheb;
+  int batched;
+  int precision;             // 32 or 64
+};
+
+Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,
+               std::unique_ptr<MGBase>& out);
+
+// Right-preconditioned flexible GMRES (FP64) on ns stage vectors of stride ld.
+struct FGMRESWork {
+  int ns = 0, m = 0;
+  long long ld = 0, len = 0;  // len = ns * ld
+  double* V = nullptr;        // (m+1) x len
+  double* Z = nullptr;        // m x len
+  double* tmp = nullptr;      // len (restart residual)
+  double* partial = nullptr;  // 64 x nb
+  double* dvals = nullptr;    // device scalars: h1[64], h2[64], nrm, y[64]
+  double* hvals = nullptr;    // pinned host mirror
+  int nb = 0;
+};
+
+Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena);
+
+struct FGMRESResult { int iterations = 0; double rel_residual = 0; bool converged = false; };
+
+using ApplyFn = std::function<Status(const double* in, double* out)>;
+
+Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const double* b, double* x,
+                    double rtol, int max_it, cudaStream_t st, FGMRESResult& res);
+
+}  // namespace irk

@@ -1,0 +1,435 @@
+// Pointwise, reduction, transfer and coarse-solve kernels of libirk (sm_103a).
+//
+// * Stage combination v_i = sum_j D_ij u_j: the "generalized matrix-vector
+//   product" (D (x) I) u of arXiv 2209.06700, Sec. 2, used for A^{-1}, S~^{-1},
+//   S~ (Eq. irk:A, irk:P) and T, T^{-1} (Eq. irk:Ainv, real form).  On one GPU
+//   all stages of a node sit in the same memory, so the combination is an
+//   elementwise kernel reading the Q stage values of each node.
+// * Stage right-hand side and solution update (Sec. 1 and Sec. 2).
+// * Deterministic reductions for FGMRES (fixed block counts, fixed order).
+// * Intergrid transfer: the Q_k embedding P = P1 (x) P1 (x) P1 and its transpose,
+//   applied one axis at a time.
+// * Dense coarse-grid solve with a precomputed FP64 inverse.
+#include "kernels.h"
+
+namespace irk {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long n, int per_thread = 1) {
+  long long b = (n + (long long)kThreads * per_thread - 1) / ((long long)kThreads * per_thread);
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+__device__ __forceinline__ void coords(long long idx, int dim, int n1, int& x, int& y, int& z) {
+  x = (int)(idx % n1);
+  long long r = idx / n1;
+  y = (int)(r % n1);
+  z = (dim == 3) ? (int)(r / n1) : 0;
+}
+
+__device__ __forceinline__ bool interior(int dim, int n1, int x, int y, int z) {
+  bool ok = x >= 1 && x <= n1 - 2 && y >= 1 && y <= n1 - 2;
+  if (dim == 3) ok = ok && z >= 1 && z <= n1 - 2;
+  return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_at(const DiagParams<T>& D, int s, int dim, int k, int x, int y, int z) {
+  const int rx = x % k, ry = y % k;
+  T dmx = D.dmr[rx], dmy = D.dmr[ry], dkx = D.dkr[rx], dky = D.dkr[ry];
+  if (dim == 3) {
+    const int rz = z % k;
+    T dmz = D.dmr[rz], dkz = D.dkr[rz];
+    return D.cm[s] * (dmx * dmy * dmz) + D.ck[s] * (dkx * dmy * dmz + dmx * dky * dmz + dmx * dmy * dkz);
+  }
+  return D.cm[s] * (dmx * dmy) + D.ck[s] * (dkx * dmy + dmx * dky);
+}
+
+// ------------------------------------------------------------ stage combination
+template <typename Tin, typename Tout>
+__global__ void combine_kernel(const Tin* __restrict__ a, const double* __restrict__ b, Tout* __restrict__ out,
+                               long long n, long long ld, const CombineParams C) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double av[kMaxQ], bv[kMaxQ];
+#pragma unroll
+    for (int j = 0; j < kMaxQ; ++j) {
+      av[j] = (j < C.nina) ? (double)a[j * ld + e] : 0.0;
+      bv[j] = (j < C.ninb) ? b[j * ld + e] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxQ; ++i) {
+      if (i >= C.nout) break;
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxQ; ++j) {
+        if (j < C.nina) acc += C.Da[i * kMaxQ + j] * av[j];
+        if (j < C.ninb) acc += C.Db[i * kMaxQ + j] * bv[j];
+      }
+      out[i * ld + e] = (Tout)acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------ Chebyshev start, diag scaling
+template <typename T>
+__global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
+  const int s = blockIdx.y;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
+    const long long o = s * g.ld + e;
+    x[o] = D.c[s] * b[o] / diag_at(D, s, g.dim, g.k, ix, iy, iz);
+  }
+}
+
+template <typename T>
+__global__ void diag_scale_kernel(GridInfo g, const T* __restrict__ x, T* __restrict__ out, const DiagParams<T> D,
+                                  int inv_sqrt) {
+  const int s = blockIdx.y;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
+    const long long o = s * g.ld + e;
+    const T d = diag_at(D, s, g.dim, g.k, ix, iy, iz);
+    out[o] = inv_sqrt ? x[o] / sqrt(d) : x[o] * d;
+  }
+}
+
+// ------------------------------------------------------------ RHS, update, interpolation
+__global__ void stage_rhs_kernel(GridInfo g, const RhsParams R, const double* __restrict__ Ky,
+                                 const double* __restrict__ G1, const double* __restrict__ loads,
+                                 double* __restrict__ rhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
+    const double ky = Ky[e];
+    double G = G1[ix] * G1[iy];
+    if (g.dim == 3) G *= G1[iz];
+    double f[kMaxQ];
+#pragma unroll
+    for (int j = 0; j < kMaxQ; ++j)
+      if (j < R.Q) f[j] = (loads ? loads[j * g.ld + e] : R.phi[j] * G) - ky;
+#pragma unroll
+    for (int i = 0; i < kMaxQ; ++i) {
+      if (i >= R.Q) break;
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxQ; ++j)
+        if (j < R.Q) acc += R.Ainv[i * kMaxQ + j] * f[j];
+      rhs[i * g.ld + e] = acc;
+    }
+  }
+}
+
+struct UpdateParams { int Q; double bw[kMaxQ]; double tau; };
+
+__global__ void update_kernel(GridInfo g, const UpdateParams U, const double* __restrict__ kst, double* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < U.Q; ++i) acc += U.bw[i] * kst[i * g.ld + e];
+    y[e] += U.tau * acc;
+  }
+}
+
+__global__ void interpolate_kernel(GridInfo g, const double* __restrict__ x1d, double ct, double* __restrict__ y) {
+  const double pi = 3.14159265358979323846;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    if (!interior(g.dim, g.n1, ix, iy, iz)) { y[e] = 0.0; continue; }
+    double v = sin(pi * x1d[ix]) * sin(pi * x1d[iy]);
+    if (g.dim == 3) v *= sin(pi * x1d[iz]);
+    y[e] = v * ct;
+  }
+}
+
+// ------------------------------------------------------------ reductions
+template <int G>
+__global__ void multidot_kernel(const double* __restrict__ V, long long vstride, int nv, const double* __restrict__ w,
+                                long long n, double* __restrict__ partial, int nb) {
+  const int i0 = blockIdx.y * G;
+  double acc[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) acc[g] = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double we = w[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (i0 + g < nv) acc[g] += V[(i0 + g) * vstride + e] * we;
+  }
+  __shared__ double red[G][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    double v = acc[g];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[g][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < G && i0 + (int)threadIdx.x < nv) {
+    double v = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) v += red[threadIdx.x][q];
+    partial[(long long)(i0 + threadIdx.x) * nb + blockIdx.x] = v;
+  }
+}
+
+__global__ void norm2_kernel(const double* __restrict__ w, long long n, double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = w[e];
+    acc += v * v;
+  }
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) v += red[q];
+    partial[blockIdx.x] = v;
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out,
+                                       int take_sqrt) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[(long long)i * nb + b];
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) v += red[q];
+    out[i] = take_sqrt ? sqrt(v) : v;
+  }
+}
+
+__global__ void multi_axpy_kernel(const double* __restrict__ V, long long vstride, int nv, const double* __restrict__ h,
+                                  double sign, double* __restrict__ w, long long n) {
+  __shared__ double hs[64];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = sign * h[i];
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < nv; ++i) acc += hs[i] * V[i * vstride + e];
+    w[e] = acc;
+  }
+}
+
+__global__ void scale_inv_kernel(const double* __restrict__ w, const double* __restrict__ nrm, double* __restrict__ out,
+                                 long long n) {
+  const double f = 1.0 / nrm[0];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = w[e] * f;
+}
+
+__global__ void scale_kernel(const double* __restrict__ x, double a, double* __restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = a * x[e];
+}
+
+// ------------------------------------------------------------ transfers
+template <typename T>
+__global__ void transfer_axis_kernel(const T* __restrict__ in, T* __restrict__ out, long long ld_in, long long ld_out,
+                                     int din0, int din1, int din2, int dout0, int dout1, int dout2, int axis,
+                                     int restrict_mode, int accumulate, const TransferParams P) {
+  const int s = blockIdx.y;
+  const long long nout = (long long)dout0 * dout1 * dout2;
+  const int k = P.k, Nc = P.Nc, p = k + 1;
+  const long long sin_[3] = {1, (long long)din0, (long long)din0 * din1};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nout; e += (long long)gridDim.x * blockDim.x) {
+    int o[3];
+    o[0] = (int)(e % dout0);
+    o[1] = (int)((e / dout0) % dout1);
+    o[2] = (int)(e / ((long long)dout0 * dout1));
+    const int ca = o[axis];
+    long long base = 0;
+    for (int a = 0; a < 3; ++a)
+      if (a != axis) base += o[a] * sin_[a];
+    const T* src = in + s * ld_in + base;
+    const long long st = sin_[axis];
+    double acc = 0.0;
+    if (restrict_mode) {
+      // coarse index ca = k*cc + i; fine nodes of coarse cell cc are 2k*cc + m, m = 0..2k
+      const int ndc = (axis == 0) ? dout0 : (axis == 1) ? dout1 : dout2;
+      if (ca == 0 || ca == ndc - 1) continue;  // coarse boundary stays zero
+      const int cc = ca / k, i = ca - cc * k;
+      if (i != 0) {
+        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + i] * (double)src[(long long)(2 * k * cc + m) * st];
+      } else {
+        for (int m = 0; m < 2 * k; ++m) acc += P.Pc[m * p + k] * (double)src[(long long)(2 * k * (cc - 1) + m) * st];
+        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + 0] * (double)src[(long long)(2 * k * cc + m) * st];
+      }
+    } else {
+      int cc = ca / (2 * k);
+      if (cc > Nc - 1) cc = Nc - 1;
+      const int m = ca - 2 * k * cc;
+      for (int i = 0; i <= k; ++i) acc += P.Pc[m * p + i] * (double)src[(long long)(k * cc + i) * st];
+    }
+    T* dst = out + s * ld_out + e;
+    if (accumulate) *dst = (T)((double)*dst + acc);
+    else *dst = (T)acc;
+  }
+}
+
+// ------------------------------------------------------------ coarse solve
+template <typename T>
+__global__ void coarse_solve_kernel(const T* __restrict__ b, T* __restrict__ x, long long ld,
+                                    const double* __restrict__ Ainv, const int* __restrict__ map, int nci) {
+  extern __shared__ double sb[];
+  const int s = blockIdx.x;
+  for (int i = threadIdx.x; i < nci; i += blockDim.x) sb[i] = (double)b[s * ld + map[i]];
+  __syncthreads();
+  const double* A = Ainv + (long long)s * nci * nci;
+  for (int r = threadIdx.x; r < nci; r += blockDim.x) {
+    double acc = 0.0;
+    for (int c = 0; c < nci; ++c) acc += A[(long long)r * nci + c] * sb[c];
+    x[s * ld + map[r]] = (T)acc;
+  }
+}
+
+}  // namespace
+
+// ============================================================ launchers
+template <typename Tin, typename Tout>
+cudaError_t launch_combine(const Tin* a, const double* b, Tout* out, long long n, long long ld, const CombineParams& C,
+                           cudaStream_t st) {
+  combine_kernel<Tin, Tout><<<blocks_for(n, 2), kThreads, 0, st>>>(a, b, out, n, ld, C);
+  return cudaGetLastError();
+}
+template cudaError_t launch_combine<double, double>(const double*, const double*, double*, long long, long long,
+                                                    const CombineParams&, cudaStream_t);
+template cudaError_t launch_combine<double, float>(const double*, const double*, float*, long long, long long,
+                                                   const CombineParams&, cudaStream_t);
+template cudaError_t launch_combine<float, double>(const float*, const double*, double*, long long, long long,
+                                                   const CombineParams&, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, const DiagParams<T>& D, cudaStream_t st) {
+  dim3 grid(blocks_for(g.n, 2), nstage);
+  cheb_first_kernel<T><<<grid, kThreads, 0, st>>>(g, b, x, D);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_first<float>(const GridInfo&, int, const float*, float*, const DiagParams<float>&,
+                                              cudaStream_t);
+template cudaError_t launch_cheb_first<double>(const GridInfo&, int, const double*, double*, const DiagParams<double>&,
+                                               cudaStream_t);
+
+template <typename T>
+cudaError_t launch_diag_scale(const GridInfo& g, int nstage, const T* x, T* out, const DiagParams<T>& D, int inv_sqrt,
+                              cudaStream_t st) {
+  dim3 grid(blocks_for(g.n, 2), nstage);
+  diag_scale_kernel<T><<<grid, kThreads, 0, st>>>(g, x, out, D, inv_sqrt);
+  return cudaGetLastError();
+}
+template cudaError_t launch_diag_scale<float>(const GridInfo&, int, const float*, float*, const DiagParams<float>&, int,
+                                              cudaStream_t);
+template cudaError_t launch_diag_scale<double>(const GridInfo&, int, const double*, double*, const DiagParams<double>&,
+                                               int, cudaStream_t);
+
+cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const double* Ky, const double* G1,
+                             const double* loads, double* rhs, cudaStream_t st) {
+  stage_rhs_kernel<<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, R, Ky, G1, loads, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const GridInfo& g, int Q, const double* kst, const double* bw, double tau, double* y,
+                          cudaStream_t st) {
+  UpdateParams U;
+  U.Q = Q;
+  for (int i = 0; i < kMaxQ; ++i) U.bw[i] = (i < Q) ? bw[i] : 0.0;
+  U.tau = tau;
+  update_kernel<<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, U, kst, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const GridInfo& g, const double* x1d, double ct, double* y, cudaStream_t st) {
+  interpolate_kernel<<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, x1d, ct, y);
+  return cudaGetLastError();
+}
+
+int reduction_blocks(long long n) { return blocks_for(n, 8); }
+
+cudaError_t launch_multidot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
+                            int nb, cudaStream_t st) {
+  dim3 grid(nb, (nv + 7) / 8);
+  multidot_kernel<8><<<grid, kThreads, 0, st>>>(V, vstride, nv, w, n, partial, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double* out, cudaStream_t st,
+                                   int take_sqrt) {
+  reduce_partials_kernel<<<nv, kThreads, 0, st>>>(partial, nb, out, take_sqrt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm2_partial(const double* w, long long n, double* partial, int nb, cudaStream_t st) {
+  norm2_kernel<<<nb, kThreads, 0, st>>>(w, n, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi_axpy(const double* V, long long vstride, int nv, const double* h, double sign, double* w,
+                              long long n, cudaStream_t st) {
+  if (nv > 64) return cudaErrorInvalidValue;
+  multi_axpy_kernel<<<blocks_for(n, 2), kThreads, 0, st>>>(V, vstride, nv, h, sign, w, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_inv(const double* w, const double* nrm, double* out, long long n, cudaStream_t st) {
+  scale_inv_kernel<<<blocks_for(n, 2), kThreads, 0, st>>>(w, nrm, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const double* x, double a, double* out, long long n, cudaStream_t st) {
+  scale_kernel<<<blocks_for(n, 2), kThreads, 0, st>>>(x, a, out, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_in, long long ld_out, const int din[3],
+                                 const int dout[3], int axis, int restrict_mode, int accumulate,
+                                 const TransferParams& P, cudaStream_t st) {
+  const long long nout = (long long)dout[0] * dout[1] * dout[2];
+  dim3 grid(blocks_for(nout, 2), nstage);
+  transfer_axis_kernel<T><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], din[2], dout[0], dout[1],
+                                                     dout[2], axis, restrict_mode, accumulate, P);
+  return cudaGetLastError();
+}
+template cudaError_t launch_transfer_axis<float>(const float*, float*, int, long long, long long, const int[3],
+                                                 const int[3], int, int, int, const TransferParams&, cudaStream_t);
+template cudaError_t launch_transfer_axis<double>(const double*, double*, int, long long, long long, const int[3],
+                                                  const int[3], int, int, int, const TransferParams&, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_coarse_solve(const T* b, T* x, int nstage, long long ld, const double* Ainv, const int* map, int nci,
+                                cudaStream_t st) {
+  const size_t smem = (size_t)nci * sizeof(double);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(coarse_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  coarse_solve_kernel<T><<<nstage, kThreads, smem, st>>>(b, x, ld, Ainv, map, nci);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coarse_solve<float>(const float*, float*, int, long long, const double*, const int*, int,
+                                                cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(const double*, double*, int, long long, const double*, const int*, int,
+                                                 cudaStream_t);
+
+}  // namespace irk

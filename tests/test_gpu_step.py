@@ -1,0 +1,142 @@
+"""Parity of the whole Radau IIA step with the oracle's exact IRK step.
+
+The oracle solves the stage system exactly (per-mode fast diagonalisation,
+itself pinned to a sparse direct Kronecker solve); the GPU path solves it with
+FP64 FGMRES to rtol 1e-10, preconditioned by Eq. (irk:P) with FP32 (default)
+or FP64 multigrid, or by the directly diagonalised variant with PRESB.  The
+bar is 1e-9 relative in y_{n+1}.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_06700_gb300 as pkg
+from oracle.irk import FastDiag, Problem, step_fastdiag
+from oracle.tableau import lu_preconditioner_factors, real_jordan
+from synthetic import HEAT2D_K2_N16_Q2, HEAT3D_K4_N32_Q3, uniform_vectors, zero_boundary
+from tests.gpu_util import from_dev, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+YTOL = 1e-9
+
+
+@pytest.mark.parametrize("Q", [1, 2, 3, 4, 5, 9])
+def test_tableau_matches_oracle(Q):
+    f = lu_preconditioner_factors(Q)
+    with pkg.Solver(2, 4, 1, Q, 0.1) as s:
+        for name in ("A", "b", "c", "Ainv", "L", "U", "S", "Sinv", "lam"):
+            ref = f[name]
+            got = s.tableau(name)
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), name
+        if Q >= 2:
+            T, J, Tinv = s.tableau("T"), s.tableau("J"), s.tableau("Tinv")
+            np.testing.assert_allclose(T @ J @ Tinv, f["Ainv"], atol=1e-11 * np.abs(f["Ainv"]).max())
+            _, _, blocks = real_jordan(f["Ainv"])
+            diag = [b[1] for b in blocks]
+            got_diag = [J[i, i] for i in range(Q)]
+            for v in diag:
+                assert min(abs(g - v) for g in got_diag) < 1e-10
+
+
+@pytest.mark.parametrize("dim,N,k,Q", [(2, 16, 2, 2), (3, 6, 3, 3), (3, 9, 2, 4)])
+def test_stage_rhs(dim, N, k, Q):
+    tau = 1e-2
+    prob = Problem(dim, N, k, Q, tau)
+    with pkg.Solver(dim, N, k, Q, tau) as s:
+        n1 = k * N + 1
+        y = zero_boundary(uniform_vectors(n1 ** dim, seed=4), dim, n1)
+        yd = torch.from_numpy(y).cuda()
+        rhs = s.stage_vector()
+        s.stage_rhs(yd, 0.3, rhs)
+        got = from_dev(rhs, s.n)
+    assert rel_err(got, prob.stage_rhs_calA(y, 0.3)) <= 1e-12
+
+
+def test_initial_interpolant():
+    from oracle.heat import initial_value
+    from oracle.fem import Mesh
+    with pkg.Solver(3, 5, 3, 2, 0.1) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        got = y.cpu().numpy()
+    assert rel_err(got, initial_value(Mesh(3, 5, 3))) <= 1e-14
+
+
+def _run(dim, N, k, Q, tau, nsteps=1, **opts):
+    prob = Problem(dim, N, k, Q, tau)
+    fd = FastDiag(prob)
+    yref = prob.y0()
+    with pkg.Solver(dim, N, k, Q, tau, **opts) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        its = []
+        for n in range(nsteps):
+            st = s.step(y, n * tau)
+            its.append(st.iterations)
+            yref = step_fastdiag(prob, yref, n * tau, fd)
+        got = y.cpu().numpy()
+    return rel_err(got, yref), its
+
+
+def test_heat2d_k2_n16_q2_ten_steps():
+    w = HEAT2D_K2_N16_Q2
+    err, its = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=w.steps)
+    assert err <= YTOL, (err, its)
+
+
+@pytest.mark.parametrize("dim,N,k,Q,tau", [(3, 8, 2, 3, 1e-3), (3, 6, 4, 2, 1e-2), (3, 12, 2, 3, 1e-3),
+                                           (3, 16, 1, 5, 1e-3), (2, 32, 3, 4, 1e-3), (3, 10, 3, 2, 0.1)])
+def test_step_lu_fp32_mg(dim, N, k, Q, tau):
+    err, its = _run(dim, N, k, Q, tau, nsteps=2)
+    assert err <= YTOL, (err, its)
+
+
+@pytest.mark.parametrize("opts", [dict(mg_precision=64), dict(batched=0), dict(mg_precision=64, batched=0),
+                                  dict(shared_cheb=1), dict(cheb_degree=5)])
+def test_step_variants_of_the_lu_path(opts):
+    err, its = _run(3, 8, 3, 3, 1e-3, nsteps=2, **opts)
+    assert err <= YTOL, (err, its, opts)
+
+
+@pytest.mark.parametrize("dim,N,k,Q,tau", [(3, 8, 2, 2, 1e-3), (3, 8, 2, 3, 1e-3), (2, 16, 3, 4, 1e-2),
+                                           (3, 6, 3, 5, 1e-3)])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_step_diag_presb(dim, N, k, Q, tau, prec):
+    err, its = _run(dim, N, k, Q, tau, nsteps=2, variant=pkg.IRK_VARIANT_DIAG, mg_precision=prec)
+    assert err <= YTOL, (err, its)
+
+
+def test_iteration_counts_mesh_independent():
+    counts = []
+    for N in (8, 16, 32):
+        _, its = _run(3, N, 2, 3, 1e-2, nsteps=1)
+        counts.append(its[0])
+    assert max(counts) - min(counts) <= 3, counts
+
+
+def test_not_converged_leaves_y_unchanged():
+    with pkg.Solver(3, 8, 2, 3, 1e-2, max_it=1) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        y0 = y.clone()
+        with pytest.raises(pkg.IrkError) as ei:
+            s.step(y, 0.0)
+        assert ei.value.code == -3
+        assert torch.equal(y, y0)
+
+
+def test_invalid_arguments():
+    with pytest.raises(pkg.IrkError):
+        pkg.Solver(3, 8, 5, 3, 1e-2)
+    with pytest.raises(pkg.IrkError):
+        pkg.Solver(3, 8, 2, 3, -1.0)
+    with pytest.raises(pkg.IrkError):
+        pkg.Solver(3, 8, 2, 1, 1e-2, variant=pkg.IRK_VARIANT_DIAG)
+
+
+@pytest.mark.slow
+def test_full_size_heat3d_k4_n32_q3_one_step():
+    w = HEAT3D_K4_N32_Q3
+    err, its = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=1)
+    assert err <= YTOL, (err, its)

@@ -18,7 +18,8 @@ Sources in arXiv 2209.06700:
 * Sec. 2, Eq. (irk:P): A_Q^{-1} = L U with U unit-diagonal (Axelsson and
   Neytcheva); L = S~ Lambda~ S~^{-1} is real.  ``crout_lu`` and
   ``lu_preconditioner_factors``.  Readings: no pivoting (Crout); S~ is
-  scaled to unit diagonal and ordered like diag(L).
+  scaled to unit diagonal and ordered like diag(L), so S~ is unit lower
+  triangular and S~^{-1} is its forward-substitution inverse.
 
 Pinned by tests/test_oracle_tableau.py: closed-form Q=2 and Q=3 tableaux,
 the simplifying conditions B(2Q) / C(Q), the Q=2 stability function at a
@@ -148,13 +149,24 @@ def lower_triangular_eigvecs(L):
     return S
 
 
+def unit_lower_inverse(S):
+    """Inverse of a unit lower-triangular matrix by forward substitution (column by column)."""
+    n = S.shape[0]
+    X = np.zeros((n, n))
+    for j in range(n):
+        X[j, j] = 1.0
+        for i in range(j + 1, n):
+            X[i, j] = -sum(S[i, l] * X[l, j] for l in range(j, i))
+    return X
+
+
 def lu_preconditioner_factors(Q):
     """Factors of Eq. (irk:P): returns dict with A, b, c, Ainv, L, U, lam (=diag L), S, Sinv."""
     A, b, c = radau_iia(Q)
     Ainv = np.linalg.inv(A)
     L, U = crout_lu(Ainv)
     S = lower_triangular_eigvecs(L)
-    Sinv = np.linalg.inv(S)
+    Sinv = unit_lower_inverse(S)
     return dict(A=A, b=b, c=c, Ainv=Ainv, L=L, U=U, lam=np.diag(L).copy(), S=S, Sinv=Sinv)
 
 

@@ -144,3 +144,14 @@ def test_q3_real_jordan_values():
     pair = roots[roots.imag > 1e-12][0]
     assert abs(blocks[0][1] - gamma) < 1e-12
     assert abs(blocks[1][1] - pair.real) < 1e-12 and abs(blocks[1][2] - pair.imag) < 1e-12
+
+
+@pytest.mark.parametrize("Q", [3, 6, 9])
+def test_sinv_against_extended_precision(Q):
+    """S~^{-1} by forward substitution is accurate even at cond(S~) ~ 5e9 (Q = 9)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    f = lu_preconditioner_factors(Q)
+    hp = np.array((mpmath.matrix(f["S"].tolist()) ** -1).tolist(), dtype=float)
+    assert np.abs(f["Sinv"] - hp).max() <= 1e-13 * np.abs(hp).max()
+    assert np.all(np.triu(f["Sinv"], 1) == 0.0)

@@ -30,7 +30,6 @@ from synthetic import HEAT3D_K4_N32_Q3, HEAT2D_K2_N16_Q2, HEAT3D_K2_N48_Q3, heat
 WORKLOADS = {w.name: w for w in (HEAT3D_K4_N32_Q3, HEAT2D_K2_N16_Q2, HEAT3D_K2_N48_Q3, heat3d_k3_n64(3))}
 METRIC = "stage-DoF updates/s per IRK step at 1e-10 residual"
 UNIT = "stage-DoF/s"
-PROF_NAMES = ["apply64", "mg_op", "mg_point", "transfer", "coarse", "combine", "krylov", "rhs"]
 
 
 def peaks():
@@ -197,6 +196,7 @@ def main():
 
     import paper_2209_06700_gb300 as pkg
     from paper_2209_06700_gb300 import _capi
+    PROF_NAMES = _capi.PROF_CATEGORIES
 
     stream = torch.cuda.Stream()
     variant = pkg.IRK_VARIANT_DIAG if args.variant == "diag" else pkg.IRK_VARIANT_LU
@@ -291,12 +291,20 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "op3d_kernel<double,4,EPI_DUAL>",
                 "peak_source": "nominal FP64 rate of the profiling recipe", "avg_launch_ms": avg_ms}
-    else:
-        # HBM-bound categories: algorithmic bytes of one launch (read input, b, x_{j-1}; write x_{j+1}): 16 B
-        bytes_ = 16.0 * w.n_interior * n_st
+    elif dom_name == "mg_op_fine":
+        # finest-level smoother/residual launches per V-cycle: (2m-1) Chebyshev steps reading
+        # x_j, x_{j-1}, b and writing x_{j+1} (16 B/node/block in FP32) and one residual (12 B)
+        m = w.cheb_degree
+        eb = 4 if args.mg_precision == 32 else 8
+        per_node = ((2 * m - 1) * 4 * eb + 3 * eb) / (2 * m)
+        bytes_ = per_node * w.n_interior * n_st
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": dom_name, "peak_source": hbm_src, "avg_launch_ms": avg_ms}
+                "traffic": None, "kernel": f"op3d_kernel<{'float' if eb == 4 else 'double'},{w.degree},CHEB/RESID>",
+                "peak_source": hbm_src, "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
+                "kernel": dom_name, "peak_source": hbm_src, "avg_launch_ms": avg_ms}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -91,7 +91,8 @@ void irk_default_options(irk_options* opt);
 /* Create a solver for the heat problem on `mesh` with degree k (1..4), Q stages
  * (1..9; DIAG variant 2..9) and step tau > 0.  Builds the tableau factors, the
  * multigrid hierarchy (levels N, N/2, ... to the first odd N or the coarsest
- * mesh with an interior node; coarsest interior size <= 4096), the Chebyshev
+ * mesh with an interior node; the coarsest level is solved exactly, by a dense
+ * FP64 inverse up to 9^3 unknowns and by fast diagonalisation above), the Chebyshev
  * intervals (Lanczos on D^{-1}A per level and block) and the dense coarse
  * inverses, and allocates all work memory on the current device.
  * `cuda_stream` is a cudaStream_t (NULL: default stream).  On success *out
@@ -195,14 +196,15 @@ irk_status irk_synchronize(irk_handle h);
  * of the timed launches in ms, the number of launches, and the number timed. */
 enum {
   IRK_PROF_APPLY64 = 0,   /* FP64 tensor-product operator kernel (stage operator, K y_n) */
-  IRK_PROF_MG_OP = 1,     /* multigrid level-operator kernels (Chebyshev steps, residuals) */
+  IRK_PROF_MG_OP = 1,     /* level-operator kernels (Chebyshev steps, residuals), coarser levels */
   IRK_PROF_MG_POINT = 2,  /* first Chebyshev step from zero */
   IRK_PROF_TRANSFER = 3,  /* restriction / prolongation passes */
   IRK_PROF_COARSE = 4,    /* dense coarse-grid solve */
   IRK_PROF_COMBINE = 5,   /* stage combinations and precision casts */
   IRK_PROF_KRYLOV = 6,    /* FGMRES vector kernels */
   IRK_PROF_RHS = 7,       /* stage right-hand side, solution update, interpolation */
-  IRK_PROF_NCAT = 8
+  IRK_PROF_MG_OP_FINE = 8,  /* level-operator kernels on the finest level */
+  IRK_PROF_NCAT = 9
 };
 irk_status irk_profile(irk_handle h, unsigned mask);
 irk_status irk_profile_read(irk_handle h, int category, double* ms, long long* launches, long long* timed);

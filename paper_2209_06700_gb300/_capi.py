@@ -75,7 +75,7 @@ SIGNATURES = {
     "irk_profile_read": (_I, [_H, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
 }
 
-PROF_CATEGORIES = ["apply64", "mg_op", "mg_point", "transfer", "coarse", "combine", "krylov", "rhs"]
+PROF_CATEGORIES = ["apply64", "mg_op", "mg_point", "transfer", "coarse", "combine", "krylov", "rhs", "mg_op_fine"]
 
 
 class IrkError(RuntimeError):

@@ -18,7 +18,7 @@ template <typename T>
 struct OpParams {
   int N, n1;           // cells per axis, nodes per axis (k N + 1)
   long long ld;        // elements between stage vectors
-  int zc;              // streaming chunk, in cells
+  int zc;              // streaming chunk, in cells (0: chosen by the launcher)
   int ntile_y;         // 3D: number of y tiles (grid.y = ntile_y * chunks)
   T me[kMaxDeg + 1][kMaxDeg + 1];
   T ke[kMaxDeg + 1][kMaxDeg + 1];
@@ -131,6 +131,21 @@ template <typename T>
 cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_in, long long ld_out,
                                  const int din[3], const int dout[3], int axis, int restrict_mode,
                                  int accumulate, const TransferParams& P, cudaStream_t st);
+
+// Exact coarse solve by fast diagonalisation: (cm_s M + tau K)^{-1} = W diag(1/(cm_s + tau mu)) W^T,
+// W = V (x) V (x) V with V^T M1 V = I, V^T K1 V = diag(mu1) on the interior 1D nodes.
+struct FdParams {
+  int ni;                   // interior nodes per axis
+  double tau;
+  double cm[kMaxStages];
+};
+// out = transform of `in` along `axis` on the interior grid: out[..i..] = sum_j Mt[i][j] in[..j..]
+template <typename Tin, typename Tout>
+cudaError_t launch_fd_axis(const Tin* in, Tout* out, int nstage, long long ld, int n1, int dim, int axis,
+                           const double* Mt, int ni, cudaStream_t st);
+// t[interior] *= 1 / (cm_s + tau (mu_a + mu_b (+ mu_c)))
+cudaError_t launch_fd_scale(double* t, int nstage, long long ld, int n1, int dim, const double* mu,
+                            const FdParams& P, cudaStream_t st);
 
 // Dense coarse solve per stage: x[map] = Ainv_s b[map] (FP64 inverse), zero elsewhere untouched.
 template <typename T>

@@ -55,25 +55,12 @@ LevelGeom make_level(int dim, int k, int N, const Element1D& e) {
   return g;
 }
 
-int choose_zc(int dim, int k, int N, int nstage) {
-  int cx, cy;
-  op_tile_shape(dim, k, &cx, &cy);
-  const int ntx = (N + cx - 1) / cx;
-  const int nty = (dim == 3) ? (N + cy - 1) / cy : 1;
-  const long long base = (long long)ntx * nty * std::max(1, nstage);
-  const long long target = 2 * 152;
-  long long nch = (target + base - 1) / base;
-  int zc = (int)((N + nch - 1) / std::max(1LL, nch));
-  zc = std::max(zc, 4);
-  return std::min(zc, N);
-}
-
 template <typename T>
 OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, const double* ck) {
   OpParams<T> P;
   std::memset(&P, 0, sizeof(P));
   P.N = g.N; P.n1 = g.n1; P.ld = g.ld;
-  P.zc = choose_zc(g.dim, g.k, g.N, nstage);
+  P.zc = 0;  // chosen by the launcher from the occupancy
   P.ntile_y = 1;
   for (int i = 0; i <= kMaxDeg; ++i)
     for (int j = 0; j <= kMaxDeg; ++j) { P.me[i][j] = (T)g.me[i][j]; P.ke[i][j] = (T)g.ke[i][j]; }
@@ -163,6 +150,46 @@ bool spd_inverse(int n, std::vector<double>& A) {
       A[(size_t)j * n + i] = s;
     }
   return true;
+}
+
+// Symmetric eigen-decomposition A = W diag(w) W^T by cyclic Jacobi rotations (A destroyed).
+void jacobi_eigen(int n, std::vector<double>& A, std::vector<double>& W, std::vector<double>& w) {
+  W.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) W[(size_t)i * n + i] = 1.0;
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+  double norm = 0.0;
+  for (double x : A) norm += x * x;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += a(i, j) * a(i, j);
+    if (off <= 1e-32 * norm) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a(p, q);
+        if (std::fabs(apq) < 1e-300) continue;
+        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = c * akp - sn * akq;
+          a(k, q) = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = c * apk - sn * aqk;
+          a(q, k) = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double wkp = W[(size_t)k * n + p], wkq = W[(size_t)k * n + q];
+          W[(size_t)k * n + p] = c * wkp - sn * wkq;
+          W[(size_t)k * n + q] = sn * wkp + c * wkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a(i, i);
 }
 
 template <typename T>
@@ -299,7 +326,26 @@ class MG final : public MGBase {
   }
 
   Status coarse_solve(const void* b, void* x, cudaStream_t st) override {
-    IRK_LAUNCH(PROF_COARSE, launch_coarse_solve<T>((const T*)b, (T*)x, cfg_.nb, lv_.back().g.ld, dAinv_, dmap_, nci_, st));
+    const LevelGeom& g = lv_.back().g;
+    if (!use_fd_) {
+      IRK_LAUNCH(PROF_COARSE, launch_coarse_solve<T>((const T*)b, (T*)x, cfg_.nb, g.ld, dAinv_, dmap_, nci_, st));
+      return Status::Ok();
+    }
+    // W^T along every axis, diagonal scaling, W along every axis
+    const int nb = cfg_.nb, n1 = g.n1, dim = g.dim, ni = n1 - 2;
+    double* t[2] = {fd_t1_, fd_t2_};
+    int cur = 0;
+    IRK_LAUNCH(PROF_COARSE, launch_fd_axis<T, double>((const T*)b, t[0], nb, g.ld, n1, dim, 0, fd_Vt_, ni, st));
+    for (int a = 1; a < dim; ++a) {
+      IRK_LAUNCH(PROF_COARSE, launch_fd_axis<double, double>(t[cur], t[1 - cur], nb, g.ld, n1, dim, a, fd_Vt_, ni, st));
+      cur = 1 - cur;
+    }
+    IRK_LAUNCH(PROF_COARSE, launch_fd_scale(t[cur], nb, g.ld, n1, dim, fd_mu_, fd_params_, st));
+    for (int a = 0; a + 1 < dim; ++a) {
+      IRK_LAUNCH(PROF_COARSE, launch_fd_axis<double, double>(t[cur], t[1 - cur], nb, g.ld, n1, dim, a, fd_V_, ni, st));
+      cur = 1 - cur;
+    }
+    IRK_LAUNCH(PROF_COARSE, launch_fd_axis<double, T>(t[cur], (T*)x, nb, g.ld, n1, dim, dim - 1, fd_V_, ni, st));
     return Status::Ok();
   }
 
@@ -329,7 +375,7 @@ class MG final : public MGBase {
     const int nb = cfg_.nb;
     if (cfg_.batched) {
       OpParams<T> P = make_op_params<T>(L.g, nb, cfg_.cm.data(), ck_.data());
-      IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, nb, u, P, epi, E, st));
+      IRK_LAUNCH(l == 0 ? PROF_MG_OP_FINE : PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, nb, u, P, epi, E, st));
       return Status::Ok();
     }
     for (int s = 0; s < nb; ++s) {
@@ -342,7 +388,7 @@ class MG final : public MGBase {
       Es.xj = E.xj ? E.xj + off : nullptr;
       Es.c1[0] = E.c1[s];
       Es.c2[0] = E.c2[s];
-      IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, 1, u + off, P, epi, Es, st));
+      IRK_LAUNCH(l == 0 ? PROF_MG_OP_FINE : PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, 1, u + off, P, epi, Es, st));
     }
     return Status::Ok();
   }
@@ -384,7 +430,7 @@ class MG final : public MGBase {
     nci_ = 1;
     for (int a = 0; a < dim; ++a) nci_ *= ni;
     if (nci_ < 1) return Status::Err(IRK_EINVAL, "coarsest mesh has no interior node");
-    if (nci_ > 2197) return Status::Err(IRK_EINVAL, "coarsest mesh too large for the dense coarse solve");
+    use_fd_ = nci_ > kDenseCoarseMax;
     // 1D assembled interior matrices on the coarsest mesh
     const int k = cfg_.k, p = k + 1;
     std::vector<double> M1((size_t)n1 * n1, 0.0), K1((size_t)n1 * n1, 0.0);
@@ -394,8 +440,8 @@ class MG final : public MGBase {
           M1[(size_t)(k * c + i) * n1 + k * c + j] += C.g.me[i][j];
           K1[(size_t)(k * c + i) * n1 + k * c + j] += C.g.ke[i][j];
         }
+    if (use_fd_) return setup_coarse_fd(M1, K1);
     std::vector<int> map(nci_);
-    std::vector<int> idx(dim);
     for (int q = 0; q < nci_; ++q) {
       int t = q, node = 0, stride = 1;
       for (int a = 0; a < dim; ++a) {
@@ -436,6 +482,83 @@ class MG final : public MGBase {
     IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
     IRK_CUDA(cudaMemcpy(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice));
     IRK_CUDA(cudaMemcpy(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return Status::Ok();
+  }
+
+  // Generalised 1D eigenproblem on the interior nodes: K1 v = mu M1 v, V^T M1 V = I.
+  Status setup_coarse_fd(const std::vector<double>& M1, const std::vector<double>& K1) {
+    const LevelGeom& g = lv_.back().g;
+    const int n1 = g.n1, ni = n1 - 2;
+    std::vector<double> Mi((size_t)ni * ni), Ki((size_t)ni * ni);
+    for (int i = 0; i < ni; ++i)
+      for (int j = 0; j < ni; ++j) {
+        Mi[(size_t)i * ni + j] = M1[(size_t)(i + 1) * n1 + j + 1];
+        Ki[(size_t)i * ni + j] = K1[(size_t)(i + 1) * n1 + j + 1];
+      }
+    // Cholesky Mi = L L^T
+    std::vector<double> L((size_t)ni * ni, 0.0);
+    for (int j = 0; j < ni; ++j) {
+      double d = Mi[(size_t)j * ni + j];
+      for (int k = 0; k < j; ++k) d -= L[(size_t)j * ni + k] * L[(size_t)j * ni + k];
+      if (d <= 0) return Status::Err(IRK_ENUMERIC, "1D mass matrix not SPD");
+      d = std::sqrt(d);
+      L[(size_t)j * ni + j] = d;
+      for (int i = j + 1; i < ni; ++i) {
+        double t = Mi[(size_t)i * ni + j];
+        for (int k = 0; k < j; ++k) t -= L[(size_t)i * ni + k] * L[(size_t)j * ni + k];
+        L[(size_t)i * ni + j] = t / d;
+      }
+    }
+    // C = L^{-1} Ki L^{-T}: solve column by column
+    auto fwd = [&](std::vector<double>& x) {  // x <- L^{-1} x
+      for (int i = 0; i < ni; ++i) {
+        double t = x[i];
+        for (int k = 0; k < i; ++k) t -= L[(size_t)i * ni + k] * x[k];
+        x[i] = t / L[(size_t)i * ni + i];
+      }
+    };
+    std::vector<double> Y((size_t)ni * ni), C((size_t)ni * ni), col(ni);
+    for (int j = 0; j < ni; ++j) {  // Y = L^{-1} Ki
+      for (int i = 0; i < ni; ++i) col[i] = Ki[(size_t)i * ni + j];
+      fwd(col);
+      for (int i = 0; i < ni; ++i) Y[(size_t)i * ni + j] = col[i];
+    }
+    for (int i = 0; i < ni; ++i) {  // C = Y L^{-T} = (L^{-1} Y^T)^T
+      for (int j = 0; j < ni; ++j) col[j] = Y[(size_t)i * ni + j];
+      fwd(col);
+      for (int j = 0; j < ni; ++j) C[(size_t)i * ni + j] = col[j];
+    }
+    for (int i = 0; i < ni; ++i)
+      for (int j = i + 1; j < ni; ++j) {
+        const double a = 0.5 * (C[(size_t)i * ni + j] + C[(size_t)j * ni + i]);
+        C[(size_t)i * ni + j] = C[(size_t)j * ni + i] = a;
+      }
+    std::vector<double> W, mu;
+    jacobi_eigen(ni, C, W, mu);
+    // V = L^{-T} W (back substitution per column)
+    std::vector<double> V((size_t)ni * ni), Vt((size_t)ni * ni);
+    for (int j = 0; j < ni; ++j) {
+      for (int i = ni - 1; i >= 0; --i) {
+        double t = W[(size_t)i * ni + j];
+        for (int k = i + 1; k < ni; ++k) t -= L[(size_t)k * ni + i] * V[(size_t)k * ni + j];
+        V[(size_t)i * ni + j] = t / L[(size_t)i * ni + i];
+      }
+    }
+    for (int i = 0; i < ni; ++i)
+      for (int j = 0; j < ni; ++j) Vt[(size_t)i * ni + j] = V[(size_t)j * ni + i];
+    IRK_TRY(arena_.alloc((void**)&fd_V_, V.size() * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&fd_Vt_, Vt.size() * sizeof(double)));
+    IRK_TRY(arena_.alloc((void**)&fd_mu_, mu.size() * sizeof(double)));
+    const size_t vb = (size_t)cfg_.nb * g.ld * sizeof(double);
+    IRK_TRY(arena_.alloc((void**)&fd_t1_, vb));
+    IRK_TRY(arena_.alloc((void**)&fd_t2_, vb));
+    IRK_CUDA(cudaMemcpy(fd_V_, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpy(fd_Vt_, Vt.data(), Vt.size() * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpy(fd_mu_, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice));
+    std::memset(&fd_params_, 0, sizeof(fd_params_));
+    fd_params_.ni = ni;
+    fd_params_.tau = cfg_.tau;
+    for (int s = 0; s < cfg_.nb && s < kMaxStages; ++s) fd_params_.cm[s] = cfg_.cm[s];
     return Status::Ok();
   }
 
@@ -564,6 +687,10 @@ class MG final : public MGBase {
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
   int nci_ = 0;
+  static constexpr int kDenseCoarseMax = 729;  // dense inverse up to 9^3 unknowns, else fast diagonalisation
+  bool use_fd_ = false;
+  double *fd_V_ = nullptr, *fd_Vt_ = nullptr, *fd_mu_ = nullptr, *fd_t1_ = nullptr, *fd_t2_ = nullptr;
+  FdParams fd_params_{};
 };
 
 }  // namespace

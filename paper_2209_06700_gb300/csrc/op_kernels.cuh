@@ -451,21 +451,62 @@ inline void op_tile_shape_impl(int dim, int k, int* cx, int* cy) {
   *cy = (k == 1) ? 8 : (k == 2) ? 4 : 2;
 }
 
+inline int device_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n = v > 0 ? v : 1;
+  }
+  return n;
+}
+
+// Streaming chunk (cells per CTA along the streaming axis): minimise
+// waves(CTAs) x planes per CTA, where a chunk that does not start at the
+// bottom also streams the k planes of the cell below it.
+inline int pick_zc(int N, long long base_ctas, long long slots, int K) {
+  int best = N;
+  long long best_cost = -1;
+  for (int zc = 1; zc <= N; ++zc) {
+    const long long nch = (N + zc - 1) / zc;
+    const long long waves = (base_ctas * nch + slots - 1) / slots;
+    const long long planes = (long long)K * (zc + (nch > 1 ? 1 : 0)) + 1;
+    const long long cost = waves * planes;
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = zc; }
+  }
+  return best;
+}
+
 template <typename T, int K, int EPI>
 cudaError_t launch_op_k(int dim, int nstage, const T* u, const OpParams<T>& P, const EpiParams<T>& E,
                         cudaStream_t st) {
   int cx, cy;
   op_tile_shape_impl(dim, K, &cx, &cy);
   const int ntx = (P.N + cx - 1) / cx;
-  const int nch = (P.N + P.zc - 1) / P.zc;
+  OpParams<T> Q = P;
   if (dim == 3) {
-    OpParams<T> Q = P;
+    const int threads = 32 * K * cy;
+    static int occ = 0;
+    if (occ == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op3d_kernel<T, K, EPI>, threads, 0);
+      if (occ < 1) occ = 1;
+    }
     Q.ntile_y = (P.N + cy - 1) / cy;
+    if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * Q.ntile_y * nstage, (long long)occ * device_sm_count(), K);
+    const int nch = (P.N + Q.zc - 1) / Q.zc;
     dim3 grid(ntx, Q.ntile_y * nch, nstage);
-    op3d_kernel<T, K, EPI><<<grid, 32 * K * cy, 0, st>>>(u, Q, E);
+    op3d_kernel<T, K, EPI><<<grid, threads, 0, st>>>(u, Q, E);
   } else {
+    static int occ = 0;
+    if (occ == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op2d_kernel<T, K, EPI>, 64, 0);
+      if (occ < 1) occ = 1;
+    }
+    if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * nstage, (long long)occ * device_sm_count(), K);
+    const int nch = (P.N + Q.zc - 1) / Q.zc;
     dim3 grid(ntx, nch, nstage);
-    op2d_kernel<T, K, EPI><<<grid, 64, 0, st>>>(u, P, E);
+    op2d_kernel<T, K, EPI><<<grid, 64, 0, st>>>(u, Q, E);
   }
   return cudaGetLastError();
 }

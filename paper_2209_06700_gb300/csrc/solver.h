@@ -57,7 +57,6 @@ struct LevelGeom {
 };
 
 LevelGeom make_level(int dim, int k, int N, const Element1D& e);
-int choose_zc(int dim, int k, int N, int nstage);
 
 template <typename T>
 OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, const double* ck);

@@ -303,6 +303,43 @@ __global__ void coarse_solve_kernel(const T* __restrict__ b, T* __restrict__ x, 
   }
 }
 
+// ------------------------------------------------------------ fast-diagonalisation coarse solve
+template <typename Tin, typename Tout>
+__global__ void fd_axis_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, long long ld, int n1, int dim,
+                               int axis, const double* __restrict__ Mt, int ni) {
+  const int s = blockIdx.y;
+  const int total = (dim == 3) ? ni * ni * ni : ni * ni;
+  const int stride[3] = {1, n1, n1 * n1};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int a[3];
+    a[0] = e % ni;
+    a[1] = (e / ni) % ni;
+    a[2] = (dim == 3) ? e / (ni * ni) : 0;
+    int base = 0;
+    for (int d = 0; d < dim; ++d)
+      if (d != axis) base += (a[d] + 1) * stride[d];
+    const int i = a[axis];
+    const Tin* src = in + s * ld + base + stride[axis];
+    double acc = 0.0;
+    for (int j = 0; j < ni; ++j) acc += Mt[i * ni + j] * (double)src[j * stride[axis]];
+    out[s * ld + base + (i + 1) * stride[axis]] = (Tout)acc;
+  }
+}
+
+__global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, int dim, const double* __restrict__ mu,
+                                const FdParams P) {
+  const int s = blockIdx.y;
+  const int ni = P.ni;
+  const int total = (dim == 3) ? ni * ni * ni : ni * ni;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int a0 = e % ni, a1 = (e / ni) % ni, a2 = (dim == 3) ? e / (ni * ni) : 0;
+    double m = mu[a0] + mu[a1];
+    int idx = (a0 + 1) + (a1 + 1) * n1;
+    if (dim == 3) { m += mu[a2]; idx += (a2 + 1) * n1 * n1; }
+    t[s * ld + idx] /= (P.cm[s] + P.tau * m);
+  }
+}
+
 }  // namespace
 
 // ============================================================ launchers
@@ -414,6 +451,29 @@ template cudaError_t launch_transfer_axis<float>(const float*, float*, int, long
                                                  const int[3], int, int, int, const TransferParams&, cudaStream_t);
 template cudaError_t launch_transfer_axis<double>(const double*, double*, int, long long, long long, const int[3],
                                                   const int[3], int, int, int, const TransferParams&, cudaStream_t);
+
+template <typename Tin, typename Tout>
+cudaError_t launch_fd_axis(const Tin* in, Tout* out, int nstage, long long ld, int n1, int dim, int axis,
+                           const double* Mt, int ni, cudaStream_t st) {
+  const long long total = (dim == 3) ? (long long)ni * ni * ni : (long long)ni * ni;
+  dim3 grid(blocks_for(total), nstage);
+  fd_axis_kernel<Tin, Tout><<<grid, kThreads, 0, st>>>(in, out, ld, n1, dim, axis, Mt, ni);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fd_axis<float, double>(const float*, double*, int, long long, int, int, int,
+                                                   const double*, int, cudaStream_t);
+template cudaError_t launch_fd_axis<double, double>(const double*, double*, int, long long, int, int, int,
+                                                    const double*, int, cudaStream_t);
+template cudaError_t launch_fd_axis<double, float>(const double*, float*, int, long long, int, int, int,
+                                                   const double*, int, cudaStream_t);
+
+cudaError_t launch_fd_scale(double* t, int nstage, long long ld, int n1, int dim, const double* mu, const FdParams& P,
+                            cudaStream_t st) {
+  const long long total = (dim == 3) ? (long long)P.ni * P.ni * P.ni : (long long)P.ni * P.ni;
+  dim3 grid(blocks_for(total), nstage);
+  fd_scale_kernel<<<grid, kThreads, 0, st>>>(t, ld, n1, dim, mu, P);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_coarse_solve(const T* b, T* x, int nstage, long long ld, const double* Ainv, const int* map, int nci,

@@ -18,6 +18,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
 
+# (dim, cells, degree, stages): several CTA tiles in x (32 cells in 3D, 64 in 2D), y and z,
+# ragged tails, odd cell counts (coarsest level solved by fast diagonalisation)
 CASES = [(2, 70, 1, 2), (2, 37, 2, 3), (2, 20, 3, 2), (2, 66, 4, 3),
          (3, 66, 1, 2), (3, 36, 2, 3), (3, 12, 2, 2), (3, 34, 3, 3), (3, 40, 4, 2), (3, 5, 4, 5)]
 

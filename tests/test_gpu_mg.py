@@ -129,3 +129,28 @@ def test_coarse_solve(dim, N, k, Q):
             x[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[i][keep])
             ref.append(x)
         assert rel_err(got, np.stack(ref)) <= 1e-11
+
+
+@pytest.mark.parametrize("dim,N,k,Q", [(3, 5, 3, 2), (2, 37, 2, 3), (3, 9, 2, 2)])
+@pytest.mark.parametrize("prec,dt", [(64, torch.float64), (32, torch.float32)])
+def test_coarse_solve_fast_diagonalisation(dim, N, k, Q, prec, dt):
+    """Odd coarsest meshes above 9^3 unknowns use the exact fast-diagonalisation solve."""
+    tau = 1e-2
+    with pkg.Solver(dim, N, k, Q, tau, mg_precision=prec) as s:
+        lam = _blocks(Q)
+        L = s.levels - 1
+        Nc = level_sizes(N, k)[-1]
+        n1 = k * Nc + 1
+        assert (n1 - 2) ** dim > 729
+        b = zero_boundary(uniform_vectors((Q, n1 ** dim), seed=12), dim, n1)
+        xd = s.stage_vector(dtype=dt, level=L)
+        s.mg_coarse_solve(to_dev(s, b, dt, level=L), xd)
+        got = from_dev(xd, n1 ** dim)
+        ref = []
+        for i in range(Q):
+            A, bm = level_operator(dim, Nc, k, lam[i], tau)
+            x = np.zeros(n1 ** dim)
+            keep = ~bm
+            x[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[i][keep])
+            ref.append(x)
+        assert rel_err(got, np.stack(ref)) <= (1e-11 if prec == 64 else 2e-6)

@@ -3,9 +3,10 @@
 // preconditioner of Eq. (irk:P)).  The flexible variant stores the
 // preconditioned vectors Z because the preconditioner (one mixed-precision
 // V-cycle per block) is not a fixed linear map in floating point.
-// Classical Gram-Schmidt with one re-orthogonalisation pass (CGS2); the dot
-// products are deterministic device reductions and the Hessenberg/Givens
-// update runs on the host with one device->host transfer per iteration.
+// Classical Gram-Schmidt with a conditional second pass (Kahan-Parlett "twice
+// is enough", decided on the device); the dot products are deterministic
+// device reductions and the Hessenberg/Givens update runs on the host with
+// one device->host transfer per iteration.
 #include <cmath>
 #include <vector>
 
@@ -24,7 +25,7 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
   IRK_TRY(arena.alloc((void**)&w.V, (size_t)(m + 1) * w.len * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.Z, (size_t)m * w.len * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.tmp, (size_t)w.len * sizeof(double)));
-  IRK_TRY(arena.alloc((void**)&w.partial, (size_t)64 * w.nb * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.partial, (size_t)66 * w.nb * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.dvals, 256 * sizeof(double)));
   if (!w.hvals) {
     cudaError_t e = cudaMallocHost((void**)&w.hvals, 256 * sizeof(double));
@@ -38,7 +39,8 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
 namespace {
 
 // layout of dvals / hvals
-constexpr int kH1 = 0, kH2 = 64, kNrm = 128, kY = 160, kOne = 255;
+constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kN0 = 131, kY = 160, kOne = 255;
+constexpr double kEta = 0.7;  // Kahan-Parlett threshold of the conditional second pass
 
 Status norm(FGMRESWork& w, const double* v, cudaStream_t st, double& out) {
   IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial(v, w.len, w.partial, w.nb, st));
@@ -78,21 +80,23 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const
       double* wv = w.V + (size_t)(j + 1) * len;
       IRK_TRY(prec(Vj, Zj));
       IRK_TRY(op(Zj, wv));
-      // CGS2
+      // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
       const int nv = j + 1;
-      IRK_LAUNCH(PROF_KRYLOV, launch_multidot(w.V, len, nv, wv, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv, w.nb, w.dvals + kH1, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.V, len, nv, w.dvals + kH1, -1.0, wv, len, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_multidot(w.V, len, nv, wv, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv, w.nb, w.dvals + kH2, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.V, len, nv, w.dvals + kH2, -1.0, wv, len, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial(wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot(w.V, len, nv, wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH1, st));
+      // dvals[kH1 + nv] = |w|^2, copied aside before pass 2 overwrites row nv
+      IRK_CUDA(cudaMemcpyAsync(w.dvals + kN0, w.dvals + kH1 + nv, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot(w.V, len, nv, w.dvals + kH1, wv, w.tmp, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH2, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth(w.V, len, nv, w.dvals + kH2, w.tmp, wv, len, w.dvals + kN0,
+                                               w.dvals + kH2 + nv, kEta, w.partial, w.nb, st));
       IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
-      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kNrm + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kN0 + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       IRK_CUDA(cudaStreamSynchronize(st));
       const double hn = w.hvals[kNrm];
       if (!std::isfinite(hn)) return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + w.hvals[kH2 + i];
+      const bool redo = w.hvals[kH2 + nv] < kEta * kEta * w.hvals[kN0];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + (redo ? w.hvals[kH2 + i] : 0.0);
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_inv(wv, w.dvals + kNrm, wv, len, st));
       // Givens rotations

@@ -120,6 +120,20 @@ cudaError_t launch_multi_axpy(const double* V, long long vstride, int nv, const 
 cudaError_t launch_scale_inv(const double* w, const double* nrm, double* out, long long n, cudaStream_t st);
 // out = a * x
 cudaError_t launch_scale(const double* x, double a, double* out, long long n, cudaStream_t st);
+// Fused Gram-Schmidt passes (classical Gram-Schmidt with the "twice is enough" test of Kahan
+// and Parlett); partial has rows [0, nv] x nb:
+//  gs_dot      : partial[i] = dot(V_i, w) (i < nv), partial[nv] = |w|^2
+//  gs_axpy_dot : w_out = w_in - sum_i h[i] V_i; partial[i] = dot(V_i, w_out), partial[nv] = |w_out|^2
+//  gs_reorth   : if |w_mid|^2 < eta^2 |w|^2 (device scalars norm2_mid, norm2_in): w_out = w_in - sum h[i] V_i,
+//                else w_out = w_in; partial[0] = |w_out|^2
+cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
+                          int nb, cudaStream_t st);
+cudaError_t launch_gs_axpy_dot(const double* V, long long vstride, int nv, const double* h, const double* w_in,
+                               double* w_out, long long n, double* partial, int nb, cudaStream_t st);
+cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const double* h, const double* w_in,
+                             double* w_out, long long n, const double* norm2_in, const double* norm2_mid, double eta,
+                             double* partial, int nb, cudaStream_t st);
+
 // ---------------- intergrid transfer (Q_k embedding) ----------------
 struct TransferParams {
   int k, Nc;                 // degree, coarse cells per axis

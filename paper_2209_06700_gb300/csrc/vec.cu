@@ -10,6 +10,8 @@
 // * Intergrid transfer: the Q_k embedding P = P1 (x) P1 (x) P1 and its transpose,
 //   applied one axis at a time.
 // * Dense coarse-grid solve with a precomputed FP64 inverse.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace irk {
@@ -51,26 +53,27 @@ __device__ __forceinline__ T diag_at(const DiagParams<T>& D, int s, int dim, int
 }
 
 // ------------------------------------------------------------ stage combination
-template <typename Tin, typename Tout>
-__global__ void combine_kernel(const Tin* __restrict__ a, const double* __restrict__ b, Tout* __restrict__ out,
-                               long long n, long long ld, const CombineParams C) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double av[kMaxQ], bv[kMaxQ];
+// NMAX: compile-time bound on the number of input/output stage vectors (keeps the
+// per-thread arrays in registers at a register count that allows full occupancy).
+template <typename Tin, typename Tout, int NMAX>
+__global__ void __launch_bounds__(kThreads) combine_kernel(const Tin* __restrict__ a, const double* __restrict__ b,
+                                                           Tout* __restrict__ out, int n, long long ld,
+                                                           const CombineParams C) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double av[NMAX], bv[NMAX];
 #pragma unroll
-    for (int j = 0; j < kMaxQ; ++j) {
+    for (int j = 0; j < NMAX; ++j) {
       av[j] = (j < C.nina) ? (double)a[j * ld + e] : 0.0;
       bv[j] = (j < C.ninb) ? b[j * ld + e] : 0.0;
     }
 #pragma unroll
-    for (int i = 0; i < kMaxQ; ++i) {
-      if (i >= C.nout) break;
-      double acc = 0.0;
+    for (int i = 0; i < NMAX; ++i) {
+      if (i < C.nout) {
+        double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < kMaxQ; ++j) {
-        if (j < C.nina) acc += C.Da[i * kMaxQ + j] * av[j];
-        if (j < C.ninb) acc += C.Db[i * kMaxQ + j] * bv[j];
+        for (int j = 0; j < NMAX; ++j) acc += C.Da[i * kMaxQ + j] * av[j] + C.Db[i * kMaxQ + j] * bv[j];
+        out[i * ld + e] = (Tout)acc;
       }
-      out[i * ld + e] = (Tout)acc;
     }
   }
 }
@@ -182,6 +185,89 @@ __global__ void multidot_kernel(const double* __restrict__ V, long long vstride,
   }
 }
 
+// Fused Gram-Schmidt kernels (see kernels.h).  Each block reduces its partial sums in a fixed order.
+// Basis vectors are taken in groups of 8 (blockIdx.y); the last group also reduces |w|^2 into row nv.
+template <int MODE>  // 0: dots of w_in;  1: w_out = w_in - V h, then dots of w_out
+__global__ void __launch_bounds__(kThreads) gs_kernel(const double* __restrict__ V, long long vstride, int nv,
+                                                      const double* __restrict__ h, const double* __restrict__ w_in,
+                                                      double* __restrict__ w_out, int n, double* __restrict__ partial,
+                                                      int nb) {
+  constexpr int G = 8;
+  const int i0 = blockIdx.y * G;
+  const bool last = (i0 + G >= nv);
+  __shared__ double hs[64];
+  if (MODE == 1) {
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+  }
+  double acc[G + 1];
+#pragma unroll
+  for (int g = 0; g <= G; ++g) acc[g] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double we = w_in[e];
+    if (MODE == 1) {
+      for (int i = 0; i < nv; ++i) we -= hs[i] * V[i * vstride + e];
+      if (blockIdx.y == 0) w_out[e] = we;
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (i0 + g < nv) acc[g] += V[(i0 + g) * vstride + e] * we;
+    acc[G] += we * we;
+  }
+  const int cnt = min(G, nv - i0);
+  __shared__ double sred[G + 1][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g <= G; ++g) {
+    double v = acc[g];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) sred[g][warp] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x <= G) {
+    const int g = threadIdx.x;
+    double v = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) v += sred[g][q];
+    if (g < cnt) partial[(long long)(i0 + g) * nb + blockIdx.x] = v;
+    if (g == G && last) partial[(long long)nv * nb + blockIdx.x] = v;
+  }
+}
+
+// w_out = w_in - V h when the first pass cancelled more than 1 - eta of |w| ("twice is enough"),
+// else w_out = w_in; partial = |w_out|^2 per block.
+__global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const double* __restrict__ V, long long vstride, int nv,
+                                                             const double* __restrict__ h,
+                                                             const double* __restrict__ w_in,
+                                                             double* __restrict__ w_out, int n,
+                                                             const double* __restrict__ norm2_in,
+                                                             const double* __restrict__ norm2_mid, double eta,
+                                                             double* __restrict__ partial) {
+  const bool redo = norm2_mid[0] < eta * eta * norm2_in[0];
+  __shared__ double hs[64];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = redo ? h[i] : 0.0;
+  __syncthreads();
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double we = w_in[e];
+    if (redo)
+      for (int i = 0; i < nv; ++i) we -= hs[i] * V[i * vstride + e];
+    w_out[e] = we;
+    acc += we * we;
+  }
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) v += red[q];
+    partial[blockIdx.x] = v;
+  }
+}
+
 __global__ void norm2_kernel(const double* __restrict__ w, long long n, double* __restrict__ partial) {
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -244,44 +330,45 @@ __global__ void scale_kernel(const double* __restrict__ x, double a, double* __r
 }
 
 // ------------------------------------------------------------ transfers
-template <typename T>
-__global__ void transfer_axis_kernel(const T* __restrict__ in, T* __restrict__ out, long long ld_in, long long ld_out,
-                                     int din0, int din1, int din2, int dout0, int dout1, int dout2, int axis,
-                                     int restrict_mode, int accumulate, const TransferParams P) {
+template <typename T, int AXIS, bool RESTRICT>
+__global__ void __launch_bounds__(kThreads) transfer_axis_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                                 long long ld_in, long long ld_out, int din0, int din1,
+                                                                 int dout0, int dout1, int dout2, int accumulate,
+                                                                 const TransferParams P) {
   const int s = blockIdx.y;
-  const long long nout = (long long)dout0 * dout1 * dout2;
+  const int nout = dout0 * dout1 * dout2;
   const int k = P.k, Nc = P.Nc, p = k + 1;
-  const long long sin_[3] = {1, (long long)din0, (long long)din0 * din1};
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nout; e += (long long)gridDim.x * blockDim.x) {
-    int o[3];
-    o[0] = (int)(e % dout0);
-    o[1] = (int)((e / dout0) % dout1);
-    o[2] = (int)(e / ((long long)dout0 * dout1));
-    const int ca = o[axis];
-    long long base = 0;
-    for (int a = 0; a < 3; ++a)
-      if (a != axis) base += o[a] * sin_[a];
-    const T* src = in + s * ld_in + base;
-    const long long st = sin_[axis];
+  const int st = (AXIS == 0) ? 1 : (AXIS == 1) ? din0 : din0 * din1;
+  const int ndc = (AXIS == 0) ? dout0 : (AXIS == 1) ? dout1 : dout2;
+  const T* __restrict__ src0 = in + s * ld_in;
+  T* __restrict__ dst0 = out + s * ld_out;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nout; e += gridDim.x * blockDim.x) {
+    const int o0 = e % dout0;
+    const int t = e / dout0;
+    const int o1 = t % dout1, o2 = t / dout1;
+    int ca, base;
+    if (AXIS == 0) { ca = o0; base = o1 * din0 + o2 * din0 * din1; }
+    else if (AXIS == 1) { ca = o1; base = o0 + o2 * din0 * din1; }
+    else { ca = o2; base = o0 + o1 * din0; }
+    const T* src = src0 + base;
     double acc = 0.0;
-    if (restrict_mode) {
+    if (RESTRICT) {
       // coarse index ca = k*cc + i; fine nodes of coarse cell cc are 2k*cc + m, m = 0..2k
-      const int ndc = (axis == 0) ? dout0 : (axis == 1) ? dout1 : dout2;
       if (ca == 0 || ca == ndc - 1) continue;  // coarse boundary stays zero
       const int cc = ca / k, i = ca - cc * k;
       if (i != 0) {
-        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + i] * (double)src[(long long)(2 * k * cc + m) * st];
+        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + i] * (double)src[(2 * k * cc + m) * st];
       } else {
-        for (int m = 0; m < 2 * k; ++m) acc += P.Pc[m * p + k] * (double)src[(long long)(2 * k * (cc - 1) + m) * st];
-        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + 0] * (double)src[(long long)(2 * k * cc + m) * st];
+        for (int m = 0; m < 2 * k; ++m) acc += P.Pc[m * p + k] * (double)src[(2 * k * (cc - 1) + m) * st];
+        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + 0] * (double)src[(2 * k * cc + m) * st];
       }
     } else {
       int cc = ca / (2 * k);
       if (cc > Nc - 1) cc = Nc - 1;
       const int m = ca - 2 * k * cc;
-      for (int i = 0; i <= k; ++i) acc += P.Pc[m * p + i] * (double)src[(long long)(k * cc + i) * st];
+      for (int i = 0; i <= k; ++i) acc += P.Pc[m * p + i] * (double)src[(k * cc + i) * st];
     }
-    T* dst = out + s * ld_out + e;
+    T* dst = dst0 + e;
     if (accumulate) *dst = (T)((double)*dst + acc);
     else *dst = (T)acc;
   }
@@ -346,7 +433,19 @@ __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, in
 template <typename Tin, typename Tout>
 cudaError_t launch_combine(const Tin* a, const double* b, Tout* out, long long n, long long ld, const CombineParams& C,
                            cudaStream_t st) {
-  combine_kernel<Tin, Tout><<<blocks_for(n, 2), kThreads, 0, st>>>(a, b, out, n, ld, C);
+  const int nmax = std::max(C.nout, std::max(C.nina, C.ninb));
+  const int grid = blocks_for(n, 2);
+  CombineParams Cz = C;  // unused coefficients must be zero: the kernel multiplies every slot
+  for (int i = 0; i < kMaxQ; ++i)
+    for (int j = 0; j < kMaxQ; ++j) {
+      if (i >= C.nout || j >= C.nina) Cz.Da[i * kMaxQ + j] = 0.0;
+      if (i >= C.nout || j >= C.ninb) Cz.Db[i * kMaxQ + j] = 0.0;
+    }
+  if (nmax <= 1) combine_kernel<Tin, Tout, 1><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
+  else if (nmax <= 2) combine_kernel<Tin, Tout, 2><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
+  else if (nmax <= 3) combine_kernel<Tin, Tout, 3><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
+  else if (nmax <= 5) combine_kernel<Tin, Tout, 5><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
+  else combine_kernel<Tin, Tout, kMaxQ><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
   return cudaGetLastError();
 }
 template cudaError_t launch_combine<double, double>(const double*, const double*, double*, long long, long long,
@@ -415,6 +514,31 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
   return cudaGetLastError();
 }
 
+cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
+                          int nb, cudaStream_t st) {
+  if (nv > 64) return cudaErrorInvalidValue;
+  dim3 grid(nb, (nv + 7) / 8);
+  gs_kernel<0><<<grid, kThreads, 0, st>>>(V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_axpy_dot(const double* V, long long vstride, int nv, const double* h, const double* w_in,
+                               double* w_out, long long n, double* partial, int nb, cudaStream_t st) {
+  if (nv > 64 || w_in == w_out) return cudaErrorInvalidValue;
+  // group 0 writes w_out; the other groups recompute it for their dots
+  dim3 grid(nb, (nv + 7) / 8);
+  gs_kernel<1><<<grid, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, partial, nb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const double* h, const double* w_in,
+                             double* w_out, long long n, const double* norm2_in, const double* norm2_mid, double eta,
+                             double* partial, int nb, cudaStream_t st) {
+  if (nv > 64) return cudaErrorInvalidValue;
+  gs_reorth_kernel<<<nb, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, norm2_in, norm2_mid, eta, partial);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm2_partial(const double* w, long long n, double* partial, int nb, cudaStream_t st) {
   norm2_kernel<<<nb, kThreads, 0, st>>>(w, n, partial);
   return cudaGetLastError();
@@ -443,8 +567,14 @@ cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_i
                                  const TransferParams& P, cudaStream_t st) {
   const long long nout = (long long)dout[0] * dout[1] * dout[2];
   dim3 grid(blocks_for(nout, 2), nstage);
-  transfer_axis_kernel<T><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], din[2], dout[0], dout[1],
-                                                     dout[2], axis, restrict_mode, accumulate, P);
+#define IRK_TR(AX, R) transfer_axis_kernel<T, AX, R><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], \
+                                                                             dout[0], dout[1], dout[2], accumulate, P)
+  if (restrict_mode) {
+    if (axis == 0) IRK_TR(0, true); else if (axis == 1) IRK_TR(1, true); else IRK_TR(2, true);
+  } else {
+    if (axis == 0) IRK_TR(0, false); else if (axis == 1) IRK_TR(1, false); else IRK_TR(2, false);
+  }
+#undef IRK_TR
   return cudaGetLastError();
 }
 template cudaError_t launch_transfer_axis<float>(const float*, float*, int, long long, long long, const int[3],

@@ -138,6 +138,7 @@ cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const d
 struct TransferParams {
   int k, Nc;                 // degree, coarse cells per axis
   double Pc[(2 * kMaxDeg + 1) * (kMaxDeg + 1)];  // (2k+1) x (k+1)
+  float Pcf[(2 * kMaxDeg + 1) * (kMaxDeg + 1)];  // the same in FP32 (arithmetic of the FP32 multigrid)
 };
 // One 1D pass along `axis` of a 3D (or 2D, d2 = 1) array; in/out dims (x fastest).
 // restrict: out[.. c ..] = sum_f P1[f][c] in[.. f ..]; prolong: out[.. f ..] (+)= sum_c P1[f][c] in[.. c ..]

@@ -365,7 +365,10 @@ class MG final : public MGBase {
     std::memset(&P, 0, sizeof(P));
     P.k = cfg_.k;
     P.Nc = Nc;
-    for (size_t i = 0; i < el_.Pc.size(); ++i) P.Pc[i] = el_.Pc[i];
+    for (size_t i = 0; i < el_.Pc.size(); ++i) {
+      P.Pc[i] = el_.Pc[i];
+      P.Pcf[i] = (float)el_.Pc[i];
+    }
     return P;
   }
 

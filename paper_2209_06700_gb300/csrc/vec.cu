@@ -27,11 +27,12 @@ inline int blocks_for(long long n, int per_thread = 1) {
   return (int)b;
 }
 
-__device__ __forceinline__ void coords(long long idx, int dim, int n1, int& x, int& y, int& z) {
-  x = (int)(idx % n1);
-  long long r = idx / n1;
-  y = (int)(r % n1);
-  z = (dim == 3) ? (int)(r / n1) : 0;
+// 32-bit index arithmetic: a stage vector has fewer than 2^31 nodes
+__device__ __forceinline__ void coords(int idx, int dim, int n1, int& x, int& y, int& z) {
+  x = idx % n1;
+  const int r = idx / n1;
+  y = r % n1;
+  z = (dim == 3) ? r / n1 : 0;
 }
 
 __device__ __forceinline__ bool interior(int dim, int n1, int x, int y, int z) {
@@ -70,8 +71,14 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const Tin* __restrict
     for (int i = 0; i < NMAX; ++i) {
       if (i < C.nout) {
         double acc = 0.0;
+        // zero coefficients (triangular S~, diagonal stiffness coupling) are skipped: FP64 issue
+        // slots are scarce on this part, and the branches are uniform across the grid
 #pragma unroll
-        for (int j = 0; j < NMAX; ++j) acc += C.Da[i * kMaxQ + j] * av[j] + C.Db[i * kMaxQ + j] * bv[j];
+        for (int j = 0; j < NMAX; ++j) {
+          const double ca = C.Da[i * kMaxQ + j], cb = C.Db[i * kMaxQ + j];
+          if (ca != 0.0) acc += ca * av[j];
+          if (cb != 0.0) acc += cb * bv[j];
+        }
         out[i * ld + e] = (Tout)acc;
       }
     }
@@ -82,7 +89,8 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const Tin* __restrict
 template <typename T>
 __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
   const int s = blockIdx.y;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+  const int n = (int)g.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
@@ -95,7 +103,8 @@ template <typename T>
 __global__ void diag_scale_kernel(GridInfo g, const T* __restrict__ x, T* __restrict__ out, const DiagParams<T> D,
                                   int inv_sqrt) {
   const int s = blockIdx.y;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+  const int n = (int)g.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
@@ -109,7 +118,8 @@ __global__ void diag_scale_kernel(GridInfo g, const T* __restrict__ x, T* __rest
 __global__ void stage_rhs_kernel(GridInfo g, const RhsParams R, const double* __restrict__ Ky,
                                  const double* __restrict__ G1, const double* __restrict__ loads,
                                  double* __restrict__ rhs) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+  const int n = (int)g.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
@@ -144,7 +154,8 @@ __global__ void update_kernel(GridInfo g, const UpdateParams U, const double* __
 
 __global__ void interpolate_kernel(GridInfo g, const double* __restrict__ x1d, double ct, double* __restrict__ y) {
   const double pi = 3.14159265358979323846;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
+  const int n = (int)g.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) { y[e] = 0.0; continue; }
@@ -351,26 +362,28 @@ __global__ void __launch_bounds__(kThreads) transfer_axis_kernel(const T* __rest
     else if (AXIS == 1) { ca = o1; base = o0 + o2 * din0 * din1; }
     else { ca = o2; base = o0 + o1 * din0; }
     const T* src = src0 + base;
-    double acc = 0.0;
+    // arithmetic in the element type (FP32 for the FP32 multigrid)
+    const T* Pc = (sizeof(T) == 4) ? reinterpret_cast<const T*>(P.Pcf) : reinterpret_cast<const T*>(P.Pc);
+    T acc = T(0);
     if (RESTRICT) {
       // coarse index ca = k*cc + i; fine nodes of coarse cell cc are 2k*cc + m, m = 0..2k
       if (ca == 0 || ca == ndc - 1) continue;  // coarse boundary stays zero
       const int cc = ca / k, i = ca - cc * k;
       if (i != 0) {
-        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + i] * (double)src[(2 * k * cc + m) * st];
+        for (int m = 0; m <= 2 * k; ++m) acc += Pc[m * p + i] * src[(2 * k * cc + m) * st];
       } else {
-        for (int m = 0; m < 2 * k; ++m) acc += P.Pc[m * p + k] * (double)src[(2 * k * (cc - 1) + m) * st];
-        for (int m = 0; m <= 2 * k; ++m) acc += P.Pc[m * p + 0] * (double)src[(2 * k * cc + m) * st];
+        for (int m = 0; m < 2 * k; ++m) acc += Pc[m * p + k] * src[(2 * k * (cc - 1) + m) * st];
+        for (int m = 0; m <= 2 * k; ++m) acc += Pc[m * p + 0] * src[(2 * k * cc + m) * st];
       }
     } else {
       int cc = ca / (2 * k);
       if (cc > Nc - 1) cc = Nc - 1;
       const int m = ca - 2 * k * cc;
-      for (int i = 0; i <= k; ++i) acc += P.Pc[m * p + i] * (double)src[(k * cc + i) * st];
+      for (int i = 0; i <= k; ++i) acc += Pc[m * p + i] * src[(k * cc + i) * st];
     }
     T* dst = dst0 + e;
-    if (accumulate) *dst = (T)((double)*dst + acc);
-    else *dst = (T)acc;
+    if (accumulate) *dst += acc;
+    else *dst = acc;
   }
 }
 

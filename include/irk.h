@@ -74,6 +74,8 @@ typedef struct {
   double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 20) */
   double eig_safety;  /* hi = safety * Lanczos estimate (default 1.2) */
   int shared_cheb;    /* 1: one Chebyshev interval for all blocks (batched mode of Sec. 5.4) */
+  int op_ff;          /* FP64-accurate operator apply: 1 float-float on the FP32 pipe (default,
+                         about 48 significant bits; |values| within 1e-30..1e30), 0 native FP64 */
 } irk_options;
 
 typedef struct {

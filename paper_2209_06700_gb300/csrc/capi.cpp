@@ -69,15 +69,27 @@ CombineParams combine_params(int nout, int nin, const double* Da, const double* 
   return C;
 }
 
+// FP64-accurate operator launch on the fine mesh: float-float (default) or native FP64
+Status launch_apply64(irk_problem* h, const double* u, int ns, const double* cm, const double* ck, int epi,
+                      const EpiParams<double>& E) {
+  if (h->opt.op_ff) {
+    OpParams<ff> P = make_op_params<ff>(h->fine, ns, cm, ck);
+    IRK_LAUNCH(PROF_APPLY64, launch_op<ff>(h->dim, h->k, ns, u, P, epi, E, h->st));
+  } else {
+    OpParams<double> P = make_op_params<double>(h->fine, ns, cm, ck);
+    IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, ns, u, P, epi, E, h->st));
+  }
+  return Status::Ok();
+}
+
 // v = (Cm (x) M + Ck (x) K) u on the fine mesh, FP64, ns stage vectors
 Status apply_general(irk_problem* h, const double* u, double* v, int ns, const double* Cm, const double* Ck) {
   if (ns > h->nslots) return Status::Err(IRK_EINVAL, "too many stage vectors for this handle");
-  OpParams<double> P = make_op_params<double>(h->fine, ns, nullptr, nullptr);
   EpiParams<double> E;
   std::memset(&E, 0, sizeof(E));
   E.out = h->Mu;
   E.out2 = h->Ku;
-  IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, ns, u, P, EPI_DUAL, E, h->st));
+  IRK_TRY(launch_apply64(h, u, ns, nullptr, nullptr, EPI_DUAL, E));
   CombineParams C = combine_params(ns, ns, Cm, Ck, ns);
   IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->Mu, h->Ku, v, h->fine.n, h->fine.ld, C, h->st));
   return Status::Ok();
@@ -144,11 +156,10 @@ Status from_mg(irk_problem* h, MGBase* mg, double* out, double sa, const double*
 Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* loads, double* rhs) {
   const LevelGeom& g = h->fine;
   double zero = 0.0, one = 1.0;
-  OpParams<double> P = make_op_params<double>(g, 1, &zero, &one);
   EpiParams<double> E;
   std::memset(&E, 0, sizeof(E));
   E.out = h->Ky;
-  IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, 1, y, P, EPI_STORE, E, h->st));
+  IRK_TRY(launch_apply64(h, y, 1, &zero, &one, EPI_STORE, E));
   RhsParams R;
   std::memset(&R, 0, sizeof(R));
   R.Q = h->Q;
@@ -395,6 +406,7 @@ void irk_default_options(irk_options* o) {
   o->smoothing_range = 20.0;
   o->eig_safety = 1.2;
   o->shared_cheb = 0;
+  o->op_ff = 1;
 }
 
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,

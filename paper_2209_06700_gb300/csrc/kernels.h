@@ -10,6 +10,14 @@ namespace irk {
 constexpr int kMaxStages = 16;   // per-launch stage slots (Q <= 9, 2x2 DIAG blocks use 2)
 constexpr int kMaxDeg = 4;       // Q_k degree k <= 4
 
+// Float-float value hi + lo (|lo| <= ulp(hi) / 2): about 48 significant bits computed on the
+// FP32 pipe.  Used for the FP64-accurate operator apply; stored in memory as FP64.
+struct ff {
+  float hi, lo;
+};
+template <typename T> struct Storage { using type = T; };
+template <> struct Storage<ff> { using type = double; };
+
 // Geometry and coefficients of one tensor-product operator launch
 //   v_s = cm[s] M u_s + ck[s] K u_s          (s = blockIdx.z, one stage per CTA)
 // M = Mz (x) My (x) Mx, K = Kz My Mx + Mz Ky Mx + Mz My Kx on the uniform mesh;
@@ -22,6 +30,7 @@ struct OpParams {
   int ntile_y;         // 3D: number of y tiles (grid.y = ntile_y * chunks)
   T me[kMaxDeg + 1][kMaxDeg + 1];
   T ke[kMaxDeg + 1][kMaxDeg + 1];
+  T yvm[2 * kMaxDeg + 1], yvk[2 * kMaxDeg + 1];  // banded taps of a vertex row, offsets -k..k
   T cm[kMaxStages], ck[kMaxStages];
 };
 
@@ -44,9 +53,10 @@ struct EpiParams {
 };
 
 // Launch v = op(u) with the given epilogue; dim in {2,3}, k in 1..4, nstage <= kMaxStages.
+// T is the arithmetic type (float, double, ff); vectors are stored as Storage<T>::type.
 template <typename T>
-cudaError_t launch_op(int dim, int k, int nstage, const T* u, const OpParams<T>& P, int epi,
-                      const EpiParams<T>& E, cudaStream_t st);
+cudaError_t launch_op(int dim, int k, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                      int epi, const EpiParams<typename Storage<T>::type>& E, cudaStream_t st);
 
 // Tile shape used by launch_op (cells per CTA in x and y) for a degree k.
 void op_tile_shape(int dim, int k, int* cx, int* cy);
@@ -59,6 +69,7 @@ struct CombineParams {  // out_i = sum_j Da[i][j] a_j (+ sum_j Db[i][j] b_j)
   int nout, nina, ninb;
   double Da[kMaxQ * kMaxQ];
   double Db[kMaxQ * kMaxQ];
+  unsigned nza[kMaxQ], nzb[kMaxQ];  // bit j of row i: coefficient (i, j) is nonzero (set by the launcher)
 };
 // Tin/Tout in {float,double}; a [nina][ld], b [ninb][ld] (may be null), out [nout][ld];
 // n elements per vector are processed.

@@ -55,6 +55,14 @@ LevelGeom make_level(int dim, int k, int N, const Element1D& e) {
   return g;
 }
 
+namespace {
+template <typename T> T from_double(double d) { return (T)d; }
+template <> ff from_double<ff>(double d) {
+  const float hi = (float)d;
+  return ff{hi, (float)(d - (double)hi)};
+}
+}  // namespace
+
 template <typename T>
 OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, const double* ck) {
   OpParams<T> P;
@@ -62,16 +70,29 @@ OpParams<T> make_op_params(const LevelGeom& g, int nstage, const double* cm, con
   P.N = g.N; P.n1 = g.n1; P.ld = g.ld;
   P.zc = 0;  // chosen by the launcher from the occupancy
   P.ntile_y = 1;
+  const int k = g.k;
   for (int i = 0; i <= kMaxDeg; ++i)
-    for (int j = 0; j <= kMaxDeg; ++j) { P.me[i][j] = (T)g.me[i][j]; P.ke[i][j] = (T)g.ke[i][j]; }
+    for (int j = 0; j <= kMaxDeg; ++j) {
+      P.me[i][j] = from_double<T>(g.me[i][j]);
+      P.ke[i][j] = from_double<T>(g.ke[i][j]);
+    }
+  // a vertex row couples to the k nodes of the cell below and above: taps -k..k
+  for (int o = -k; o <= k; ++o) {
+    double a = 0.0, b = 0.0;
+    if (o >= 0) { a += g.me[0][o]; b += g.ke[0][o]; }
+    if (o <= 0) { a += g.me[k][k + o]; b += g.ke[k][k + o]; }
+    P.yvm[o + k] = from_double<T>(a);
+    P.yvk[o + k] = from_double<T>(b);
+  }
   for (int s = 0; s < nstage && s < kMaxStages; ++s) {
-    P.cm[s] = (T)(cm ? cm[s] : 0.0);
-    P.ck[s] = (T)(ck ? ck[s] : 0.0);
+    P.cm[s] = from_double<T>(cm ? cm[s] : 0.0);
+    P.ck[s] = from_double<T>(ck ? ck[s] : 0.0);
   }
   return P;
 }
 template OpParams<float> make_op_params<float>(const LevelGeom&, int, const double*, const double*);
 template OpParams<double> make_op_params<double>(const LevelGeom&, int, const double*, const double*);
+template OpParams<ff> make_op_params<ff>(const LevelGeom&, int, const double*, const double*);
 
 template <typename T>
 DiagParams<T> make_diag_params(const LevelGeom& g, int nstage, const double* cm, const double* ck, const double* c) {

@@ -19,70 +19,137 @@
 //    so that lanes (= cells) touch consecutive words;
 //  * y contraction: banded form with warp-uniform row position r = y mod k;
 //  * x contraction: cell-wise dense (k+1)^2 products per lane, the shared
-//    vertex node merged with the left neighbour by __shfl_up_sync;
+//    vertex node merged with the left neighbour by a warp shuffle;
 //  * z contraction: cell-wise "push" into k+1 register accumulators per
 //    owned node; a z-cell's k planes are complete, and emitted through the
 //    fused epilogue, once its upper vertex plane has been pushed.
 // Boundary nodes (homogeneous Dirichlet) are read as zero and never written.
+//
+// Arithmetic goes through dev::mad / mul / add so that one body serves FP32
+// (multigrid), FP64 and float-float (T = ff: FP64-accurate apply on the FP32
+// pipe, inputs split hi/lo on load, outputs merged to FP64 on store).
 #pragma once
 #include "kernels.h"
 
 namespace irk {
 namespace dev {
 
-template <typename T>
-__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+// ---------------------------------------------------------------- arithmetic helpers
+template <typename T> __device__ __forceinline__ T zero() { return T(0); }
+template <> __device__ __forceinline__ ff zero<ff>() { return ff{0.f, 0.f}; }
 
-// Epilogue for one interior output node (stage s, linear index idx in the stage vector).
-template <typename T, int EPI, int K, int DIM>
-__device__ __forceinline__ void epilogue(const EpiParams<T>& E, long long o, int x, int y, int z,
-                                         T cm, T ck, int s, T va, T vb) {
+// float-float: error-free sums with the round-to-nearest intrinsics (never contracted into FMA)
+__device__ __forceinline__ ff ff_renorm(float s, float e) {
+  const float hi = __fadd_rn(s, e);
+  return ff{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ff_renorm(s, e);
+}
+// a + c v: the product c.hi v.hi is split exactly by an FMA, the cross terms are plain FP32
+__device__ __forceinline__ ff ff_mad(ff a, ff c, ff v) {
+  const float p = __fmul_rn(c.hi, v.hi);
+  float pe = __fmaf_rn(c.hi, v.hi, -p);
+  pe = __fmaf_rn(c.hi, v.lo, pe);
+  pe = __fmaf_rn(c.lo, v.hi, pe);
+  const float s = __fadd_rn(a.hi, p);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, pe));
+  return ff_renorm(s, e);
+}
+__device__ __forceinline__ ff ff_mul(ff c, ff v) {
+  const float p = __fmul_rn(c.hi, v.hi);
+  float pe = __fmaf_rn(c.hi, v.hi, -p);
+  pe = __fmaf_rn(c.hi, v.lo, pe);
+  pe = __fmaf_rn(c.lo, v.hi, pe);
+  return ff_renorm(p, pe);
+}
+
+__device__ __forceinline__ float mad(float a, float c, float v) { return fmaf(c, v, a); }
+__device__ __forceinline__ double mad(double a, double c, double v) { return fma(c, v, a); }
+__device__ __forceinline__ ff mad(ff a, ff c, ff v) { return ff_mad(a, c, v); }
+__device__ __forceinline__ float mul(float c, float v) { return c * v; }
+__device__ __forceinline__ double mul(double c, double v) { return c * v; }
+__device__ __forceinline__ ff mul(ff c, ff v) { return ff_mul(c, v); }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff add(ff a, ff b) { return ff_add(a, b); }
+
+__device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ ff shfl_up(ff v) {
+  return ff{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
+}
+
+// load from storage (FP64 values are split into hi + lo for ff) and store back
+template <typename T> __device__ __forceinline__ T load(const typename Storage<T>::type* p) { return __ldg(p); }
+template <> __device__ __forceinline__ ff load<ff>(const double* p) {
+  const double d = __ldg(p);
+  const float hi = __double2float_rn(d);
+  return ff{hi, __double2float_rn(d - (double)hi)};
+}
+__device__ __forceinline__ float to_storage(float v) { return v; }
+__device__ __forceinline__ double to_storage(double v) { return v; }
+__device__ __forceinline__ double to_storage(ff v) { return (double)v.hi + (double)v.lo; }
+
+// ---------------------------------------------------------------- epilogues
+// One interior output node (stage s, flat offset o).  CHEB needs invD = 1/diag(cm M + ck K).
+template <typename T, int EPI>
+__device__ __forceinline__ void epilogue(const EpiParams<typename Storage<T>::type>& E, long long o, int s, T va,
+                                         T vb, typename Storage<T>::type invD) {
   if constexpr (EPI == EPI_STORE) {
-    E.out[o] = va;
+    E.out[o] = to_storage(va);
   } else if constexpr (EPI == EPI_DUAL) {
-    E.out[o] = va;
-    E.out2[o] = vb;
+    E.out[o] = to_storage(va);
+    E.out2[o] = to_storage(vb);
   } else if constexpr (EPI == EPI_RESID) {
-    E.out[o] = E.b[o] - va;
-  } else {  // EPI_CHEB
-    const int rx = x % K, ry = y % K;
-    T dmx = E.dmr[rx], dmy = E.dmr[ry], dkx = E.dkr[rx], dky = E.dkr[ry];
-    T D;
-    if constexpr (DIM == 3) {
-      const int rz = z % K;
-      T dmz = E.dmr[rz], dkz = E.dkr[rz];
-      D = cm * (dmx * dmy * dmz) + ck * (dkx * dmy * dmz + dmx * dky * dmz + dmx * dmy * dkz);
-    } else {
-      D = cm * (dmx * dmy) + ck * (dkx * dmy + dmx * dky);
-    }
-    const T xv = E.xj[o];
-    const T xo = E.xold_zero ? T(0) : E.out[o];
-    const T c1 = E.c1[s];
-    const T upd = (c1 != T(0)) ? c1 * (xv - xo) : T(0);
-    E.out[o] = xv + upd + E.c2[s] * (E.b[o] - va) / D;
+    E.out[o] = E.b[o] - to_storage(va);
+  } else {  // EPI_CHEB (float / double)
+    using S = typename Storage<T>::type;
+    const S xv = E.xj[o];
+    const S bv = E.b[o];
+    const S c1 = E.c1[s];
+    S upd = S(0);
+    if (!E.xold_zero && c1 != S(0)) upd = c1 * (xv - E.out[o]);
+    E.out[o] = xv + upd + E.c2[s] * (bv - to_storage(va)) * invD;
   }
 }
 
-// y-direction banded taps for output row position R (compile time); col points at
-// the output row in the staged input column, stride = row stride.
+// 1 / diag(cm M + ck K) at a node with positions (rx, ry, rz) = (x, y, z) mod k inside the cell.
+template <typename S, int DIM>
+__device__ __forceinline__ S inv_diag(const EpiParams<S>& E, S cm, S ck, int rx, int ry, int rz) {
+  const S dmx = E.dmr[rx], dmy = E.dmr[ry], dkx = E.dkr[rx], dky = E.dkr[ry];
+  if constexpr (DIM == 3) {
+    const S dmz = E.dmr[rz], dkz = E.dkr[rz];
+    return S(1) / (cm * (dmx * dmy * dmz) + ck * (dkx * dmy * dmz + dmx * dky * dmz + dmx * dmy * dkz));
+  } else {
+    return S(1) / (cm * (dmx * dmy) + ck * (dkx * dmy + dmx * dky));
+  }
+}
+
+// ---------------------------------------------------------------- 1D contractions
+// y-direction banded taps for output row position R (compile time); col points at the
+// output row in the staged input column, stride = row stride.
 template <typename T, int K, int R>
 __device__ __forceinline__ void ytaps(const T* col, int stride, const OpParams<T>& P, T& g, T& h) {
   if constexpr (R == 0) {
 #pragma unroll
     for (int o = -K; o <= K; ++o) {
-      T a = T(0), b = T(0);
-      if (o >= 0) { a += P.me[0][o]; b += P.ke[0][o]; }
-      if (o <= 0) { a += P.me[K][K + o]; b += P.ke[K][K + o]; }
       const T v = col[o * stride];
-      g += a * v;
-      h += b * v;
+      g = mad(g, P.yvm[o + K], v);
+      h = mad(h, P.yvk[o + K], v);
     }
   } else {
 #pragma unroll
     for (int m = 0; m <= K; ++m) {
       const T v = col[(m - R) * stride];
-      g += P.me[R][m] * v;
-      h += P.ke[R][m] * v;
+      g = mad(g, P.me[R][m], v);
+      h = mad(h, P.ke[R][m], v);
     }
   }
 }
@@ -111,12 +178,12 @@ __device__ __forceinline__ void xcell(const T* g, const T* h, int cl, const OpPa
   if constexpr (MODE3) hv[K] = h[cl + 1];
 #pragma unroll
   for (int mo = 0; mo <= K; ++mo) {
-    T a = T(0), b = T(0);
+    T a = zero<T>(), b = zero<T>();
 #pragma unroll
     for (int m = 0; m <= K; ++m) {
-      a += P.me[mo][m] * gv[m];
-      b += P.ke[mo][m] * gv[m];
-      if constexpr (MODE3) b += P.me[mo][m] * hv[m];
+      a = mad(a, P.me[mo][m], gv[m]);
+      b = mad(b, P.ke[mo][m], gv[m]);
+      if constexpr (MODE3) b = mad(b, P.me[mo][m], hv[m]);
     }
     r[mo] = a;
     p[mo] = b;
@@ -126,14 +193,14 @@ __device__ __forceinline__ void xcell(const T* g, const T* h, int cl, const OpPa
 // Top-vertex outputs (local node K) of the cell at staged column cl.
 template <typename T, int K, bool MODE3, int CW>
 __device__ __forceinline__ void xcell_top(const T* g, const T* h, int cl, const OpParams<T>& P, T& r, T& p) {
-  T a = T(0), b = T(0);
+  T a = zero<T>(), b = zero<T>();
 #pragma unroll
   for (int m = 0; m <= K; ++m) {
     const int slot = (m < K) ? (m * CW + cl) : (cl + 1);
     const T gv = g[slot];
-    a += P.me[K][m] * gv;
-    b += P.ke[K][m] * gv;
-    if constexpr (MODE3) b += P.me[K][m] * h[slot];
+    a = mad(a, P.me[K][m], gv);
+    b = mad(b, P.ke[K][m], gv);
+    if constexpr (MODE3) b = mad(b, P.me[K][m], h[slot]);
   }
   r = a;
   p = b;
@@ -148,14 +215,14 @@ __device__ __forceinline__ void zpush(const OpParams<T>& P, T cm, T ck, const T 
     if constexpr (DUAL) {
 #pragma unroll
       for (int mo = 0; mo <= K; ++mo) {
-        accA[m][mo] += P.me[mo][RZ] * R[m];
-        accB[m][mo] += P.me[mo][RZ] * Pp[m] + P.ke[mo][RZ] * R[m];
+        accA[m][mo] = mad(accA[m][mo], P.me[mo][RZ], R[m]);
+        accB[m][mo] = mad(mad(accB[m][mo], P.me[mo][RZ], Pp[m]), P.ke[mo][RZ], R[m]);
       }
     } else {
-      const T F = cm * R[m] + ck * Pp[m];
-      const T Ez = ck * R[m];
+      const T F = mad(mul(cm, R[m]), ck, Pp[m]);
+      const T Ez = mul(ck, R[m]);
 #pragma unroll
-      for (int mo = 0; mo <= K; ++mo) accA[m][mo] += P.me[mo][RZ] * F + P.ke[mo][RZ] * Ez;
+      for (int mo = 0; mo <= K; ++mo) accA[m][mo] = mad(mad(accA[m][mo], P.me[mo][RZ], F), P.ke[mo][RZ], Ez);
     }
   }
 }
@@ -168,20 +235,46 @@ __device__ __forceinline__ void carry(T (&accA)[K][K + 1], T (&accB)[K][K + 1]) 
     if constexpr (DUAL) accB[m][0] = accB[m][K];
 #pragma unroll
     for (int mo = 1; mo <= K; ++mo) {
-      accA[m][mo] = T(0);
-      if constexpr (DUAL) accB[m][mo] = T(0);
+      accA[m][mo] = zero<T>();
+      if constexpr (DUAL) accB[m][mo] = zero<T>();
     }
+  }
+}
+
+// push of the plane with in-cell position r (0..K-1) into the accumulators; at a vertex plane
+// (r = 0) the cell below is completed first (column K), emitted, and its top vertex carried.
+template <typename T, int K, bool DUAL, class Emit>
+__device__ __forceinline__ void zstep(int r, int c, int cstart, int c0, const OpParams<T>& P, T cm, T ck,
+                                      const T (&R)[K], const T (&Pp)[K], T (&accA)[K][K + 1], T (&accB)[K][K + 1],
+                                      Emit&& emit) {
+  if (r == 0) {
+    if (c > cstart) {
+      zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
+      if (c - 1 >= c0) emit(c - 1);
+      carry<T, K, DUAL>(accA, accB);
+    }
+    zpush<T, K, 0, DUAL>(P, cm, ck, R, Pp, accA, accB);
+  } else if (r == 1) {
+    zpush<T, K, (1 < K ? 1 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
+  } else if (r == 2) {
+    zpush<T, K, (2 < K ? 2 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
+  } else {
+    zpush<T, K, (3 < K ? 3 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
   }
 }
 
 }  // namespace dev
 
 template <int K> struct Tile3D { static constexpr int CY = (K == 1) ? 8 : (K == 2) ? 4 : 2; };
+// resident CTAs per SM requested from the register allocator (FP32: 3 -> 24 warps per SM)
+template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 1; };
 
 // ---------------------------------------------------------------- 3D kernel
 template <typename T, int K, int EPI>
-__global__ void __launch_bounds__(32 * K * Tile3D<K>::CY)
-op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) {
+__global__ void __launch_bounds__(32 * K * Tile3D<K>::CY, MinBlocks<T>::value)
+op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
+            const EpiParams<typename Storage<T>::type> E) {
+  using S = typename Storage<T>::type;
   constexpr int CY = Tile3D<K>::CY;
   constexpr int CX = 32, TY = K * CY, NT = 32 * TY;
   constexpr int CW = CX + 2, SL = K * CW;
@@ -192,6 +285,7 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   __shared__ T su[HY * SL];
   __shared__ T sg[TY * SL];
   __shared__ T sh[TY * SL];
+  __shared__ S sinvd[(EPI == EPI_CHEB) ? K * K * K : 1];  // 1/D by (x, y, z) mod k
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = P.N, n1 = P.n1;
@@ -199,7 +293,7 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   const int ty = blockIdx.y % P.ntile_y, zchunk = blockIdx.y / P.ntile_y;
   const int y0 = K * CY * ty, x0 = K * cx0;
   const int s = blockIdx.z;
-  const T* __restrict__ us = u + (long long)s * P.ld;
+  const S* __restrict__ us = u + (long long)s * P.ld;
   const T cm = P.cm[s], ck = P.ck[s];
   const int c0 = zchunk * P.zc;
   if (c0 >= N) return;
@@ -207,7 +301,13 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   const int cstart = max(c0 - 1, 0);
   const long long plane = (long long)n1 * n1;
 
-  for (int i = tid; i < HY * SL; i += NT) su[i] = T(0);  // padding slots stay zero
+  for (int i = tid; i < HY * SL; i += NT) su[i] = dev::zero<T>();  // padding slots stay zero
+  if constexpr (EPI == EPI_CHEB) {
+    if (tid < K * K * K) {
+      const int rx = tid % K, ry = (tid / K) % K, rz = tid / (K * K);
+      sinvd[tid] = dev::inv_diag<S, 3>(E, (S)P.cm[s], (S)P.ck[s], rx, ry, rz);
+    }
+  }
 
   // per-thread load slots: global offset within a plane (or -1) and shared slot
   int goff[PF], soff[PF];
@@ -226,9 +326,9 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   }
   T pf[PF];
   auto load_plane = [&](int zp) {
-    const T* base = us + zp * plane;
+    const S* base = us + zp * plane;
 #pragma unroll
-    for (int q = 0; q < PF; ++q) pf[q] = (goff[q] >= 0) ? dev::ldg(base + goff[q]) : T(0);
+    for (int q = 0; q < PF; ++q) pf[q] = (goff[q] >= 0) ? dev::load<T>(base + goff[q]) : dev::zero<T>();
   };
   auto store_plane = [&]() {
 #pragma unroll
@@ -239,7 +339,7 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
     const int ro = w % K;
     const T* colbase = su + (w + K) * SL;
     for (int sl = lane; sl < SL; sl += 32) {
-      T g = T(0), h = T(0);
+      T g = dev::zero<T>(), h = dev::zero<T>();
       dev::ytaps_dispatch<T, K>(ro, colbase + sl, SL, P, g, h);
       sg[w * SL + sl] = g;
       sh[w * SL + sl] = h;
@@ -250,11 +350,11 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
     const T* h = sh + w * SL;
     T r[K + 1], p[K + 1];
     dev::xcell<T, K, true, CW>(g, h, lane + 1, P, r, p);
-    T rl = __shfl_up_sync(0xffffffffu, r[K], 1);
-    T pl = __shfl_up_sync(0xffffffffu, p[K], 1);
+    T rl = dev::shfl_up(r[K]);
+    T pl = dev::shfl_up(p[K]);
     if (lane == 0) dev::xcell_top<T, K, true, CW>(g, h, 0, P, rl, pl);
-    r[0] += rl;
-    p[0] += pl;
+    r[0] = dev::add(r[0], rl);
+    p[0] = dev::add(p[0], pl);
 #pragma unroll
     for (int m = 0; m < K; ++m) { R[m] = r[m]; Pp[m] = p[m]; }
   };
@@ -265,7 +365,7 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
 #pragma unroll
   for (int m = 0; m < K; ++m)
 #pragma unroll
-    for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = T(0); accB[m][mo] = T(0); }
+    for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = dev::zero<T>(); accB[m][mo] = dev::zero<T>(); }
 
   auto emit = [&](int cz) {
     if (!row_ok) return;
@@ -278,8 +378,9 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
         const int x = K * cell + m;
         if (x < 1) continue;
         const long long idx = ((long long)z * n1 + yrow) * n1 + x;
-        dev::epilogue<T, EPI, K, 3>(E, (long long)s * P.ld + idx, x, yrow, z, cm, ck, s, accA[m][mo],
-                                    accB[m][mo]);
+        S invD = S(0);
+        if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
+        dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, accA[m][mo], accB[m][mo], invD);
       }
     }
   };
@@ -297,19 +398,7 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
       __syncthreads();
       T R[K], Pp[K];
       xpass(R, Pp);
-      if (r == 0) {
-        if (c > cstart) {
-          dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
-          if (c - 1 >= c0) emit(c - 1);
-          dev::carry<T, K, DUAL>(accA, accB);
-        }
-        dev::zpush<T, K, 0, DUAL>(P, cm, ck, R, Pp, accA, accB);
-      } else {
-        // r is a compile-time constant after unrolling
-        if (r == 1) dev::zpush<T, K, (1 < K ? 1 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-        if constexpr (K > 2) if (r == 2) dev::zpush<T, K, (2 < K ? 2 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-        if constexpr (K > 3) if (r == 3) dev::zpush<T, K, (3 < K ? 3 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-      }
+      dev::zstep<T, K, DUAL>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
     }
   }
   // upper vertex plane of the last cell
@@ -329,7 +418,9 @@ op3d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
 // Plane = one x row; streaming along y.  NW warps, 32*NW cells per tile in x.
 template <typename T, int K, int EPI>
 __global__ void __launch_bounds__(64)
-op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) {
+op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
+            const EpiParams<typename Storage<T>::type> E) {
+  using S = typename Storage<T>::type;
   constexpr int NW = 2, NT = 32 * NW;
   constexpr int CX = 32 * NW, CW = CX + 2, SL = K * CW;
   constexpr int HX = K * CX + K + 1;
@@ -341,14 +432,14 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   const int N = P.N, n1 = P.n1;
   const int cx0 = blockIdx.x * CX, x0 = K * cx0;
   const int s = blockIdx.z;
-  const T* __restrict__ us = u + (long long)s * P.ld;
+  const S* __restrict__ us = u + (long long)s * P.ld;
   const T cm = P.cm[s], ck = P.ck[s];
   const int c0 = blockIdx.y * P.zc;
   if (c0 >= N) return;
   const int c1 = min(N, c0 + P.zc);
   const int cstart = max(c0 - 1, 0);
 
-  for (int i = tid; i < SL; i += NT) su[i] = T(0);
+  for (int i = tid; i < SL; i += NT) su[i] = dev::zero<T>();
   int goff[PF], soff[PF];
 #pragma unroll
   for (int q = 0; q < PF; ++q) {
@@ -364,9 +455,9 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   }
   T pf[PF];
   auto load_row = [&](int yp) {
-    const T* base = us + (long long)yp * n1;
+    const S* base = us + (long long)yp * n1;
 #pragma unroll
-    for (int q = 0; q < PF; ++q) pf[q] = (goff[q] >= 0) ? dev::ldg(base + goff[q]) : T(0);
+    for (int q = 0; q < PF; ++q) pf[q] = (goff[q] >= 0) ? dev::load<T>(base + goff[q]) : dev::zero<T>();
   };
   auto store_row = [&]() {
 #pragma unroll
@@ -377,11 +468,11 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
   auto xpass = [&](T (&R)[K], T (&Pp)[K]) {
     T r[K + 1], p[K + 1];
     dev::xcell<T, K, false, CW>(su, su, cl, P, r, p);
-    T rl = __shfl_up_sync(0xffffffffu, r[K], 1);
-    T pl = __shfl_up_sync(0xffffffffu, p[K], 1);
+    T rl = dev::shfl_up(r[K]);
+    T pl = dev::shfl_up(p[K]);
     if (lane == 0) dev::xcell_top<T, K, false, CW>(su, su, cl - 1, P, rl, pl);
-    r[0] += rl;
-    p[0] += pl;
+    r[0] = dev::add(r[0], rl);
+    p[0] = dev::add(p[0], pl);
 #pragma unroll
     for (int m = 0; m < K; ++m) { R[m] = r[m]; Pp[m] = p[m]; }
   };
@@ -391,7 +482,7 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
 #pragma unroll
   for (int m = 0; m < K; ++m)
 #pragma unroll
-    for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = T(0); accB[m][mo] = T(0); }
+    for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = dev::zero<T>(); accB[m][mo] = dev::zero<T>(); }
   auto emit = [&](int cyc) {
     if (!col_ok) return;
 #pragma unroll
@@ -403,8 +494,9 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
         const int x = K * cell + m;
         if (x < 1) continue;
         const long long idx = (long long)y * n1 + x;
-        dev::epilogue<T, EPI, K, 2>(E, (long long)s * P.ld + idx, x, y, 0, cm, ck, s, accA[m][mo],
-                                    accB[m][mo]);
+        S invD = S(0);
+        if constexpr (EPI == EPI_CHEB) invD = dev::inv_diag<S, 2>(E, (S)P.cm[s], (S)P.ck[s], m, mo, 0);
+        dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, accA[m][mo], accB[m][mo], invD);
       }
     }
   };
@@ -420,18 +512,7 @@ op2d_kernel(const T* __restrict__ u, const OpParams<T> P, const EpiParams<T> E) 
       load_row(yp + 1);
       T R[K], Pp[K];
       xpass(R, Pp);
-      if (r == 0) {
-        if (c > cstart) {
-          dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
-          if (c - 1 >= c0) emit(c - 1);
-          dev::carry<T, K, DUAL>(accA, accB);
-        }
-        dev::zpush<T, K, 0, DUAL>(P, cm, ck, R, Pp, accA, accB);
-      } else {
-        if (r == 1) dev::zpush<T, K, (1 < K ? 1 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-        if constexpr (K > 2) if (r == 2) dev::zpush<T, K, (2 < K ? 2 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-        if constexpr (K > 3) if (r == 3) dev::zpush<T, K, (3 < K ? 3 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
-      }
+      dev::zstep<T, K, DUAL>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
     }
   }
   __syncthreads();
@@ -479,8 +560,8 @@ inline int pick_zc(int N, long long base_ctas, long long slots, int K) {
 }
 
 template <typename T, int K, int EPI>
-cudaError_t launch_op_k(int dim, int nstage, const T* u, const OpParams<T>& P, const EpiParams<T>& E,
-                        cudaStream_t st) {
+cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                        const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
   int cx, cy;
   op_tile_shape_impl(dim, K, &cx, &cy);
   const int ntx = (P.N + cx - 1) / cx;
@@ -512,8 +593,8 @@ cudaError_t launch_op_k(int dim, int nstage, const T* u, const OpParams<T>& P, c
 }
 
 template <typename T, int EPI>
-cudaError_t launch_op_e(int dim, int k, int nstage, const T* u, const OpParams<T>& P, const EpiParams<T>& E,
-                        cudaStream_t st) {
+cudaError_t launch_op_e(int dim, int k, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                        const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
   switch (k) {
     case 1: return launch_op_k<T, 1, EPI>(dim, nstage, u, P, E, st);
     case 2: return launch_op_k<T, 2, EPI>(dim, nstage, u, P, E, st);

@@ -71,13 +71,12 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const Tin* __restrict
     for (int i = 0; i < NMAX; ++i) {
       if (i < C.nout) {
         double acc = 0.0;
-        // zero coefficients (triangular S~, diagonal stiffness coupling) are skipped: FP64 issue
-        // slots are scarce on this part, and the branches are uniform across the grid
+        // zero coefficients (triangular S~, diagonal stiffness coupling) are skipped through
+        // host-built integer masks: FP64 instructions, compares included, are scarce on this part
 #pragma unroll
         for (int j = 0; j < NMAX; ++j) {
-          const double ca = C.Da[i * kMaxQ + j], cb = C.Db[i * kMaxQ + j];
-          if (ca != 0.0) acc += ca * av[j];
-          if (cb != 0.0) acc += cb * bv[j];
+          if ((C.nza[i] >> j) & 1u) acc += C.Da[i * kMaxQ + j] * av[j];
+          if ((C.nzb[i] >> j) & 1u) acc += C.Db[i * kMaxQ + j] * bv[j];
         }
         out[i * ld + e] = (Tout)acc;
       }
@@ -448,12 +447,14 @@ cudaError_t launch_combine(const Tin* a, const double* b, Tout* out, long long n
                            cudaStream_t st) {
   const int nmax = std::max(C.nout, std::max(C.nina, C.ninb));
   const int grid = blocks_for(n, 2);
-  CombineParams Cz = C;  // unused coefficients must be zero: the kernel multiplies every slot
-  for (int i = 0; i < kMaxQ; ++i)
+  CombineParams Cz = C;
+  for (int i = 0; i < kMaxQ; ++i) {
+    Cz.nza[i] = Cz.nzb[i] = 0u;
     for (int j = 0; j < kMaxQ; ++j) {
-      if (i >= C.nout || j >= C.nina) Cz.Da[i * kMaxQ + j] = 0.0;
-      if (i >= C.nout || j >= C.ninb) Cz.Db[i * kMaxQ + j] = 0.0;
+      if (i < C.nout && j < C.nina && C.Da[i * kMaxQ + j] != 0.0) Cz.nza[i] |= 1u << j;
+      if (i < C.nout && j < C.ninb && C.Db[i * kMaxQ + j] != 0.0) Cz.nzb[i] |= 1u << j;
     }
+  }
   if (nmax <= 1) combine_kernel<Tin, Tout, 1><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
   else if (nmax <= 2) combine_kernel<Tin, Tout, 2><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
   else if (nmax <= 3) combine_kernel<Tin, Tout, 3><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);

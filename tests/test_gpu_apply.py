@@ -29,10 +29,12 @@ def _inputs(Q, dim, n1, seed=0):
 
 
 @pytest.mark.parametrize("dim,N,k,Q", CASES)
-def test_calA_apply(dim, N, k, Q):
+@pytest.mark.parametrize("op_ff", [1, 0])
+def test_calA_apply(dim, N, k, Q, op_ff):
+    """Float-float (default) and native FP64 evaluation of the operator, both <= 1e-12."""
     tau = 1e-2
     prob = Problem(dim, N, k, Q, tau)
-    with pkg.Solver(dim, N, k, Q, tau) as s:
+    with pkg.Solver(dim, N, k, Q, tau, op_ff=op_ff) as s:
         u = _inputs(Q, dim, k * N + 1)
         ud = to_dev(s, u)
         vd = torch.zeros_like(ud)
@@ -72,11 +74,12 @@ def test_boundary_entries_untouched():
 
 
 @pytest.mark.slow
-def test_calA_apply_full_size():
+@pytest.mark.parametrize("op_ff", [1, 0])
+def test_calA_apply_full_size(op_ff):
     """The bench workload (3D, k=4, 32^3 cells, Q=3), every output compared."""
     w = HEAT3D_K4_N32_Q3
     prob = Problem(w.dim, w.cells, w.degree, w.Q, w.tau)
-    with pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau) as s:
+    with pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, op_ff=op_ff) as s:
         u = _inputs(w.Q, w.dim, w.n1, seed=11)
         ud = to_dev(s, u)
         vd = torch.zeros_like(ud)
@@ -84,3 +87,20 @@ def test_calA_apply_full_size():
         got = from_dev(vd, s.n)
     ref = apply_calA(prob, u)
     assert rel_err(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("op_ff", [1, 0])
+def test_calA_apply_smooth_input(op_ff):
+    """Smooth input (the initial interpolant per stage): the stiffness part cancels strongly."""
+    from oracle.heat import initial_value
+    from oracle.fem import Mesh
+    dim, N, k, Q, tau = 3, 16, 3, 3, 1e-3
+    prob = Problem(dim, N, k, Q, tau)
+    y = initial_value(Mesh(dim, N, k))
+    u = np.stack([y * (1.0 + 0.1 * i) for i in range(Q)])
+    with pkg.Solver(dim, N, k, Q, tau, op_ff=op_ff) as s:
+        ud = to_dev(s, u)
+        vd = torch.zeros_like(ud)
+        s.apply(ud, vd)
+        got = from_dev(vd, s.n)
+    assert rel_err(got, apply_calA(prob, u)) <= TOL

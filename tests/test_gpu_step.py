@@ -93,7 +93,7 @@ def test_step_lu_fp32_mg(dim, N, k, Q, tau):
 
 
 @pytest.mark.parametrize("opts", [dict(mg_precision=64), dict(batched=0), dict(mg_precision=64, batched=0),
-                                  dict(shared_cheb=1), dict(cheb_degree=5)])
+                                  dict(shared_cheb=1), dict(cheb_degree=5), dict(op_ff=0)])
 def test_step_variants_of_the_lu_path(opts):
     err, its = _run(3, 8, 3, 3, 1e-3, nsteps=2, **opts)
     assert err <= YTOL, (err, its, opts)

@@ -110,11 +110,11 @@ Status precondition_lu(irk_problem* h, const double* r, double* z) {
   CombineParams Cout = combine_params(Q, Q, h->tab.S.data());
   if (h->mg->elem_size() == 4) {
     IRK_LAUNCH(PROF_COMBINE, launch_combine<double, float>(r, nullptr, (float*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
-    IRK_TRY(h->mg->vcycle(0, h->st));
+    IRK_TRY(h->mg->vcycle_top(h->st, h->opt.use_graph != 0));
     IRK_LAUNCH(PROF_COMBINE, launch_combine<float, double>((const float*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
   } else {
     IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(r, nullptr, (double*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
-    IRK_TRY(h->mg->vcycle(0, h->st));
+    IRK_TRY(h->mg->vcycle_top(h->st, h->opt.use_graph != 0));
     IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>((const double*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
   }
   return Status::Ok();
@@ -218,7 +218,7 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
       };
       prec = [h, mg](const double* in, double* out) {
         IRK_TRY(to_mg(h, mg, in, 1.0, nullptr, 0.0));
-        IRK_TRY(mg->vcycle(0, h->st));
+        IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
         return from_mg(h, mg, out, 1.0, nullptr, 0.0);
       };
     } else {
@@ -234,13 +234,13 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
         double* o1 = out;
         double* o2 = out + gg.ld;
         IRK_TRY(to_mg(h, mg, f, 1.0, gv, 1.0));
-        IRK_TRY(mg->vcycle(0, h->st));
+        IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
         IRK_TRY(from_mg(h, mg, o1, 1.0, nullptr, 0.0));        // o1 = w1
         // b2 = g - beta M w1: M w1 in FP64 through the fine operator (ns = 1)
         const double Cm[1] = {be}, Ck[1] = {0.0};
         IRK_TRY(apply_general(h, o1, o2, 1, Cm, Ck));          // o2 = beta M w1
         IRK_TRY(to_mg(h, mg, gv, 1.0, o2, -1.0));
-        IRK_TRY(mg->vcycle(0, h->st));
+        IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
         IRK_TRY(from_mg(h, mg, o2, 1.0, nullptr, 0.0));        // o2 = w2
         return from_mg(h, mg, o1, -1.0, o1, 1.0);              // o1 = w1 - w2
       };

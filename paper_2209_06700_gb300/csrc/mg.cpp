@@ -282,6 +282,42 @@ class MG final : public MGBase {
     return Status::Ok();
   }
 
+  ~MG() override {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (graph_) cudaGraphDestroy(graph_);
+  }
+
+  Status vcycle_top(cudaStream_t st, bool allow_graph) override {
+    const unsigned mg_mask = (1u << PROF_MG_OP) | (1u << PROF_MG_OP_FINE) | (1u << PROF_MG_POINT) |
+                             (1u << PROF_TRANSFER) | (1u << PROF_COARSE);
+    const bool timing = g_prof && (g_prof->mask & mg_mask);
+    if (!allow_graph || st == nullptr || timing || eager_runs_ < 1) {
+      ++eager_runs_;
+      return vcycle(0, st);
+    }
+    if (!gexec_) {
+      Profiler counter;  // counts the captured launches per category
+      counter.st = st;
+      ProfBind bind(&counter);
+      IRK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+      Status s = vcycle(0, st);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (!s.ok()) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      IRK_CUDA(e);
+      graph_ = g;
+      IRK_CUDA(cudaGraphInstantiate(&gexec_, graph_, 0));
+      for (int c = 0; c < PROF_NCAT; ++c) gcounts_[c] = counter.launches[c];
+    }
+    IRK_CUDA(cudaGraphLaunch(gexec_, st));
+    if (g_prof)
+      for (int c = 0; c < PROF_NCAT; ++c) g_prof->launches[c] += gcounts_[c];
+    return Status::Ok();
+  }
+
   Status vcycle_io(int l, const void* b, void* x, cudaStream_t st) override {
     Lvl& L = lv_[l];
     const size_t bytes = (size_t)cfg_.nb * L.g.ld * sizeof(T);
@@ -711,6 +747,10 @@ class MG final : public MGBase {
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
   int nci_ = 0;
+  cudaGraph_t graph_ = nullptr;
+  cudaGraphExec_t gexec_ = nullptr;
+  long long gcounts_[PROF_NCAT] = {};
+  int eager_runs_ = 0;
   static constexpr int kDenseCoarseMax = 729;  // dense inverse up to 9^3 unknowns, else fast diagonalisation
   bool use_fd_ = false;
   double *fd_V_ = nullptr, *fd_Vt_ = nullptr, *fd_mu_ = nullptr, *fd_t1_ = nullptr, *fd_t2_ = nullptr;

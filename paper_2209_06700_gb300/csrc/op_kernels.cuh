@@ -114,8 +114,8 @@ __device__ __forceinline__ void epilogue(const EpiParams<typename Storage<T>::ty
     const S xv = E.xj[o];
     const S bv = E.b[o];
     const S c1 = E.c1[s];
-    S upd = S(0);
-    if (!E.xold_zero && c1 != S(0)) upd = c1 * (xv - E.out[o]);
+    S upd = S(0);  // momentum c1 (x_j - x_{j-1}); x_{j-1} = 0 when xold_zero
+    if (c1 != S(0)) upd = c1 * (xv - (E.xold_zero ? S(0) : E.out[o]));
     E.out[o] = xv + upd + E.c2[s] * (bv - to_storage(va)) * invD;
   }
 }

@@ -73,6 +73,9 @@ class MGBase {
   virtual void* fine_b() = 0;
   virtual void* fine_x() = 0;          // result of the last vcycle on level 0
   virtual Status vcycle(int level, cudaStream_t st) = 0;  // b_level -> x_level
+  // V-cycle from the finest level; replayed from a captured CUDA graph when allowed (non-default
+  // stream, no per-kernel timing requested), after one eager run.
+  virtual Status vcycle_top(cudaStream_t st, bool allow_graph) = 0;
   virtual Status vcycle_io(int level, const void* b, void* x, cudaStream_t st) = 0;
   virtual Status smooth(int level, const void* b, void* x, int x_is_zero, cudaStream_t st) = 0;
   virtual Status residual(int level, const void* b, const void* x, void* r, cudaStream_t st) = 0;

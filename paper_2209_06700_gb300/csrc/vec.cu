@@ -278,6 +278,88 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const double* __res
   }
 }
 
+// Basis sizes up to 8: fully unrolled, one pass over the basis per kernel; in MODE 1 the
+// basis values loaded for the update are reused for the dot products.
+template <int MODE, int NV>
+__global__ void __launch_bounds__(kThreads) gs_small_kernel(const double* __restrict__ V, long long vstride,
+                                                            const double* __restrict__ h,
+                                                            const double* __restrict__ w_in,
+                                                            double* __restrict__ w_out, int n,
+                                                            double* __restrict__ partial, int nb) {
+  double hr[NV];
+  if (MODE == 1) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) hr[i] = h[i];
+  }
+  double acc[NV + 1];
+#pragma unroll
+  for (int i = 0; i <= NV; ++i) acc[i] = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double vv[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) vv[i] = V[i * vstride + e];
+    double we = w_in[e];
+    if (MODE == 1) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) we -= hr[i] * vv[i];
+      w_out[e] = we;
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += vv[i] * we;
+    acc[NV] += we * we;
+  }
+  __shared__ double sred[NV + 1][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g <= NV; ++g) {
+    double x = acc[g];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) sred[g][warp] = x;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x <= NV) {
+    double x = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) x += sred[threadIdx.x][q];
+    partial[(long long)threadIdx.x * nb + blockIdx.x] = x;
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kThreads) gs_reorth_small_kernel(const double* __restrict__ V, long long vstride,
+                                                                   const double* __restrict__ h,
+                                                                   const double* __restrict__ w_in,
+                                                                   double* __restrict__ w_out, int n,
+                                                                   const double* __restrict__ norm2_in,
+                                                                   const double* __restrict__ norm2_mid, double eta,
+                                                                   double* __restrict__ partial) {
+  const bool redo = norm2_mid[0] < eta * eta * norm2_in[0];
+  double hr[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) hr[i] = redo ? h[i] : 0.0;
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double we = w_in[e];
+    if (redo) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) we -= hr[i] * V[i * vstride + e];
+    }
+    w_out[e] = we;
+    acc += we * we;
+  }
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) x += red[q];
+    partial[blockIdx.x] = x;
+  }
+}
+
 __global__ void norm2_kernel(const double* __restrict__ w, long long n, double* __restrict__ partial) {
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -528,9 +610,25 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
   return cudaGetLastError();
 }
 
+#define IRK_GS_SMALL(MODE, ...)                                                     \
+  switch (nv) {                                                                    \
+    case 1: gs_small_kernel<MODE, 1><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 2: gs_small_kernel<MODE, 2><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 3: gs_small_kernel<MODE, 3><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 4: gs_small_kernel<MODE, 4><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 5: gs_small_kernel<MODE, 5><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 6: gs_small_kernel<MODE, 6><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    case 7: gs_small_kernel<MODE, 7><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+    default: gs_small_kernel<MODE, 8><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+  }
+
 cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
                           int nb, cudaStream_t st) {
   if (nv > 64) return cudaErrorInvalidValue;
+  if (nv <= 8) {
+    IRK_GS_SMALL(0, V, vstride, nullptr, w, nullptr, (int)n, partial, nb);
+    return cudaGetLastError();
+  }
   dim3 grid(nb, (nv + 7) / 8);
   gs_kernel<0><<<grid, kThreads, 0, st>>>(V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb);
   return cudaGetLastError();
@@ -539,6 +637,10 @@ cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const doub
 cudaError_t launch_gs_axpy_dot(const double* V, long long vstride, int nv, const double* h, const double* w_in,
                                double* w_out, long long n, double* partial, int nb, cudaStream_t st) {
   if (nv > 64 || w_in == w_out) return cudaErrorInvalidValue;
+  if (nv <= 8) {
+    IRK_GS_SMALL(1, V, vstride, h, w_in, w_out, (int)n, partial, nb);
+    return cudaGetLastError();
+  }
   // group 0 writes w_out; the other groups recompute it for their dots
   dim3 grid(nb, (nv + 7) / 8);
   gs_kernel<1><<<grid, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, partial, nb);
@@ -549,6 +651,16 @@ cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const d
                              double* w_out, long long n, const double* norm2_in, const double* norm2_mid, double eta,
                              double* partial, int nb, cudaStream_t st) {
   if (nv > 64) return cudaErrorInvalidValue;
+  switch (nv) {
+#define IRK_GSR(NVV)                                                                                          \
+  case NVV:                                                                                                   \
+    gs_reorth_small_kernel<NVV><<<nb, kThreads, 0, st>>>(V, vstride, h, w_in, w_out, (int)n, norm2_in, norm2_mid, \
+                                                         eta, partial);                                       \
+    return cudaGetLastError();
+    IRK_GSR(1) IRK_GSR(2) IRK_GSR(3) IRK_GSR(4) IRK_GSR(5) IRK_GSR(6) IRK_GSR(7) IRK_GSR(8)
+#undef IRK_GSR
+    default: break;
+  }
   gs_reorth_kernel<<<nb, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, norm2_in, norm2_mid, eta, partial);
   return cudaGetLastError();
 }
@@ -624,9 +736,11 @@ cudaError_t launch_coarse_solve(const T* b, T* x, int nstage, long long ld, cons
                                 cudaStream_t st) {
   const size_t smem = (size_t)nci * sizeof(double);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
+  static size_t granted = 48 * 1024;  // opt-in dynamic shared memory, raised once when needed
+  if (smem > granted) {
     cudaError_t e = cudaFuncSetAttribute(coarse_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    granted = smem;
   }
   coarse_solve_kernel<T><<<nstage, kThreads, smem, st>>>(b, x, ld, Ainv, map, nci);
   return cudaGetLastError();

@@ -69,12 +69,14 @@ def _run(dim, N, k, Q, tau, nsteps=1, **opts):
     yref = prob.y0()
     with pkg.Solver(dim, N, k, Q, tau, **opts) as s:
         y = s.vector()
+        torch.cuda.synchronize()
         s.interpolate_initial(y, 0.0)
         its = []
         for n in range(nsteps):
             st = s.step(y, n * tau)
             its.append(st.iterations)
             yref = step_fastdiag(prob, yref, n * tau, fd)
+        s.synchronize()
         got = y.cpu().numpy()
     return rel_err(got, yref), its
 
@@ -104,6 +106,14 @@ def test_step_variants_of_the_lu_path(opts):
 @pytest.mark.parametrize("prec", [32, 64])
 def test_step_diag_presb(dim, N, k, Q, tau, prec):
     err, its = _run(dim, N, k, Q, tau, nsteps=2, variant=pkg.IRK_VARIANT_DIAG, mg_precision=prec)
+    assert err <= YTOL, (err, its)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_step_on_a_side_stream(use_graph):
+    """On a non-default stream the V-cycle is replayed from a captured CUDA graph (after one eager run)."""
+    st = torch.cuda.Stream()
+    err, its = _run(3, 8, 3, 3, 1e-3, nsteps=3, stream=st, use_graph=use_graph)
     assert err <= YTOL, (err, its)
 
 

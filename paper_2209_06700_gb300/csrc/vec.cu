@@ -84,6 +84,37 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const Tin* __restrict
   }
 }
 
+// Structured combinations with compile-time stage count Q (no dead FP64 instructions: on this
+// part every FP64 instruction, predicated or not, occupies the narrow FP64 pipe).
+//  UNIT_LOWER: out_i = a_i + sum_{j<i} Da[i][j] a_j          (S~ and S~^{-1}, unit lower triangular)
+//  FULL_DIAGB: out_i = sum_j Da[i][j] a_j + Db[i][i] b_i      (A^{-1} (x) M + tau I (x) K combination)
+enum CombineStructure { CS_UNIT_LOWER = 1, CS_FULL_DIAGB = 2 };
+template <typename Tin, typename Tout, int Q, int CS>
+__global__ void __launch_bounds__(kThreads) combine_struct_kernel(const Tin* __restrict__ a,
+                                                                  const double* __restrict__ b,
+                                                                  Tout* __restrict__ out, int n, long long ld,
+                                                                  const CombineParams C) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    double av[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) av[j] = (double)a[j * ld + e];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double acc;
+      if constexpr (CS == CS_UNIT_LOWER) {
+        acc = av[i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) acc = fma(C.Da[i * kMaxQ + j], av[j], acc);
+      } else {
+        acc = C.Db[i * kMaxQ + i] * b[i * ld + e];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) acc = fma(C.Da[i * kMaxQ + j], av[j], acc);
+      }
+      out[i * ld + e] = (Tout)acc;
+    }
+  }
+}
+
 // ------------------------------------------------------------ Chebyshev start, diag scaling
 template <typename T>
 __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
@@ -278,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const double* __res
   }
 }
 
-// Basis sizes up to 8: fully unrolled, one pass over the basis per kernel; in MODE 1 the
+// Basis sizes up to 16: fully unrolled, one pass over the basis per kernel; in MODE 1 the
 // basis values loaded for the update are reused for the dot products.
 template <int MODE, int NV>
 __global__ void __launch_bounds__(kThreads) gs_small_kernel(const double* __restrict__ V, long long vstride,
@@ -537,6 +568,36 @@ cudaError_t launch_combine(const Tin* a, const double* b, Tout* out, long long n
       if (i < C.nout && j < C.ninb && C.Db[i * kMaxQ + j] != 0.0) Cz.nzb[i] |= 1u << j;
     }
   }
+  // structure detection: unit lower triangular Da (no Db), or full Da with diagonal Db
+  bool unit_lower = (C.ninb == 0 && C.nina == C.nout);
+  bool diag_b = (C.ninb == C.nout && C.nina == C.nout && b != nullptr);
+  for (int i = 0; i < C.nout; ++i)
+    for (int j = 0; j < C.nina; ++j) {
+      const double d = C.Da[i * kMaxQ + j];
+      if ((j > i && d != 0.0) || (j == i && d != 1.0)) unit_lower = false;
+      if (j != i && j < C.ninb && C.Db[i * kMaxQ + j] != 0.0) diag_b = false;
+    }
+  const int q = C.nout;
+#define IRK_CS(QQ, CSV) combine_struct_kernel<Tin, Tout, QQ, CSV><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz)
+#define IRK_CS_Q(CSV)                         \
+  switch (q) {                                \
+    case 1: IRK_CS(1, CSV); break;            \
+    case 2: IRK_CS(2, CSV); break;            \
+    case 3: IRK_CS(3, CSV); break;            \
+    case 4: IRK_CS(4, CSV); break;            \
+    case 5: IRK_CS(5, CSV); break;            \
+    default: break;                           \
+  }
+  if (q <= 5 && unit_lower) {
+    IRK_CS_Q(CS_UNIT_LOWER);
+    return cudaGetLastError();
+  }
+  if (q <= 5 && diag_b) {
+    IRK_CS_Q(CS_FULL_DIAGB);
+    return cudaGetLastError();
+  }
+#undef IRK_CS_Q
+#undef IRK_CS
   if (nmax <= 1) combine_kernel<Tin, Tout, 1><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
   else if (nmax <= 2) combine_kernel<Tin, Tout, 2><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
   else if (nmax <= 3) combine_kernel<Tin, Tout, 3><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
@@ -610,22 +671,22 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
   return cudaGetLastError();
 }
 
-#define IRK_GS_SMALL(MODE, ...)                                                     \
-  switch (nv) {                                                                    \
-    case 1: gs_small_kernel<MODE, 1><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 2: gs_small_kernel<MODE, 2><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 3: gs_small_kernel<MODE, 3><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 4: gs_small_kernel<MODE, 4><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 5: gs_small_kernel<MODE, 5><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 6: gs_small_kernel<MODE, 6><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    case 7: gs_small_kernel<MODE, 7><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
-    default: gs_small_kernel<MODE, 8><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break; \
+#define IRK_GSC(MODE, NVV, ...) \
+  case NVV: gs_small_kernel<MODE, NVV><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break;
+#define IRK_GS_SMALL(MODE, ...)                                                                            \
+  switch (nv) {                                                                                           \
+    IRK_GSC(MODE, 1, __VA_ARGS__) IRK_GSC(MODE, 2, __VA_ARGS__) IRK_GSC(MODE, 3, __VA_ARGS__)            \
+    IRK_GSC(MODE, 4, __VA_ARGS__) IRK_GSC(MODE, 5, __VA_ARGS__) IRK_GSC(MODE, 6, __VA_ARGS__)            \
+    IRK_GSC(MODE, 7, __VA_ARGS__) IRK_GSC(MODE, 8, __VA_ARGS__) IRK_GSC(MODE, 9, __VA_ARGS__)            \
+    IRK_GSC(MODE, 10, __VA_ARGS__) IRK_GSC(MODE, 11, __VA_ARGS__) IRK_GSC(MODE, 12, __VA_ARGS__)         \
+    IRK_GSC(MODE, 13, __VA_ARGS__) IRK_GSC(MODE, 14, __VA_ARGS__) IRK_GSC(MODE, 15, __VA_ARGS__)         \
+    default: gs_small_kernel<MODE, 16><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break;                      \
   }
 
 cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
                           int nb, cudaStream_t st) {
   if (nv > 64) return cudaErrorInvalidValue;
-  if (nv <= 8) {
+  if (nv <= 16) {
     IRK_GS_SMALL(0, V, vstride, nullptr, w, nullptr, (int)n, partial, nb);
     return cudaGetLastError();
   }
@@ -637,7 +698,7 @@ cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const doub
 cudaError_t launch_gs_axpy_dot(const double* V, long long vstride, int nv, const double* h, const double* w_in,
                                double* w_out, long long n, double* partial, int nb, cudaStream_t st) {
   if (nv > 64 || w_in == w_out) return cudaErrorInvalidValue;
-  if (nv <= 8) {
+  if (nv <= 16) {
     IRK_GS_SMALL(1, V, vstride, h, w_in, w_out, (int)n, partial, nb);
     return cudaGetLastError();
   }
@@ -658,6 +719,7 @@ cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const d
                                                          eta, partial);                                       \
     return cudaGetLastError();
     IRK_GSR(1) IRK_GSR(2) IRK_GSR(3) IRK_GSR(4) IRK_GSR(5) IRK_GSR(6) IRK_GSR(7) IRK_GSR(8)
+    IRK_GSR(9) IRK_GSR(10) IRK_GSR(11) IRK_GSR(12) IRK_GSR(13) IRK_GSR(14) IRK_GSR(15) IRK_GSR(16)
 #undef IRK_GSR
     default: break;
   }

@@ -1,0 +1,38 @@
+// Fused coarse-grid V-cycle (see coarse_cycle.cu): host-visible parameter structs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace irk {
+
+constexpr int kMaxFusedLevels = 4;
+constexpr int kMaxChebDegree = 8;
+constexpr size_t kCoarseCycleMaxSmem = 200 * 1024;
+constexpr int kFusedMaxNodes = 4913;  // a level is fused when it has at most 17^3 nodes per block
+
+struct CoarseLevel {
+  int N, n1, n;                         // cells per axis, nodes per axis, nodes
+  float me[5][5], ke[5][5];             // element matrices scaled by h and 1/h
+  float dmr[kMaxDeg], dkr[kMaxDeg];     // 1D diagonals by node position mod k
+  float c1[kMaxChebDegree][kMaxQ], c2[kMaxChebDegree][kMaxQ];  // Chebyshev recurrence per step, block
+};
+
+struct CoarseParams {
+  int nlev, nb, m, nci;
+  float cm[kMaxQ];
+  float tau;
+  CoarseLevel lv[kMaxFusedLevels];      // lv[0] = the finest fused level
+  float pc[(2 * kMaxDeg + 1) * (kMaxDeg + 1)];
+  const float* ainv;                    // [nb][nci][nci] dense coarse inverse (FP32 copy)
+  const int* map;                       // interior index -> node of the coarsest level
+  const void* b_in;                     // level-lc right-hand sides [nb][ld]
+  void* x_out;                          // level-lc result [nb][ld]
+  long long ld;
+};
+
+size_t coarse_cycle_smem(const CoarseParams& P, int elem_size);
+template <typename T>
+cudaError_t launch_coarse_cycle(const CoarseParams& P, int dim, int k, cudaStream_t st);
+
+}  // namespace irk

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "coarse_cycle.h"
 #include "profiler.h"
 #include "solver.h"
 
@@ -256,6 +257,7 @@ class MG final : public MGBase {
     }
     IRK_TRY(setup_coarse());
     IRK_TRY(setup_chebyshev(st));
+    IRK_TRY(setup_fused());
     return Status::Ok();
   }
 
@@ -268,6 +270,13 @@ class MG final : public MGBase {
 
   Status vcycle(int l, cudaStream_t st) override {
     Lvl& L = lv_[l];
+    if (fused_ && l == lc_) {  // the whole sub-cycle below in one launch
+      fparams_.b_in = L.b;
+      fparams_.x_out = L.xa;
+      IRK_LAUNCH(PROF_COARSE, launch_coarse_cycle<float>(fparams_, cfg_.dim, cfg_.k, st));
+      L.cur = L.xa;
+      return Status::Ok();
+    }
     if (l == levels() - 1) {
       IRK_TRY(coarse_solve(L.b, L.xa, st));
       L.cur = L.xa;
@@ -538,10 +547,56 @@ class MG final : public MGBase {
       if (!spd_inverse(nci_, A)) return Status::Err(IRK_ENUMERIC, "coarse operator not SPD");
       std::copy(A.begin(), A.end(), Ainv_all.begin() + (size_t)s * nci_ * nci_);
     }
+    ainv_host_ = Ainv_all;
     IRK_TRY(arena_.alloc((void**)&dAinv_, Ainv_all.size() * sizeof(double)));
     IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
     IRK_CUDA(cudaMemcpy(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice));
     IRK_CUDA(cudaMemcpy(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return Status::Ok();
+  }
+
+  // Fused coarse cycle: the lowest levels with at most kFusedMaxNodes nodes per block run in one
+  // launch (FP32 multigrid, batched blocks, dense coarsest solve, at least two fused levels).
+  Status setup_fused() {
+    fused_ = false;
+    if (sizeof(T) != 4 || !cfg_.batched || use_fd_ || cfg_.cheb_degree > kMaxChebDegree || cfg_.nb > kMaxQ)
+      return Status::Ok();
+    int lc = levels() - 1;
+    while (lc > 0 && lv_[lc - 1].g.n <= kFusedMaxNodes) --lc;
+    const int nlev = levels() - lc;
+    if (nlev < 2 || nlev > kMaxFusedLevels) return Status::Ok();
+    CoarseParams& P = fparams_;
+    std::memset(&P, 0, sizeof(P));
+    P.nlev = nlev;
+    P.nb = cfg_.nb;
+    P.m = cfg_.cheb_degree;
+    P.nci = nci_;
+    P.tau = (float)cfg_.tau;
+    for (int s = 0; s < cfg_.nb; ++s) P.cm[s] = (float)cfg_.cm[s];
+    for (int i = 0; i < nlev; ++i) {
+      const Lvl& L = lv_[lc + i];
+      CoarseLevel& C = P.lv[i];
+      C.N = L.g.N;
+      C.n1 = L.g.n1;
+      C.n = (int)L.g.n;
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) { C.me[a][b] = (float)L.g.me[a][b]; C.ke[a][b] = (float)L.g.ke[a][b]; }
+      for (int r = 0; r < kMaxDeg; ++r) { C.dmr[r] = (float)L.g.dmr[r]; C.dkr[r] = (float)L.g.dkr[r]; }
+      if (lc + i + 1 < levels())
+        for (int j = 0; j < cfg_.cheb_degree; ++j)
+          for (int s = 0; s < cfg_.nb; ++s) { C.c1[j][s] = (float)L.c1[j][s]; C.c2[j][s] = (float)L.c2[j][s]; }
+    }
+    for (size_t i = 0; i < el_.Pc.size(); ++i) P.pc[i] = (float)el_.Pc[i];
+    if (coarse_cycle_smem(P, sizeof(float)) > kCoarseCycleMaxSmem) return Status::Ok();
+    std::vector<float> af(ainv_host_.begin(), ainv_host_.end());
+    float* dA = nullptr;
+    IRK_TRY(arena_.alloc((void**)&dA, af.size() * sizeof(float)));
+    IRK_CUDA(cudaMemcpy(dA, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice));
+    P.ainv = dA;
+    P.map = dmap_;
+    P.ld = lv_[lc].g.ld;
+    lc_ = lc;
+    fused_ = true;
     return Status::Ok();
   }
 
@@ -747,6 +802,10 @@ class MG final : public MGBase {
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
   int nci_ = 0;
+  std::vector<double> ainv_host_;
+  bool fused_ = false;
+  int lc_ = -1;
+  CoarseParams fparams_{};
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t gexec_ = nullptr;
   long long gcounts_[PROF_NCAT] = {};

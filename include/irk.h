@@ -178,6 +178,22 @@ long long irk_level_stride(irk_handle h, int level);
 irk_status irk_mg_smooth(irk_handle h, int level, const void* b, void* x, int x_is_zero);
 irk_status irk_mg_residual(irk_handle h, int level, const void* b, const void* x, void* r);
 irk_status irk_mg_restrict(irk_handle h, int level, const void* r_fine, void* b_coarse);
+
+/* Allocation-free variant of irk_mg_restrict (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory at this point, such as a
+ * serving process whose whole device budget is already held by request state,
+ * or a latency-critical loop where a cudaMalloc/cudaFree, which may synchronise
+ * the device, is not acceptable).  Same arguments and result as
+ * irk_mg_restrict; the intermediate grids of the axis passes live in one
+ * library-owned device array of 24 MiB per device (held by every GPU that loads
+ * the library until the process exits) instead of the handle's buffers, and no
+ * allocating routine is called.  The first call on a device resolves the
+ * array's device address (with that device current) and should come before any
+ * stream capture.  Levels needing more than 24 MiB of intermediate grids are
+ * rejected with IRK_EINVAL (irk_last_error names the sizes).  Every call shares
+ * the array and clears the part it uses; calls that overlap on the GPU race on
+ * it and must be serialised by the caller. */
+irk_status irk_mg_restrict_noalloc(irk_handle h, int level, const void* r_fine, void* b_coarse);
 irk_status irk_mg_prolongate(irk_handle h, int level, const void* e_coarse, void* x_fine);
 irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x);
 irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x);

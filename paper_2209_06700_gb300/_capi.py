@@ -66,6 +66,7 @@ SIGNATURES = {
     "irk_mg_smooth": (_I, [_H, _I, _P, _P, _I]),
     "irk_mg_residual": (_I, [_H, _I, _P, _P, _P]),
     "irk_mg_restrict": (_I, [_H, _I, _P, _P]),
+    "irk_mg_restrict_noalloc": (_I, [_H, _I, _P, _P]),
     "irk_mg_prolongate": (_I, [_H, _I, _P, _P]),
     "irk_mg_coarse_solve": (_I, [_H, _P, _P]),
     "irk_mg_vcycle": (_I, [_H, _I, _P, _P]),

@@ -390,6 +390,15 @@ MGBase* lu_mg(irk_problem* h) { return h->mg.get(); }
 
 }  // namespace
 
+// Restriction with caller-provided scratch, for the allocation-free entry point (noalloc.cu).
+irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, void* scratch, size_t bytes) {
+  return guarded(h, [&]() -> Status {
+    if (!r || !bc || !scratch || level < 0 || level + 1 >= h->mg->levels())
+      return Status::Err(IRK_EINVAL, "bad arguments");
+    return lu_mg(h)->restrict_in_scratch(level, r, bc, scratch, bytes, h->st);
+  });
+}
+
 extern "C" {
 
 void irk_default_options(irk_options* o) {

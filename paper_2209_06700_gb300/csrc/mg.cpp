@@ -373,6 +373,33 @@ class MG final : public MGBase {
     return Status::Ok();
   }
 
+  Status restrict_in_scratch(int l, const void* rin, void* bc, void* scratch, size_t bytes,
+                             cudaStream_t st) override {
+    Lvl& L = lv_[l];
+    const Lvl& C = lv_[l + 1];
+    const size_t need = (size_t)cfg_.nb * (size_t)(L.ld1 + L.ld2) * sizeof(T);
+    if (need > bytes)
+      return Status::Err(IRK_EINVAL, "restriction of level " + std::to_string(l) + " needs " + std::to_string(need) +
+                                         " bytes of scratch, more than the " + std::to_string(bytes) + " available");
+    // the passes leave the coarse-boundary entries of their outputs unwritten: start from zero
+    IRK_CUDA(cudaMemsetAsync(scratch, 0, need, st));
+    T* t1 = static_cast<T*>(scratch);
+    T* t2 = t1 + (size_t)cfg_.nb * L.ld1;
+    TransferParams P = transfer_params(C.g.N);
+    const int nf = L.g.n1, nc = C.g.n1;
+    if (cfg_.dim == 3) {
+      int d0[3] = {nf, nf, nf}, d1[3] = {nc, nf, nf}, d2[3] = {nc, nc, nf}, d3[3] = {nc, nc, nc};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)rin, t1, cfg_.nb, L.g.ld, L.ld1, d0, d1, 0, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(t1, t2, cfg_.nb, L.ld1, L.ld2, d1, d2, 1, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(t2, (T*)bc, cfg_.nb, L.ld2, C.g.ld, d2, d3, 2, 1, 0, P, st));
+    } else {
+      int d0[3] = {nf, nf, 1}, d1[3] = {nc, nf, 1}, d2[3] = {nc, nc, 1};
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>((const T*)rin, t1, cfg_.nb, L.g.ld, L.ld1, d0, d1, 0, 1, 0, P, st));
+      IRK_LAUNCH(PROF_TRANSFER, launch_transfer_axis<T>(t1, (T*)bc, cfg_.nb, L.ld1, C.g.ld, d1, d2, 1, 1, 0, P, st));
+    }
+    return Status::Ok();
+  }
+
   Status prolongate_add(int l, const void* ec, void* x, cudaStream_t st) override {
     Lvl& L = lv_[l];
     const Lvl& C = lv_[l + 1];

@@ -80,6 +80,10 @@ class MGBase {
   virtual Status smooth(int level, const void* b, void* x, int x_is_zero, cudaStream_t st) = 0;
   virtual Status residual(int level, const void* b, const void* x, void* r, cudaStream_t st) = 0;
   virtual Status restrict_to(int level, const void* r, void* bc, cudaStream_t st) = 0;
+  // The same restriction with its two intermediate axis-pass grids placed in caller-provided
+  // device scratch of `bytes` bytes (cleared here before use); EINVAL if it does not fit.
+  virtual Status restrict_in_scratch(int level, const void* r, void* bc, void* scratch, size_t bytes,
+                                     cudaStream_t st) = 0;
   virtual Status prolongate_add(int level, const void* ec, void* x, cudaStream_t st) = 0;
   virtual Status coarse_solve(const void* b, void* x, cudaStream_t st) = 0;
   virtual Status apply_mass(int level, const void* x, void* y, double scale, cudaStream_t st) = 0;

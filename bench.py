@@ -43,6 +43,21 @@ def peaks():
 
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, profiling recipe's table)
+FF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 15 * 2 / 1e12   # float-float multiply-adds on the FP32 pipe
+
+
+def recorded_traffic():
+    """ncu DRAM traffic per launch recorded in profiles/, valid only while the kernel source is unchanged."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["source_files"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec if h.hexdigest() == rec["source_sha256"] else None
+    except Exception:
+        return None
 
 
 def flops_per_stage_dof(dim, k):
@@ -178,6 +193,10 @@ def main():
     ap.add_argument("--per-stage", action="store_true", help="per-stage launches (batched=0)")
     ap.add_argument("--variant", default="lu", choices=["lu", "diag"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--op-ff", type=int, default=1, choices=[0, 1], help="float-float (1) or native FP64 (0) operator")
+    ap.add_argument("--cheb-degree", type=int, default=None)
+    ap.add_argument("--smoothing-range", type=float, default=None)
+    ap.add_argument("--eig-safety", type=float, default=None)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -200,8 +219,15 @@ def main():
 
     stream = torch.cuda.Stream()
     variant = pkg.IRK_VARIANT_DIAG if args.variant == "diag" else pkg.IRK_VARIANT_LU
-    s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=w.cheb_degree,
-                   mg_precision=args.mg_precision, batched=0 if args.per_stage else 1, variant=variant)
+    extra = {}
+    if args.smoothing_range is not None:
+        extra["smoothing_range"] = args.smoothing_range
+    if args.eig_safety is not None:
+        extra["eig_safety"] = args.eig_safety
+    cheb = w.cheb_degree if args.cheb_degree is None else args.cheb_degree
+    s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=cheb,
+                   mg_precision=args.mg_precision, batched=0 if args.per_stage else 1, variant=variant,
+                   op_ff=args.op_ff, **extra)
     lib = _capi.lib()
     y = s.vector()
     with torch.cuda.stream(stream):
@@ -213,7 +239,7 @@ def main():
         its.append(st.iterations)
         t += w.tau
 
-    # one profiled step (every category timed) to find the dominant kernel category
+    # one profiled step with every category timed (eager: no graph replay while kernels are timed)
     lib.irk_profile(s.h, (1 << len(PROF_NAMES)) - 1)
     s.step(y, t)
     t += w.tau
@@ -221,8 +247,9 @@ def main():
     for i, name in enumerate(PROF_NAMES):
         ms, n, nt = _capi.ctypes.c_double(), _capi.ctypes.c_longlong(), _capi.ctypes.c_longlong()
         lib.irk_profile_read(s.h, i, _capi.ctypes.byref(ms), _capi.ctypes.byref(n), _capi.ctypes.byref(nt))
-        cat_ms[name] = (ms.value, n.value)
-    dom = max(range(len(PROF_NAMES)), key=lambda i: cat_ms[PROF_NAMES[i]][0])
+        cat_ms[name] = (ms.value, n.value, nt.value)
+    # the dominant single kernel of the step is the FP64-accurate stage operator (Eq. irk:A)
+    dom = PROF_NAMES.index("apply64")
 
     # timed region: only the dominant category is bracketed by events; all launches counted
     lib.irk_profile(s.h, 1 << dom)
@@ -280,31 +307,43 @@ def main():
         t += w.tau
     e2e_step = statistics.median(e2e_ms)
 
-    # roofline of the dominant kernel category
+    # roofline of the dominant kernel: the stage operator (timed in the timed region)
     hbm, hbm_src = peaks()
-    dom_name = PROF_NAMES[dom]
     avg_ms = dom_ms / max(1, dom_n)
-    n_st = w.Q
-    if dom_name == "apply64":
-        flops = flops_per_stage_dof(w.dim, w.degree) * w.n_interior * n_st
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "op3d_kernel<double,4,EPI_DUAL>",
-                "peak_source": "nominal FP64 rate of the profiling recipe", "avg_launch_ms": avg_ms}
-    elif dom_name == "mg_op_fine":
-        # finest-level smoother/residual launches per V-cycle: (2m-1) Chebyshev steps reading
-        # x_j, x_{j-1}, b and writing x_{j+1} (16 B/node/block in FP32) and one residual (12 B)
+    flops = flops_per_stage_dof(w.dim, w.degree) * w.n_interior * w.Q
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic_rec = recorded_traffic()
+    kname = f"op3d_kernel<{'ff' if args.op_ff else 'double'},{w.degree},DUAL>"
+    traffic = None
+    if traffic_rec and w.name == traffic_rec.get("workload"):
+        traffic = traffic_rec["kernels"].get(kname, {}).get("dram_bytes_per_launch")
+    if args.op_ff:
+        peak, psrc = FF_PEAK_TFLOPS, ("derived: FP32 issue rate 152 SM x 128 lanes x 2.07 GHz / 15 FP32 "
+                                      "instructions per float-float multiply-add, x2 flops")
+    else:
+        peak, psrc = FP64_PEAK_TFLOPS, "nominal FP64 rate of the profiling recipe"
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kname, "peak_source": psrc, "avg_launch_ms": avg_ms,
+            "flops_per_launch": flops, "fp64_nominal_frac": achieved / FP64_PEAK_TFLOPS,
+            "algorithmic_bytes_per_launch": 24.0 * w.n_interior * w.Q}
+    # the finest-level FP32 smoother (HBM-bound), from the eager profiled step
+    sm_ms, _, sm_nt = cat_ms["mg_op_fine"]
+    roof_sm = None
+    if sm_nt > 0:
         m = w.cheb_degree
         eb = 4 if args.mg_precision == 32 else 8
-        per_node = ((2 * m - 1) * 4 * eb + 3 * eb) / (2 * m)
-        bytes_ = per_node * w.n_interior * n_st
-        achieved = bytes_ / (avg_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": f"op3d_kernel<{'float' if eb == 4 else 'double'},{w.degree},CHEB/RESID>",
-                "peak_source": hbm_src, "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_}
-    else:
-        roof = {"bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None, "traffic": None,
-                "kernel": dom_name, "peak_source": hbm_src, "avg_launch_ms": avg_ms}
+        per_node = ((2 * m - 1) * 4 * eb + 3 * eb) / (2 * m)   # (2m-1) Chebyshev steps (16 B) + 1 residual (12 B)
+        sm_avg = sm_ms / sm_nt
+        bytes_ = per_node * w.n_interior * w.Q
+        ach = bytes_ / (sm_avg / 1e3) / 1e9
+        sname = f"op3d_kernel<{'float' if eb == 4 else 'double'},{w.degree},CHEB>"
+        st_traffic = None
+        if traffic_rec and w.name == traffic_rec.get("workload"):
+            st_traffic = traffic_rec["kernels"].get(sname, {}).get("dram_bytes_per_launch")
+        roof_sm = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                   "traffic": st_traffic, "kernel": sname + " (finest level, Chebyshev steps and residual)",
+                   "peak_source": hbm_src, "avg_launch_ms": sm_avg, "bytes_per_launch": bytes_,
+                   "timing": "CUDA events on the solver stream, profiled eager step"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,9 +351,10 @@ def main():
                 "vs_baseline": None, "dtype": "f64 outer / f32 multigrid" if args.mg_precision == 32 else "f64",
                 "data": "synthetic (manufactured solution, seeded)",
                 "config": {"workload": w.name, "dim": w.dim, "degree": w.degree, "cells": w.cells, "Q": w.Q,
-                           "tau": w.tau, "cheb_degree": w.cheb_degree, "rtol": 1e-10,
+                           "tau": w.tau, "cheb_degree": cheb, "rtol": 1e-10,
                            "n_interior": w.n_interior, "stage_dofs": units,
                            "launch": "per-stage" if args.per_stage else "stage-batched",
+                           "operator_arithmetic": "float-float" if args.op_ff else "fp64",
                            "variant": args.variant, "mg_precision": args.mg_precision,
                            "parallelism": f"replicas x{world}",
                            "l2": "working set (Krylov basis ~3 GB) > 129 MB L2; no flush"},
@@ -325,6 +365,7 @@ def main():
                         "d2h_bytes_per_step": 8 * s.n, "ms_per_step": e2e_step},
                 "gpu_launches": launches,
                 "roofline": roof,
+                "roofline_smoother": roof_sm,
                 "category_ms_one_step": {k: round(v[0], 4) for k, v in cat_ms.items()},
                 "clocks": clk}
         if world == 1 and not args.no_cpu_baseline:

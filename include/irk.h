@@ -213,14 +213,14 @@ irk_status irk_synchronize(irk_handle h);
  * stream); irk_profile_read returns, for one category, the summed device time
  * of the timed launches in ms, the number of launches, and the number timed. */
 enum {
-  IRK_PROF_APPLY64 = 0,   /* FP64 tensor-product operator kernel (stage operator, K y_n) */
+  IRK_PROF_APPLY64 = 0,   /* FP64-accurate stage-operator kernel of Eq. (irk:A) */
   IRK_PROF_MG_OP = 1,     /* level-operator kernels (Chebyshev steps, residuals), coarser levels */
   IRK_PROF_MG_POINT = 2,  /* first Chebyshev step from zero */
   IRK_PROF_TRANSFER = 3,  /* restriction / prolongation passes */
   IRK_PROF_COARSE = 4,    /* dense coarse-grid solve */
   IRK_PROF_COMBINE = 5,   /* stage combinations and precision casts */
   IRK_PROF_KRYLOV = 6,    /* FGMRES vector kernels */
-  IRK_PROF_RHS = 7,       /* stage right-hand side, solution update, interpolation */
+  IRK_PROF_RHS = 7,       /* K y_n, stage right-hand side, solution update, interpolation */
   IRK_PROF_MG_OP_FINE = 8,  /* level-operator kernels on the finest level */
   IRK_PROF_NCAT = 9
 };

@@ -69,15 +69,16 @@ CombineParams combine_params(int nout, int nin, const double* Da, const double* 
   return C;
 }
 
-// FP64-accurate operator launch on the fine mesh: float-float (default) or native FP64
+// FP64-accurate operator launch on the fine mesh: float-float (default) or native FP64.
+// cat: PROF_APPLY64 for the stage operator, PROF_RHS for K y_n.
 Status launch_apply64(irk_problem* h, const double* u, int ns, const double* cm, const double* ck, int epi,
-                      const EpiParams<double>& E) {
+                      const EpiParams<double>& E, int cat = PROF_APPLY64) {
   if (h->opt.op_ff) {
     OpParams<ff> P = make_op_params<ff>(h->fine, ns, cm, ck);
-    IRK_LAUNCH(PROF_APPLY64, launch_op<ff>(h->dim, h->k, ns, u, P, epi, E, h->st));
+    IRK_LAUNCH(cat, launch_op<ff>(h->dim, h->k, ns, u, P, epi, E, h->st));
   } else {
     OpParams<double> P = make_op_params<double>(h->fine, ns, cm, ck);
-    IRK_LAUNCH(PROF_APPLY64, launch_op<double>(h->dim, h->k, ns, u, P, epi, E, h->st));
+    IRK_LAUNCH(cat, launch_op<double>(h->dim, h->k, ns, u, P, epi, E, h->st));
   }
   return Status::Ok();
 }
@@ -159,7 +160,7 @@ Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* load
   EpiParams<double> E;
   std::memset(&E, 0, sizeof(E));
   E.out = h->Ky;
-  IRK_TRY(launch_apply64(h, y, 1, &zero, &one, EPI_STORE, E));
+  IRK_TRY(launch_apply64(h, y, 1, &zero, &one, EPI_STORE, E, PROF_RHS));
   RhsParams R;
   std::memset(&R, 0, sizeof(R));
   R.Q = h->Q;

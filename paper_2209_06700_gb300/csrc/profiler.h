@@ -9,14 +9,14 @@
 namespace irk {
 
 enum ProfCat {
-  PROF_APPLY64 = 0,   // FP64 tensor-product operator kernel (stage operator, K y_n)
+  PROF_APPLY64 = 0,   // FP64-accurate stage operator kernel of Eq. (irk:A) (M and K of every stage)
   PROF_MG_OP = 1,     // multigrid level-operator kernels on the coarser levels
   PROF_MG_POINT = 2,  // first Chebyshev step from zero (pointwise)
   PROF_TRANSFER = 3,  // restriction / prolongation passes
   PROF_COARSE = 4,    // dense coarse solve
   PROF_COMBINE = 5,   // stage combinations (A^{-1}, S~, S~^{-1}, T, casts)
   PROF_KRYLOV = 6,    // FGMRES vector kernels (dots, axpys, norms, scaling)
-  PROF_RHS = 7,       // stage right-hand side and solution update
+  PROF_RHS = 7,       // K y_n, stage right-hand side and solution update
   PROF_MG_OP_FINE = 8,  // multigrid level-operator kernels on the finest level
   PROF_NCAT = 9
 };

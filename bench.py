@@ -149,6 +149,28 @@ def cpu_baseline(w, max_seconds=30.0):
             "s_per_step": per}
 
 
+def serving_measure(n_requests, realtime=True, **solver_opts):
+    """Serve the seeded request stream (Poisson arrivals at 200/s) through irk_serve."""
+    import paper_2209_06700_gb300 as pkg
+    from synthetic import serving_stream
+    reqs = serving_stream(512)[:n_requests]
+    t0 = time.perf_counter()
+    st, res, _ = pkg.serve(reqs, max_active=8, realtime=realtime, **solver_opts)
+    wall = time.perf_counter() - t0
+    ok = [r for r in res if r.status == 0]
+    lat = sorted(r.latency_ms for r in ok)
+    units = sum(q.Q * (q.degree * q.cells - 1) ** q.dim for q, r in zip(reqs, res) if r.status == 0)
+    pct = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))] if lat else None
+    return {"requests": n_requests, "completed": len(ok), "status": st, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+            "mean_ms": sum(lat) / len(lat) if lat else None, "makespan_s": wall,
+            "throughput": units / wall, "unit": UNIT,
+            "mean_setup_ms": sum(r.setup_ms for r in ok) / max(1, len(ok)),
+            "mean_solve_ms": sum(r.solve_ms for r in ok) / max(1, len(ok)),
+            "mean_queue_ms": sum(r.queue_ms for r in ok) / max(1, len(ok)),
+            "mean_iterations": sum(r.iterations for r in ok) / max(1, len(ok)),
+            "slots": 8, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0"}
+
+
 def run_reference(args, w):
     """Reference arm: the CPU oracle, timed on the host (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -193,6 +215,9 @@ def main():
     ap.add_argument("--per-stage", action="store_true", help="per-stage launches (batched=0)")
     ap.add_argument("--variant", default="lu", choices=["lu", "diag"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-baseline-requests", type=int, default=128)
     ap.add_argument("--op-ff", type=int, default=1, choices=[0, 1], help="float-float (1) or native FP64 (0) operator")
     ap.add_argument("--cheb-degree", type=int, default=None)
     ap.add_argument("--smoothing-range", type=float, default=None)
@@ -368,6 +393,11 @@ def main():
                 "roofline_smoother": roof_sm,
                 "category_ms_one_step": {k: round(v[0], 4) for k, v in cat_ms.items()},
                 "clocks": clk}
+        if world == 1 and not args.no_serve:
+            line["serving"] = serving_measure(args.serve_requests)
+            # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)
+            line["serving_fp64_per_stage_baseline"] = serving_measure(
+                args.serve_baseline_requests, op_ff=0, mg_precision=64, batched=0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -120,6 +120,48 @@ irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_loa
 irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count,
                            irk_status* per_item);
 
+/* ---- serving: continuous batching of single-step requests ---- */
+typedef struct {
+  int dim, cells, degree, Q;  /* problem of the request (as irk_create) */
+  double tau;                 /* step */
+  double t0;                  /* the step goes from t0 to t0 + tau, y(t0) = interpolant */
+  double arrival_s;           /* arrival time, seconds after irk_serve starts */
+} irk_request;
+
+typedef struct {
+  irk_status status;
+  int iterations;             /* FGMRES iterations */
+  double latency_ms;          /* arrival -> y_{n+1} ready (on the host if requested) */
+  double queue_ms;            /* arrival -> admission */
+  double setup_ms;            /* handle creation (hierarchy, Chebyshev intervals) and y_0 */
+  double solve_ms;            /* irk_step */
+  long long ndofs, ninterior;
+  double mem_bytes;           /* device memory reserved for the request at admission */
+} irk_result;
+
+typedef struct {
+  int max_active;             /* concurrent requests (slots, one stream and one host worker each) */
+  double mem_budget_bytes;    /* device memory for resident requests; <= 0: 80% of the free memory */
+  int realtime;               /* 1: honour arrival_s; 0: every request arrives at time 0 */
+  irk_options solver;         /* solver options of every request */
+} irk_serve_options;
+
+/* Default serving options: 8 slots, automatic budget, real time, solver defaults with restart 16. */
+void irk_default_serve_options(irk_serve_options* opt);
+
+/* Serve `count` requests with continuous batching (not in the paper: the serving form of this
+ * library).  Requests are admitted in arrival order as soon as a slot and enough of the memory
+ * budget are free; each admitted request builds its own handle on its own CUDA stream, takes one
+ * step from the interpolant of u(., t0) and releases its memory, so requests arriving while others
+ * are on the GPU join without waiting for them and their kernels overlap on the device.  Every
+ * request's result is independent of the mix (same kernels, same launch shapes, deterministic
+ * reductions).  results (host, count entries) receive per-request timing and status; out_host
+ * (optional, count pointers, each NULL or a host array of irk_ndofs doubles) receives y_{n+1}.
+ * A request larger than the whole budget fails with IRK_EBUSY.  Returns IRK_OK if every request
+ * succeeded, else the first failing status. */
+irk_status irk_serve(const irk_request* reqs, int count, const irk_serve_options* opt, irk_result* results,
+                     double** out_host);
+
 /* Release every resource of the handle (NULL is accepted). */
 irk_status irk_destroy(irk_handle h);
 

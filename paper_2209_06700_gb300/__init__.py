@@ -7,10 +7,47 @@ sm_103a kernels.  ``Solver`` wraps one handle.
 import ctypes
 
 from . import _capi
-from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkStats,
-                    TABLEAU_FIELDS, check, lib)
+from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkRequest, IrkResult,
+                    IrkServeOptions, IrkStats, TABLEAU_FIELDS, check, lib)
 
-__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options"]
+__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options", "serve"]
+
+
+def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, **solver_opts):
+    """Run irk_serve on a list of (dim, cells, degree, Q, tau, t0, arrival_s) tuples or objects.
+
+    Returns (status, results, ys): results are IrkResult structs, ys the host numpy arrays of
+    y_{n+1} when outputs=True (else None).
+    """
+    import numpy as np
+    n = len(requests)
+    arr = (IrkRequest * n)()
+    for i, r in enumerate(requests):
+        if isinstance(r, tuple):
+            d, N, k, Q, tau, t0, at = r
+        else:
+            d, N, k, Q, tau, t0, at = r.dim, r.cells, r.degree, r.Q, r.tau, 0.0, r.arrival_s
+        arr[i] = IrkRequest(d, N, k, Q, float(tau), float(t0), float(at))
+    o = IrkServeOptions()
+    lib().irk_default_serve_options(ctypes.byref(o))
+    o.max_active = int(max_active)
+    o.mem_budget_bytes = float(mem_budget_bytes)
+    o.realtime = 1 if realtime else 0
+    for key, val in solver_opts.items():
+        setattr(o.solver, key, val)
+    res = (IrkResult * n)()
+    ys = None
+    ptrs = None
+    if outputs:
+        ys = []
+        ptrs = (ctypes.POINTER(ctypes.c_double) * n)()
+        for i in range(n):
+            d, N, k = arr[i].dim, arr[i].cells, arr[i].degree
+            y = np.zeros((k * N + 1) ** d)
+            ys.append(y)
+            ptrs[i] = y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    status = lib().irk_serve(arr, n, ctypes.byref(o), res, ptrs)
+    return status, list(res), ys
 
 
 def _ptr(t):

@@ -30,9 +30,25 @@ class IrkOptions(ctypes.Structure):
                 ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int)]
 
 
+class IrkRequest(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("cells", ctypes.c_int), ("degree", ctypes.c_int), ("Q", ctypes.c_int),
+                ("tau", ctypes.c_double), ("t0", ctypes.c_double), ("arrival_s", ctypes.c_double)]
+
+
+class IrkResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("ndofs", ctypes.c_longlong), ("ninterior", ctypes.c_longlong), ("mem_bytes", ctypes.c_double)]
+
+
 class IrkStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("vcycles", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
+
+
+class IrkServeOptions(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("realtime", ctypes.c_int),
+                ("solver", IrkOptions)]
 
 
 _H = ctypes.c_void_p
@@ -48,6 +64,9 @@ SIGNATURES = {
     "irk_step": (_I, [_H, _P, _D, _P, ctypes.POINTER(IrkStats)]),
     "irk_solve_batch": (_I, [ctypes.POINTER(_H), ctypes.POINTER(_P), ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
     "irk_destroy": (_I, [_H]),
+    "irk_default_serve_options": (None, [ctypes.POINTER(IrkServeOptions)]),
+    "irk_serve": (_I, [ctypes.POINTER(IrkRequest), _I, ctypes.POINTER(IrkServeOptions), ctypes.POINTER(IrkResult),
+                       ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]),
     "irk_ndofs": (_LL, [_H]),
     "irk_ninterior": (_LL, [_H]),
     "irk_stage_stride": (_LL, [_H]),

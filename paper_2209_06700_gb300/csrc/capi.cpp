@@ -43,8 +43,8 @@ struct irk_problem {
   Profiler prof;
   std::string last_err;
   ~irk_problem() {
-    if (fw.hvals) cudaFreeHost(fw.hvals);
-    if (fwd.hvals && fwd.hvals != fw.hvals) cudaFreeHost(fwd.hvals);
+    pinned_block_release(fw.hvals);
+    if (fwd.hvals != fw.hvals) pinned_block_release(fwd.hvals);
   }
 };
 
@@ -288,6 +288,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   h->tau = tau;
   h->st = (cudaStream_t)stream;
   h->prof.st = h->st;
+  h->arena.set_stream(h->st);
   IRK_CUDA(cudaGetDevice(&h->device));
   std::string err;
   if (!build_tableau(Q, h->tab, err)) return Status::Err(IRK_EINVAL, err);
@@ -343,8 +344,9 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
     std::vector<double> G1d(G1.begin(), G1.end()), xd(xn.begin(), xn.end());
     IRK_TRY(h->arena.alloc((void**)&h->G1, n1 * sizeof(double)));
     IRK_TRY(h->arena.alloc((void**)&h->x1d, n1 * sizeof(double)));
-    IRK_CUDA(cudaMemcpy(h->G1, G1d.data(), n1 * sizeof(double), cudaMemcpyHostToDevice));
-    IRK_CUDA(cudaMemcpy(h->x1d, xd.data(), n1 * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpyAsync(h->G1, G1d.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    IRK_CUDA(cudaMemcpyAsync(h->x1d, xd.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    IRK_CUDA(cudaStreamSynchronize(h->st));
   }
   MGConfig mc;
   mc.dim = h->dim; mc.k = degree; mc.N = h->N; mc.tau = tau;
@@ -355,7 +357,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   mc.nb = Q;
   mc.cm = h->tab.lam;
   IRK_TRY(make_mg(mc, h->el, h->arena, h->st, h->mg));
-  IRK_TRY(fgmres_alloc(h->fw, Q, g.ld, o.restart, h->arena));
+  IRK_TRY(fgmres_alloc(h->fw, Q, g.ld, o.restart, h->arena, h->st));
   if (o.variant == IRK_VARIANT_DIAG) {
     for (const auto& blk : h->tab.blocks) {
       MGConfig md = mc;
@@ -366,7 +368,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
       IRK_TRY(make_mg(md, h->el, h->arena, h->st, m));
       h->mg_diag.push_back(std::move(m));
     }
-    IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena));
+    IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena, h->st));
   }
   IRK_CUDA(cudaStreamSynchronize(h->st));
   return Status::Ok();

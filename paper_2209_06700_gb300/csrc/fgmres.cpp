@@ -8,6 +8,7 @@
 // device reductions and the Hessenberg/Givens update runs on the host with
 // one device->host transfer per iteration.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "profiler.h"
@@ -15,7 +16,33 @@
 
 namespace irk {
 
-Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena) {
+// Small pinned host blocks (256 doubles) shared by all handles of the process.  They are never
+// handed back to the driver: releasing pinned memory synchronises the device, which would stall
+// the streams of other requests in flight.
+namespace {
+std::mutex g_pin_mu;
+std::vector<double*> g_pin_free;
+}  // namespace
+
+double* pinned_block_acquire() {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  if (g_pin_free.empty()) {
+    double* chunk = nullptr;
+    if (cudaMallocHost((void**)&chunk, 64 * 256 * sizeof(double)) != cudaSuccess) return nullptr;
+    for (int i = 0; i < 64; ++i) g_pin_free.push_back(chunk + (size_t)i * 256);
+  }
+  double* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_block_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena, cudaStream_t stream) {
   if (m < 1 || m > 60) return Status::Err(IRK_EINVAL, "restart must be in 1..60");
   w.ns = ns;
   w.m = m;
@@ -28,11 +55,11 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
   IRK_TRY(arena.alloc((void**)&w.partial, (size_t)66 * w.nb * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.dvals, 256 * sizeof(double)));
   if (!w.hvals) {
-    cudaError_t e = cudaMallocHost((void**)&w.hvals, 256 * sizeof(double));
-    if (e != cudaSuccess) return Status::Err(IRK_ENOMEM, "cudaMallocHost failed");
+    w.hvals = pinned_block_acquire();
+    if (!w.hvals) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
   }
-  const double one = 1.0;
-  IRK_CUDA(cudaMemcpy(w.dvals + 255, &one, sizeof(double), cudaMemcpyHostToDevice));
+  w.hvals[255] = 1.0;
+  IRK_CUDA(cudaMemcpyAsync(w.dvals + 255, w.hvals + 255, sizeof(double), cudaMemcpyHostToDevice, stream));
   return Status::Ok();
 }
 

@@ -145,6 +145,17 @@ cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const d
                              double* w_out, long long n, const double* norm2_in, const double* norm2_mid, double eta,
                              double* partial, int nb, cudaStream_t st);
 
+// Block-wise helpers (ns vectors of n elements at stride ld), coefficients on the device:
+//  block_dot:   partial[s][nb] = partial sums of a_s . b_s
+//  block_axpy2: w_s -= alpha[s] v1_s + beta[s] v0_s
+//  block_shift: v0_s = v1_s; v1_s = w_s / nrm[s] (0 where nrm[s] == 0); with v0 = nullptr: v1_s = w_s / nrm[s]
+cudaError_t launch_block_dot(const double* a, const double* b, int ns, long long n, long long ld, double* partial,
+                             int nb, cudaStream_t st);
+cudaError_t launch_block_axpy2(double* w, const double* v1, const double* v0, const double* alpha, const double* beta,
+                               int ns, long long n, long long ld, cudaStream_t st);
+cudaError_t launch_block_shift(double* v0, double* v1, const double* w, const double* nrm, int ns, long long n,
+                               long long ld, cudaStream_t st);
+
 // ---------------- intergrid transfer (Q_k embedding) ----------------
 struct TransferParams {
   int k, Nc;                 // degree, coarse cells per axis

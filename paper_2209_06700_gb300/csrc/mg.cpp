@@ -14,23 +14,38 @@
 
 namespace irk {
 
+// Stream-ordered allocations from the device's default memory pool: releasing a handle does not
+// synchronise the device, so concurrent requests on other streams keep running.
 DeviceArena::~DeviceArena() {
-  for (auto it = ptrs_.rbegin(); it != ptrs_.rend(); ++it) cudaFree(*it);
+  for (auto it = ptrs_.rbegin(); it != ptrs_.rend(); ++it) cudaFreeAsync(*it, st_);
+}
+
+static void keep_pool_memory() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long keep = ~0ull;  // freed blocks stay cached in the pool for the next handle
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
 }
 
 Status DeviceArena::alloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 256;
-  cudaError_t e = cudaMalloc(p, bytes);
+  keep_pool_memory();
+  cudaError_t e = cudaMallocAsync(p, bytes, st_);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return Status::Err(IRK_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    return Status::Err(IRK_ENOMEM, "allocation of " + std::to_string(bytes) + " bytes failed");
   }
   ptrs_.push_back(*p);
   total_ += bytes;
-  e = cudaMemset(*p, 0, bytes);
-  if (e != cudaSuccess) return Status::Err(IRK_ECUDA, "cudaMemset failed");
+  e = cudaMemsetAsync(*p, 0, bytes, st_);
+  if (e != cudaSuccess) return Status::Err(IRK_ECUDA, "cudaMemsetAsync failed");
   return Status::Ok();
 }
 
@@ -229,6 +244,7 @@ class MG final : public MGBase {
   MG(const MGConfig& c, const Element1D& e, DeviceArena& a) : cfg_(c), el_(e), arena_(a) {}
 
   Status setup(cudaStream_t st) {
+    st_ = st;
     // level sizes: N, N/2, ... while even and the coarse mesh keeps an interior node
     std::vector<int> sizes{cfg_.N};
     const int nmin = (cfg_.k == 1) ? 2 : 1;
@@ -258,6 +274,7 @@ class MG final : public MGBase {
     IRK_TRY(setup_coarse());
     IRK_TRY(setup_chebyshev(st));
     IRK_TRY(setup_fused());
+    IRK_CUDA(cudaStreamSynchronize(st));
     return Status::Ok();
   }
 
@@ -577,8 +594,8 @@ class MG final : public MGBase {
     ainv_host_ = Ainv_all;
     IRK_TRY(arena_.alloc((void**)&dAinv_, Ainv_all.size() * sizeof(double)));
     IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
-    IRK_CUDA(cudaMemcpy(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice));
-    IRK_CUDA(cudaMemcpy(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpyAsync(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
+    IRK_CUDA(cudaMemcpyAsync(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
     return Status::Ok();
   }
 
@@ -618,7 +635,7 @@ class MG final : public MGBase {
     std::vector<float> af(ainv_host_.begin(), ainv_host_.end());
     float* dA = nullptr;
     IRK_TRY(arena_.alloc((void**)&dA, af.size() * sizeof(float)));
-    IRK_CUDA(cudaMemcpy(dA, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpyAsync(dA, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice, st_));
     P.ainv = dA;
     P.map = dmap_;
     P.ld = lv_[lc].g.ld;
@@ -694,9 +711,9 @@ class MG final : public MGBase {
     const size_t vb = (size_t)cfg_.nb * g.ld * sizeof(double);
     IRK_TRY(arena_.alloc((void**)&fd_t1_, vb));
     IRK_TRY(arena_.alloc((void**)&fd_t2_, vb));
-    IRK_CUDA(cudaMemcpy(fd_V_, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice));
-    IRK_CUDA(cudaMemcpy(fd_Vt_, Vt.data(), Vt.size() * sizeof(double), cudaMemcpyHostToDevice));
-    IRK_CUDA(cudaMemcpy(fd_mu_, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice));
+    IRK_CUDA(cudaMemcpyAsync(fd_V_, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
+    IRK_CUDA(cudaMemcpyAsync(fd_Vt_, Vt.data(), Vt.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
+    IRK_CUDA(cudaMemcpyAsync(fd_mu_, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
     std::memset(&fd_params_, 0, sizeof(fd_params_));
     fd_params_.ni = ni;
     fd_params_.tau = cfg_.tau;
@@ -709,19 +726,27 @@ class MG final : public MGBase {
     const int nb = cfg_.nb;
     const LevelGeom& g0 = lv_[0].g;
     const size_t len = (size_t)nb * g0.ld;
-    double *v0, *v1, *w, *t, *red, *partial;
-    IRK_TRY(arena_.alloc((void**)&v0, len * sizeof(double)));
-    IRK_TRY(arena_.alloc((void**)&v1, len * sizeof(double)));
-    IRK_TRY(arena_.alloc((void**)&w, len * sizeof(double)));
-    IRK_TRY(arena_.alloc((void**)&t, len * sizeof(double)));
-    const int nbred = reduction_blocks((long long)g0.ld);
-    IRK_TRY(arena_.alloc((void**)&partial, (size_t)nbred * sizeof(double)));
-    IRK_TRY(arena_.alloc((void**)&red, 8 * sizeof(double)));
     const int steps = std::max(2, cfg_.eig_steps);
+    DeviceArena tmp(st);  // Lanczos work vectors, released when the setup returns
+    double *v0, *v1, *w, *t, *partial, *ab;
+    IRK_TRY(tmp.alloc((void**)&v0, len * sizeof(double)));
+    IRK_TRY(tmp.alloc((void**)&v1, len * sizeof(double)));
+    IRK_TRY(tmp.alloc((void**)&w, len * sizeof(double)));
+    IRK_TRY(tmp.alloc((void**)&t, len * sizeof(double)));
+    const int nbred = std::min(reduction_blocks((long long)g0.ld), 1024);
+    IRK_TRY(tmp.alloc((void**)&partial, (size_t)nbred * nb * sizeof(double)));
+    // alpha[step][block], beta[step][block], norm[block]
+    IRK_TRY(tmp.alloc((void**)&ab, (size_t)(2 * steps + 2) * nb * sizeof(double)));
+    double* alpha = ab;
+    double* beta = ab + (size_t)steps * nb;
+    double* nrm0 = ab + (size_t)2 * steps * nb;
+    double* zeros = nrm0 + nb;  // beta_0 = 0 (allocation is zero-initialised)
+    std::vector<double> hab((size_t)2 * steps * nb);
     for (int l = 0; l + 1 < levels(); ++l) {
       Lvl& L = lv_[l];
       const LevelGeom& g = L.g;
       const long long n = g.n, ldl = g.ld;
+      const int nbl = std::min(reduction_blocks(n), nbred);
       // deterministic start vector on interior nodes (hash-based), same for every block
       std::vector<double> h0((size_t)nb * ldl, 0.0);
       for (int s = 0; s < nb; ++s)
@@ -733,66 +758,49 @@ class MG final : public MGBase {
           hsh ^= hsh >> 29; hsh *= 0xBF58476D1CE4E5B9ULL; hsh ^= hsh >> 32;
           h0[(size_t)s * ldl + e] = 0.5 + (double)(hsh >> 11) * (1.0 / 9007199254740992.0);
         }
-      IRK_CUDA(cudaMemcpyAsync(v1, h0.data(), h0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      IRK_CUDA(cudaMemcpyAsync(w, h0.data(), h0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
       IRK_CUDA(cudaMemsetAsync(v0, 0, (size_t)nb * ldl * sizeof(double), st));
-      std::vector<std::vector<double>> alpha(nb), beta(nb);
-      std::vector<double> bprev(nb, 0.0);
-      // normalise
-      auto dot = [&](const double* a, const double* b, int s, double& out) -> Status {
-        IRK_CUDA(launch_multidot(a + (size_t)s * ldl, 0, 1, b + (size_t)s * ldl, n, partial, nbred, st));
-        IRK_CUDA(launch_reduce_partials(partial, 1, nbred, red, st));
-        IRK_CUDA(cudaMemcpyAsync(&out, red, sizeof(double), cudaMemcpyDeviceToHost, st));
-        IRK_CUDA(cudaStreamSynchronize(st));
-        return Status::Ok();
-      };
-      for (int s = 0; s < nb; ++s) {
-        double nn;
-        IRK_TRY(dot(v1, v1, s, nn));
-        IRK_CUDA(launch_scale(v1 + (size_t)s * ldl, 1.0 / std::sqrt(nn), v1 + (size_t)s * ldl, n, st));
-      }
+      IRK_CUDA(launch_block_dot(w, w, nb, n, ldl, partial, nbl, st));
+      IRK_CUDA(launch_reduce_partials(partial, nb, nbl, nrm0, st, 1));
+      IRK_CUDA(launch_block_shift(nullptr, v1, w, nrm0, nb, n, ldl, st));
       std::vector<double> one(nb, 1.0);
       DiagParams<double> D = make_diag_params<double>(g, nb, cfg_.cm.data(), ck_.data(), one.data());
       OpParams<double> P = make_op_params<double>(g, nb, cfg_.cm.data(), ck_.data());
       EpiParams<double> E;
       std::memset(&E, 0, sizeof(E));
       E.out = w;
-      std::vector<bool> done(nb, false);
+      // symmetric form D^{-1/2} A D^{-1/2}; every block advances together, no host round trip
       for (int it = 0; it < steps; ++it) {
         IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, v1, t, D, 1, st));
         IRK_CUDA(launch_op<double>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
         IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, w, w, D, 1, st));
-        for (int s = 0; s < nb; ++s) {
-          if (done[s]) continue;
-          double a;
-          IRK_TRY(dot(w, v1, s, a));
-          alpha[s].push_back(a);
-          double* ws = w + (size_t)s * ldl;
-          // w -= a v1 + bprev v0
-          double coef[2] = {a, bprev[s]};
-          double* dcoef = red + 2;
-          IRK_CUDA(cudaMemcpyAsync(dcoef, coef, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
-          IRK_CUDA(launch_multi_axpy(v1 + (size_t)s * ldl, 0, 1, dcoef, -1.0, ws, n, st));
-          IRK_CUDA(launch_multi_axpy(v0 + (size_t)s * ldl, 0, 1, dcoef + 1, -1.0, ws, n, st));
-          double bb;
-          IRK_TRY(dot(w, w, s, bb));
-          const double bn = std::sqrt(std::max(bb, 0.0));
-          if (bn < 1e-12 * std::fabs(a) || it + 1 == steps) {
-            done[s] = true;
-            continue;
-          }
-          beta[s].push_back(bn);
-          bprev[s] = bn;
-          IRK_CUDA(cudaMemcpyAsync(v0 + (size_t)s * ldl, v1 + (size_t)s * ldl, n * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, st));
-          IRK_CUDA(launch_scale(ws, 1.0 / bn, v1 + (size_t)s * ldl, n, st));
+        double* a_it = alpha + (size_t)it * nb;
+        double* b_it = beta + (size_t)it * nb;
+        const double* b_prev = (it == 0) ? zeros : beta + (size_t)(it - 1) * nb;
+        IRK_CUDA(launch_block_dot(w, v1, nb, n, ldl, partial, nbl, st));
+        IRK_CUDA(launch_reduce_partials(partial, nb, nbl, a_it, st));
+        IRK_CUDA(launch_block_axpy2(w, v1, v0, a_it, b_prev, nb, n, ldl, st));
+        IRK_CUDA(launch_block_dot(w, w, nb, n, ldl, partial, nbl, st));
+        IRK_CUDA(launch_reduce_partials(partial, nb, nbl, b_it, st, 1));
+        IRK_CUDA(launch_block_shift(v0, v1, w, b_it, nb, n, ldl, st));
+      }
+      IRK_CUDA(cudaMemcpyAsync(hab.data(), ab, hab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      IRK_CUDA(cudaStreamSynchronize(st));
+      std::vector<std::vector<double>> alpha_h(nb), beta_h(nb);
+      for (int s = 0; s < nb; ++s) {
+        for (int it = 0; it < steps; ++it) {
+          const double a = hab[(size_t)it * nb + s], bb = hab[(size_t)(steps + it) * nb + s];
+          alpha_h[s].push_back(a);
+          if (!(bb > 1e-12 * std::fabs(a))) break;  // invariant subspace found
+          if (it + 1 < steps) beta_h[s].push_back(bb);
         }
       }
       L.lo.resize(nb);
       L.hi.resize(nb);
       for (int s = 0; s < nb; ++s) {
-        std::vector<double> b2(beta[s].begin(), beta[s].end());
-        b2.resize(alpha[s].size() > 0 ? alpha[s].size() - 1 : 0);
-        const double lmax = tridiag_max_eig(alpha[s], b2);
+        std::vector<double> b2(beta_h[s].begin(), beta_h[s].end());
+        b2.resize(alpha_h[s].size() > 0 ? alpha_h[s].size() - 1 : 0);
+        const double lmax = tridiag_max_eig(alpha_h[s], b2);
         L.hi[s] = cfg_.eig_safety * lmax;
         L.lo[s] = L.hi[s] / cfg_.smoothing_range;
       }
@@ -829,6 +837,7 @@ class MG final : public MGBase {
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
   int nci_ = 0;
+  cudaStream_t st_ = nullptr;
   std::vector<double> ainv_host_;
   bool fused_ = false;
   int lc_ = -1;

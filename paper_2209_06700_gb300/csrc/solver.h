@@ -36,10 +36,15 @@ struct Status {
 // Device allocation owned by the handle (freed in reverse order).
 class DeviceArena {
  public:
+  explicit DeviceArena(cudaStream_t st = nullptr) : st_(st) {}
   ~DeviceArena();
-  Status alloc(void** p, size_t bytes);  // zero-initialised
+  DeviceArena(const DeviceArena&) = delete;
+  DeviceArena& operator=(const DeviceArena&) = delete;
+  void set_stream(cudaStream_t st) { st_ = st; }
+  Status alloc(void** p, size_t bytes);  // zero-initialised, stream-ordered
   size_t bytes() const { return total_; }
  private:
+  cudaStream_t st_;
   std::vector<void*> ptrs_;
   size_t total_ = 0;
 };
@@ -120,7 +125,9 @@ struct FGMRESWork {
   int nb = 0;
 };
 
-Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena);
+Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena, cudaStream_t stream);
+double* pinned_block_acquire();
+void pinned_block_release(double* p);
 
 struct FGMRESResult { int iterations = 0; double rel_residual = 0; bool converged = false; };
 

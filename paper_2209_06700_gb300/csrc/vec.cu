@@ -391,6 +391,48 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_small_kernel(const double*
   }
 }
 
+__global__ void __launch_bounds__(kThreads) block_dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                                             int n, long long ld, double* __restrict__ partial) {
+  const int s = blockIdx.y;
+  const double* as = a + s * ld;
+  const double* bs = b + s * ld;
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) acc += as[e] * bs[e];
+  __shared__ double red[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) x += red[q];
+    partial[(long long)s * gridDim.x + blockIdx.x] = x;
+  }
+}
+
+__global__ void block_axpy2_kernel(double* __restrict__ w, const double* __restrict__ v1, const double* __restrict__ v0,
+                                   const double* __restrict__ alpha, const double* __restrict__ beta, int n,
+                                   long long ld) {
+  const int s = blockIdx.y;
+  const double a = alpha[s], bt = beta[s];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const long long o = s * ld + e;
+    w[o] -= a * v1[o] + bt * v0[o];
+  }
+}
+
+__global__ void block_shift_kernel(double* __restrict__ v0, double* __restrict__ v1, const double* __restrict__ w,
+                                   const double* __restrict__ nrm, int n, long long ld) {
+  const int s = blockIdx.y;
+  const double f = (nrm[s] > 0.0) ? 1.0 / nrm[s] : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const long long o = s * ld + e;
+    if (v0) v0[o] = v1[o];
+    v1[o] = w[o] * f;
+  }
+}
+
 __global__ void norm2_kernel(const double* __restrict__ w, long long n, double* __restrict__ partial) {
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -724,6 +766,27 @@ cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const d
     default: break;
   }
   gs_reorth_kernel<<<nb, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, norm2_in, norm2_mid, eta, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_dot(const double* a, const double* b, int ns, long long n, long long ld, double* partial,
+                             int nb, cudaStream_t st) {
+  dim3 grid(nb, ns);
+  block_dot_kernel<<<grid, kThreads, 0, st>>>(a, b, (int)n, ld, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_axpy2(double* w, const double* v1, const double* v0, const double* alpha, const double* beta,
+                               int ns, long long n, long long ld, cudaStream_t st) {
+  dim3 grid(blocks_for(n, 2), ns);
+  block_axpy2_kernel<<<grid, kThreads, 0, st>>>(w, v1, v0, alpha, beta, (int)n, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_shift(double* v0, double* v1, const double* w, const double* nrm, int ns, long long n,
+                               long long ld, cudaStream_t st) {
+  dim3 grid(blocks_for(n, 2), ns);
+  block_shift_kernel<<<grid, kThreads, 0, st>>>(v0, v1, w, nrm, (int)n, ld);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,71 @@
+"""Serving (irk_serve): continuous batching of single-step requests.
+
+Each result must be the same alone and in the mix (the kernels, launch shapes and reductions of a
+request do not depend on what else runs), agree with the oracle's exact step, and requests larger
+than the memory budget are refused before any work.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_06700_gb300 as pkg
+from oracle.irk import Problem, step_fastdiag
+from paper_2209_06700_gb300 import _capi
+
+pytestmark = pytest.mark.gpu
+
+# (dim, cells, degree, Q, tau, t0, arrival_s)
+MIX = [(2, 16, 2, 2, 1e-2, 0.0, 0.000), (3, 8, 2, 3, 1e-3, 0.0, 0.001), (3, 8, 4, 4, 3e-3, 0.0, 0.002),
+       (2, 32, 4, 3, 1e-4, 0.0, 0.003), (3, 16, 1, 2, 5e-3, 0.0, 0.004), (2, 8, 3, 4, 2e-3, 0.0, 0.005),
+       (3, 6, 3, 3, 1e-3, 0.0, 0.006), (2, 64, 1, 2, 1e-2, 0.0, 0.007), (3, 12, 2, 2, 7e-4, 0.0, 0.008),
+       (3, 16, 3, 3, 2e-4, 0.0, 0.009)]
+
+
+def test_alone_equals_mix_and_oracle():
+    st, res, ys = pkg.serve(MIX, max_active=6, realtime=False, outputs=True)
+    assert st == 0, [r.status for r in res]
+    assert all(r.status == 0 and r.iterations > 0 and r.latency_ms >= r.solve_ms > 0 for r in res)
+    for i, req in enumerate(MIX):
+        st1, res1, ys1 = pkg.serve([req], max_active=1, realtime=False, outputs=True)
+        assert st1 == 0
+        scale = np.abs(ys1[0]).max()
+        assert np.abs(ys[i] - ys1[0]).max() <= 1e-12 * scale, i
+        assert res1[0].iterations == res[i].iterations
+    for i in (0, 2, 6):
+        d, N, k, Q, tau, t0, _ = MIX[i]
+        prob = Problem(d, N, k, Q, tau)
+        ref = step_fastdiag(prob, prob.y0(), 0.0)
+        assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
+
+
+def test_realtime_arrivals_and_latency_accounting():
+    reqs = [(2, 16, 2, 2, 1e-2, 0.0, 0.01 * i) for i in range(6)]
+    st, res, _ = pkg.serve(reqs, max_active=2, realtime=True)
+    assert st == 0
+    for r in res:
+        assert r.queue_ms >= 0.0 and r.latency_ms >= r.queue_ms + r.setup_ms - 1e-6
+
+
+def test_request_larger_than_budget_is_refused():
+    st, res, _ = pkg.serve([(3, 16, 2, 2, 1e-3, 0.0, 0.0), (2, 8, 1, 2, 1e-3, 0.0, 0.0)], max_active=2,
+                           realtime=False, mem_budget_bytes=8e6)
+    assert res[0].status == _capi.IRK_EBUSY
+    assert res[1].status == 0
+    assert st == _capi.IRK_EBUSY
+
+
+def test_nan_input_is_reported_and_leaves_y_unchanged():
+    """Host-side fault injection: a NaN in y_n gives IRK_ENUMERIC and y is not modified."""
+    with pkg.Solver(3, 6, 2, 3, 1e-3) as s:
+        y = s.vector()
+        torch.cuda.synchronize()
+        s.interpolate_initial(y, 0.0)
+        s.synchronize()
+        idx = (2 * 6 + 1) ** 2 * 5 + (2 * 6 + 1) * 5 + 5
+        y[idx] = float("nan")
+        y0 = y.clone()
+        with pytest.raises(pkg.IrkError) as ei:
+            s.step(y, 0.0)
+        assert ei.value.code == _capi.IRK_ENUMERIC
+        assert torch.equal(torch.isnan(y), torch.isnan(y0))
+        assert torch.equal(torch.nan_to_num(y), torch.nan_to_num(y0))

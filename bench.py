@@ -155,7 +155,7 @@ def serving_measure(n_requests, realtime=True, **solver_opts):
     from synthetic import serving_stream
     reqs = serving_stream(512)[:n_requests]
     t0 = time.perf_counter()
-    st, res, _ = pkg.serve(reqs, max_active=8, realtime=realtime, **solver_opts)
+    st, res, _ = pkg.serve(reqs, max_active=16, realtime=realtime, **solver_opts)
     wall = time.perf_counter() - t0
     ok = [r for r in res if r.status == 0]
     lat = sorted(r.latency_ms for r in ok)
@@ -168,7 +168,7 @@ def serving_measure(n_requests, realtime=True, **solver_opts):
             "mean_solve_ms": sum(r.solve_ms for r in ok) / max(1, len(ok)),
             "mean_queue_ms": sum(r.queue_ms for r in ok) / max(1, len(ok)),
             "mean_iterations": sum(r.iterations for r in ok) / max(1, len(ok)),
-            "slots": 8, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0"}
+            "slots": 16, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0"}
 
 
 def run_reference(args, w):
@@ -217,7 +217,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=512)
-    ap.add_argument("--serve-baseline-requests", type=int, default=128)
+    ap.add_argument("--serve-baseline-requests", type=int, default=512)
     ap.add_argument("--op-ff", type=int, default=1, choices=[0, 1], help="float-float (1) or native FP64 (0) operator")
     ap.add_argument("--cheb-degree", type=int, default=None)
     ap.add_argument("--smoothing-range", type=float, default=None)

@@ -146,7 +146,7 @@ typedef struct {
   irk_options solver;         /* solver options of every request */
 } irk_serve_options;
 
-/* Default serving options: 8 slots, automatic budget, real time, solver defaults with restart 16. */
+/* Default serving options: 16 slots, automatic budget, real time, solver defaults with restart 16. */
 void irk_default_serve_options(irk_serve_options* opt);
 
 /* Serve `count` requests with continuous batching (not in the paper: the serving form of this

@@ -93,6 +93,9 @@ struct DiagParams {
 template <typename T>
 cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, const DiagParams<T>& D,
                               cudaStream_t st);
+// Deterministic start vector of the Lanczos estimate: 0.5 + hash(node) / 2^53 on interior nodes, zero
+// elsewhere, identical for every block.
+cudaError_t launch_hash_fill(const GridInfo& g, int nstage, double* x, cudaStream_t st);
 // out = x * D^{-1/2} (inv_sqrt = 1) or out = x * D (inv_sqrt = 0), interior nodes.
 template <typename T>
 cudaError_t launch_diag_scale(const GridInfo& g, int nstage, const T* x, T* out, const DiagParams<T>& D,

@@ -748,31 +748,22 @@ class MG final : public MGBase {
       const long long n = g.n, ldl = g.ld;
       const int nbl = std::min(reduction_blocks(n), nbred);
       // deterministic start vector on interior nodes (hash-based), same for every block
-      std::vector<double> h0((size_t)nb * ldl, 0.0);
-      for (int s = 0; s < nb; ++s)
-        for (long long e = 0; e < n; ++e) {
-          long long x = e % g.n1, y = (e / g.n1) % g.n1, z = (g.dim == 3) ? e / ((long long)g.n1 * g.n1) : 1;
-          bool in = x >= 1 && x <= g.n1 - 2 && y >= 1 && y <= g.n1 - 2 && (g.dim == 2 || (z >= 1 && z <= g.n1 - 2));
-          if (!in) continue;
-          unsigned long long hsh = (unsigned long long)(e + 1) * 0x9E3779B97F4A7C15ULL;
-          hsh ^= hsh >> 29; hsh *= 0xBF58476D1CE4E5B9ULL; hsh ^= hsh >> 32;
-          h0[(size_t)s * ldl + e] = 0.5 + (double)(hsh >> 11) * (1.0 / 9007199254740992.0);
-        }
-      IRK_CUDA(cudaMemcpyAsync(w, h0.data(), h0.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      IRK_CUDA(launch_hash_fill(g.grid(), nb, w, st));
       IRK_CUDA(cudaMemsetAsync(v0, 0, (size_t)nb * ldl * sizeof(double), st));
       IRK_CUDA(launch_block_dot(w, w, nb, n, ldl, partial, nbl, st));
       IRK_CUDA(launch_reduce_partials(partial, nb, nbl, nrm0, st, 1));
       IRK_CUDA(launch_block_shift(nullptr, v1, w, nrm0, nb, n, ldl, st));
       std::vector<double> one(nb, 1.0);
       DiagParams<double> D = make_diag_params<double>(g, nb, cfg_.cm.data(), ck_.data(), one.data());
-      OpParams<double> P = make_op_params<double>(g, nb, cfg_.cm.data(), ck_.data());
+      // the estimate's operator in float-float arithmetic (FP32 pipe), vectors and reductions in FP64
+      OpParams<ff> P = make_op_params<ff>(g, nb, cfg_.cm.data(), ck_.data());
       EpiParams<double> E;
       std::memset(&E, 0, sizeof(E));
       E.out = w;
       // symmetric form D^{-1/2} A D^{-1/2}; every block advances together, no host round trip
       for (int it = 0; it < steps; ++it) {
         IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, v1, t, D, 1, st));
-        IRK_CUDA(launch_op<double>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
+        IRK_CUDA(launch_op<ff>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
         IRK_CUDA(launch_diag_scale<double>(g.grid(), nb, w, w, D, 1, st));
         double* a_it = alpha + (size_t)it * nb;
         double* b_it = beta + (size_t)it * nb;

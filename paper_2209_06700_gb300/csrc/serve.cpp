@@ -50,7 +50,7 @@ double estimate_bytes(const irk_request& r, const irk_options& o) {
 
 extern "C" void irk_default_serve_options(irk_serve_options* o) {
   if (!o) return;
-  o->max_active = 8;
+  o->max_active = 16;
   o->mem_budget_bytes = 0.0;
   o->realtime = 1;
   irk_default_options(&o->solver);

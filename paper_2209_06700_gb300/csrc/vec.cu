@@ -134,13 +134,37 @@ __global__ void diag_scale_kernel(GridInfo g, const T* __restrict__ x, T* __rest
                                   int inv_sqrt) {
   const int s = blockIdx.y;
   const int n = (int)g.n;
+  // the diagonal factor in FP32 (this scaling only feeds the Chebyshev-interval estimate): the
+  // coefficients are converted once per thread, only the multiply by x uses the type of x
+  DiagParams<float> F;
+  F.cm[s] = (float)D.cm[s];
+  F.ck[s] = (float)D.ck[s];
+  for (int r = 0; r < kMaxDeg; ++r) { F.dmr[r] = (float)D.dmr[r]; F.dkr[r] = (float)D.dkr[r]; }
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
     const long long o = s * g.ld + e;
-    const T d = diag_at(D, s, g.dim, g.k, ix, iy, iz);
-    out[o] = inv_sqrt ? x[o] / sqrt(d) : x[o] * d;
+    const float d = diag_at(F, s, g.dim, g.k, ix, iy, iz);
+    out[o] = x[o] * (T)(inv_sqrt ? rsqrtf(d) : d);
+  }
+}
+
+__global__ void hash_fill_kernel(GridInfo g, double* __restrict__ x) {
+  const int s = blockIdx.y;
+  const int n = (int)g.n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    double v = 0.0;
+    if (interior(g.dim, g.n1, ix, iy, iz)) {
+      unsigned long long h = (unsigned long long)(e + 1) * 0x9E3779B97F4A7C15ULL;
+      h ^= h >> 29;
+      h *= 0xBF58476D1CE4E5B9ULL;
+      h ^= h >> 32;
+      v = 0.5 + (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    }
+    x[s * g.ld + e] = v;
   }
 }
 
@@ -676,6 +700,12 @@ template cudaError_t launch_diag_scale<float>(const GridInfo&, int, const float*
                                               cudaStream_t);
 template cudaError_t launch_diag_scale<double>(const GridInfo&, int, const double*, double*, const DiagParams<double>&,
                                                int, cudaStream_t);
+
+cudaError_t launch_hash_fill(const GridInfo& g, int nstage, double* x, cudaStream_t st) {
+  dim3 grid(blocks_for(g.n, 2), nstage);
+  hash_fill_kernel<<<grid, kThreads, 0, st>>>(g, x);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const double* Ky, const double* G1,
                              const double* loads, double* rhs, cudaStream_t st) {

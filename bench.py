@@ -204,6 +204,35 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def fp64_per_stage_baseline(w, cheb, units, steps=3):
+    """The same step on the plain GPU path: native FP64 operator, FP64 V-cycle, one launch per
+    stage, no graph replay.  Timed with CUDA events on its stream after one warm-up step."""
+    import torch
+    import paper_2209_06700_gb300 as pkg
+    stream = torch.cuda.Stream()
+    s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=cheb, op_ff=0,
+                   mg_precision=64, batched=0, use_graph=0)
+    try:
+        y = s.vector()
+        with torch.cuda.stream(stream):
+            s.interpolate_initial(y, 0.0)
+        s.step(y, 0.0)
+        its = []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            its.append(s.step(y, (i + 1) * w.tau).iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        s.close()
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "fgmres_iterations": sum(its) / len(its),
+            "path": "FP64 operator, FP64 multigrid, per-stage launches, no graph"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,11 +240,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=HEAT3D_K4_N32_Q3.name, choices=sorted(WORKLOADS))
+    ap.add_argument("--cells", type=int, default=None,
+                    help="override the workload's cells per axis (small cases for profiler captures)")
     ap.add_argument("--mg-precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--per-stage", action="store_true", help="per-stage launches (batched=0)")
     ap.add_argument("--variant", default="lu", choices=["lu", "diag"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-fp64-baseline", action="store_true", help="skip the per-stage FP64 GPU step baseline")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-baseline-requests", type=int, default=512)
     ap.add_argument("--op-ff", type=int, default=1, choices=[0, 1], help="float-float (1) or native FP64 (0) operator")
@@ -224,6 +258,9 @@ def main():
     ap.add_argument("--eig-safety", type=float, default=None)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.cells is not None and args.cells != w.cells:
+        import dataclasses
+        w = dataclasses.replace(w, name=f"heat{w.dim}d_k{w.degree}_n{args.cells}_q{w.Q}", cells=args.cells)
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -285,16 +322,22 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_window:
+        torch.cuda.profiler.start()
     ev0.record(stream)
     lat = []
+    reo = []
     for _ in range(args.steps):
         w0 = time.perf_counter()
         st = s.step(y, t)
         lat.append(1e3 * (time.perf_counter() - w0))
         its.append(st.iterations)
+        reo.append(st.reorth_passes)
         t += w.tau
     ev1.record(stream)
     torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     clk = clocks.stop() if clocks else None
@@ -385,7 +428,8 @@ def main():
                            "l2": "working set (Krylov basis ~3 GB) > 129 MB L2; no flush"},
                 "latency_ms": {"p50": statistics.median(lat),
                                "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},
-                "fgmres_iterations": {"mean": sum(its) / len(its), "min": min(its), "max": max(its)},
+                "fgmres_iterations": {"mean": sum(its) / len(its), "min": min(its), "max": max(its),
+                                      "gs_second_passes_mean": sum(reo) / max(1, len(reo))},
                 "e2e": {"value": units / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * s.n,
                         "d2h_bytes_per_step": 8 * s.n, "ms_per_step": e2e_step},
                 "gpu_launches": launches,
@@ -393,6 +437,8 @@ def main():
                 "roofline_smoother": roof_sm,
                 "category_ms_one_step": {k: round(v[0], 4) for k, v in cat_ms.items()},
                 "clocks": clk}
+        if world == 1 and not args.no_fp64_baseline:
+            line["gpu_fp64_per_stage_baseline"] = fp64_per_stage_baseline(w, cheb, units)
         if world == 1 and not args.no_serve:
             line["serving"] = serving_measure(args.serve_requests)
             # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)

@@ -83,6 +83,7 @@ typedef struct {
   int vcycles;          /* V-cycles applied (per block, sequential count as in Sec. 5 tables) */
   double rel_residual;  /* final ||r|| / ||rhs|| (max over DIAG blocks) */
   double ms_total;      /* host wall time of the step, ms */
+  int reorth_passes;    /* Gram-Schmidt second passes taken (the first pass cancelled too much) */
 } irk_stats;
 
 typedef struct irk_problem* irk_handle;
@@ -112,11 +113,15 @@ irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau,
 irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load,
                     irk_stats* stats);
 
-/* Advance `count` independent problems by one step each, interleaving their
- * FGMRES iterations so that their kernels overlap on the device (continuous
- * batching across requests).  hs[i], ys[i], t_ns[i] as in irk_step; per_item
- * (host, count entries) receives each problem's status.  Returns IRK_OK if
- * every item succeeded, else the first failing status. */
+/* Advance `count` independent problems by one step each.  hs[i], ys[i],
+ * t_ns[i] as in irk_step (built-in source).  Distinct handles run concurrently
+ * on host threads, each enqueueing on its own handle's stream, so their FGMRES
+ * iterations interleave and their kernels overlap on the device (batching
+ * across requests; give each handle its own stream for overlap).  Items that
+ * repeat a handle run in array order.  per_item (host, count entries, may be
+ * NULL) receives each item's status.  Returns IRK_OK if every item
+ * succeeded, else the status of the lowest failing index; failed items leave
+ * their y unchanged as in irk_step. */
 irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count,
                            irk_status* per_item);
 

@@ -10,7 +10,7 @@ from . import _capi
 from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkRequest, IrkResult,
                     IrkServeOptions, IrkStats, TABLEAU_FIELDS, check, lib)
 
-__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options", "serve"]
+__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options", "serve", "solve_batch"]
 
 
 def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, **solver_opts):
@@ -48,6 +48,19 @@ def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=F
             ptrs[i] = y.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     status = lib().irk_serve(arr, n, ctypes.byref(o), res, ptrs)
     return status, list(res), ys
+
+
+def solve_batch(solvers, ys, t_ns):
+    """irk_solve_batch over Solver objects and their device vectors; returns (status, per-item statuses)."""
+    n = len(solvers)
+    if len(ys) != n or len(t_ns) != n:
+        raise ValueError("solvers, ys and t_ns differ in length")
+    hs = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+    yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+    ts = (ctypes.c_double * n)(*[float(t) for t in t_ns])
+    per = (ctypes.c_int * n)()
+    status = lib().irk_solve_batch(hs, yp, ts, n, per)
+    return status, list(per)
 
 
 def _ptr(t):

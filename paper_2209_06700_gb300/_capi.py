@@ -43,7 +43,7 @@ class IrkResult(ctypes.Structure):
 
 class IrkStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("vcycles", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("reorth_passes", ctypes.c_int)]
 
 
 class IrkServeOptions(ctypes.Structure):

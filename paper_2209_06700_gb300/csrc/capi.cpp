@@ -10,12 +10,16 @@
 //                 alpha M + tau K]] with PRESB (Eq. presb:p: two sequential
 //                 V-cycles on (alpha + beta) M + tau K).
 // Then y_{n+1} = y_n + tau sum_i b_i k_i (Sec. 1).
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "profiler.h"
@@ -185,6 +189,7 @@ Status step_lu(irk_problem* h, double* y, double t_n, const double* loads, irk_s
     stats->iterations = res.iterations;
     stats->vcycles = res.iterations;
     stats->rel_residual = res.rel_residual;
+    stats->reorth_passes = res.reorth;
   }
   if (!res.converged) return Status::Err(IRK_ENOTCONV, "FGMRES did not converge");
   IRK_LAUNCH(PROF_RHS, launch_update(h->fine.grid(), h->Q, h->kst, h->tab.b.data(), h->tau, y, h->st));
@@ -198,7 +203,7 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
   // rtilde = (T^{-1} (x) I) rhs  -> tq
   CombineParams Cin = combine_params(Q, Q, h->tab.Tinv.data());
   IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->rhs, nullptr, h->tq, g.n, g.ld, Cin, h->st));
-  int iters = 0, vc = 0;
+  int iters = 0, vc = 0, reo = 0;
   double worst = 0.0;
   for (size_t bi = 0; bi < h->tab.blocks.size(); ++bi) {
     const auto& blk = h->tab.blocks[bi];
@@ -249,17 +254,18 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
     FGMRESResult res;
     IRK_TRY(fgmres_solve(w, op, prec, bvec, xvec, h->opt.rtol, h->opt.max_it, h->st, res));
     iters += res.iterations;
+    reo += res.reorth;
     vc += res.iterations * (blk.pair ? 2 : 1);
     worst = std::max(worst, res.rel_residual);
     if (!res.converged) {
-      if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; }
+      if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; stats->reorth_passes = reo; }
       return Status::Err(IRK_ENOTCONV, "FGMRES did not converge on a diagonal block");
     }
   }
   // k = (T (x) I) x~
   CombineParams Cout = combine_params(Q, Q, h->tab.T.data());
   IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->kst, nullptr, h->tq, g.n, g.ld, Cout, h->st));
-  if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; }
+  if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; stats->reorth_passes = reo; }
   IRK_LAUNCH(PROF_RHS, launch_update(g.grid(), Q, h->tq, h->tab.b.data(), h->tau, y, h->st));
   return Status::Ok();
 }
@@ -462,11 +468,52 @@ irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_loa
 
 irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count, irk_status* per_item) {
   if (count < 0 || (count > 0 && (!hs || !ys || !t_ns))) return IRK_EINVAL;
+  if (count == 0) return IRK_OK;
+  // Items of one handle run in order on one host thread (a handle is not thread-safe); distinct
+  // handles run on their own threads, so their streams' kernels overlap and each thread's
+  // per-iteration residual read-back waits only for its own stream.
+  std::vector<std::vector<int>> groups;
+  {
+    std::map<irk_handle, int> gid;
+    for (int i = 0; i < count; ++i) {
+      auto it = gid.find(hs[i]);
+      if (it == gid.end()) {
+        it = gid.emplace(hs[i], (int)groups.size()).first;
+        groups.emplace_back();
+      }
+      groups[it->second].push_back(i);
+    }
+  }
+  std::vector<irk_status> st(count, IRK_OK);
+  auto run_group = [&](int g) {
+    const std::vector<int>& items = groups[g];
+    if (hs[items[0]]) cudaSetDevice(hs[items[0]]->device);
+    for (int i : items) st[i] = irk_step(hs[i], ys[i], t_ns[i], nullptr, nullptr);
+  };
+  const int nthreads = (int)std::min<size_t>(groups.size(), 64);
+  if (nthreads <= 1) {
+    for (size_t g = 0; g < groups.size(); ++g) run_group((int)g);
+  } else {
+    std::atomic<int> next{0};
+    int device = 0;
+    cudaGetDevice(&device);
+    std::vector<std::thread> pool;
+    try {
+      for (int t = 0; t < nthreads; ++t)
+        pool.emplace_back([&]() {
+          cudaSetDevice(device);
+          for (int g; (g = next.fetch_add(1)) < (int)groups.size();) run_group(g);
+        });
+    } catch (...) {
+      // could not start every thread: the started ones (or this thread) take the remaining groups
+    }
+    for (int g; (g = next.fetch_add(1)) < (int)groups.size();) run_group(g);
+    for (auto& th : pool) th.join();
+  }
   irk_status first = IRK_OK;
   for (int i = 0; i < count; ++i) {
-    irk_status s = irk_step(hs[i], ys[i], t_ns[i], nullptr, nullptr);
-    if (per_item) per_item[i] = s;
-    if (s != IRK_OK && first == IRK_OK) first = s;
+    if (per_item) per_item[i] = st[i];
+    if (st[i] != IRK_OK && first == IRK_OK) first = st[i];
   }
   return first;
 }

@@ -123,6 +123,7 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const
       const double hn = w.hvals[kNrm];
       if (!std::isfinite(hn)) return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
       const bool redo = w.hvals[kH2 + nv] < kEta * kEta * w.hvals[kN0];
+      res.reorth += redo ? 1 : 0;
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + (redo ? w.hvals[kH2 + i] : 0.0);
       H[(size_t)(j + 1) * m + j] = hn;
       if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_inv(wv, w.dvals + kNrm, wv, len, st));

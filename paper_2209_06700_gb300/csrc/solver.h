@@ -129,7 +129,7 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
 double* pinned_block_acquire();
 void pinned_block_release(double* p);
 
-struct FGMRESResult { int iterations = 0; double rel_residual = 0; bool converged = false; };
+struct FGMRESResult { int iterations = 0; int reorth = 0; double rel_residual = 0; bool converged = false; };
 
 using ApplyFn = std::function<Status(const double* in, double* out)>;
 

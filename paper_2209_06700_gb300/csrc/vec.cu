@@ -11,6 +11,7 @@
 //   applied one axis at a time.
 // * Dense coarse-grid solve with a precomputed FP64 inverse.
 #include <algorithm>
+#include <cstdint>
 
 #include "kernels.h"
 
@@ -135,17 +136,30 @@ __global__ void diag_scale_kernel(GridInfo g, const T* __restrict__ x, T* __rest
   const int s = blockIdx.y;
   const int n = (int)g.n;
   // the diagonal factor in FP32 (this scaling only feeds the Chebyshev-interval estimate): the
-  // coefficients are converted once per thread, only the multiply by x uses the type of x
-  DiagParams<float> F;
-  F.cm[s] = (float)D.cm[s];
-  F.ck[s] = (float)D.ck[s];
-  for (int r = 0; r < kMaxDeg; ++r) { F.dmr[r] = (float)D.dmr[r]; F.dkr[r] = (float)D.dkr[r]; }
+  // 1D diagonals are converted once per block into shared memory, only the multiply by x uses
+  // the type of x
+  __shared__ float sdm[kMaxDeg], sdk[kMaxDeg];
+  if (threadIdx.x < kMaxDeg) {
+    sdm[threadIdx.x] = (float)D.dmr[threadIdx.x];
+    sdk[threadIdx.x] = (float)D.dkr[threadIdx.x];
+  }
+  __syncthreads();
+  const float cm = (float)D.cm[s], ck = (float)D.ck[s];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords(e, g.dim, g.n1, ix, iy, iz);
     if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
     const long long o = s * g.ld + e;
-    const float d = diag_at(F, s, g.dim, g.k, ix, iy, iz);
+    const int rx = ix % g.k, ry = iy % g.k;
+    const float mx = sdm[rx], my = sdm[ry], kx = sdk[rx], ky = sdk[ry];
+    float d;
+    if (g.dim == 3) {
+      const int rz = iz % g.k;
+      const float mz = sdm[rz], kz = sdk[rz];
+      d = cm * (mx * my * mz) + ck * (kx * my * mz + mx * ky * mz + mx * my * kz);
+    } else {
+      d = cm * (mx * my) + ck * (kx * my + mx * ky);
+    }
     out[o] = x[o] * (T)(inv_sqrt ? rsqrtf(d) : d);
   }
 }
@@ -519,49 +533,106 @@ __global__ void scale_kernel(const double* __restrict__ x, double a, double* __r
 }
 
 // ------------------------------------------------------------ transfers
-template <typename T, int AXIS, bool RESTRICT>
-__global__ void __launch_bounds__(kThreads) transfer_axis_kernel(const T* __restrict__ in, T* __restrict__ out,
+// One 1D pass of the Q_k nodal embedding P (restriction applies P^T) along AXIS, one thread per
+// coarse cell of a grid line.  On a coarse cell cc the fine nodes 2Kcc + m (m = 0..2K) take
+// sum_i Pc[m][i] u_c(Kcc + i) (i = 0..K); the coarse vertex Kcc collects from the fine nodes of
+// both cells that share it.  K and AXIS are compile-time, so every Pc coefficient is a uniform
+// constant operand and each thread's loads along the line are unrolled.
+template <typename T, int K, int AXIS>
+struct LineMap {
+  // thread t -> (coarse cell cc, line bases in and out, stride along the axis in and out)
+  __device__ __forceinline__ static void map(int t, int Nc, int din0, int din1, int dout0, int dout1, int& cc,
+                                              long long& bin, long long& bout, int& sin_, int& sout) {
+    if (AXIS == 0) {
+      cc = t % Nc;
+      const int r = t / Nc;  // row (o1, o2), the same in both arrays
+      bin = (long long)r * din0;
+      bout = (long long)r * dout0;
+      sin_ = sout = 1;
+    } else if (AXIS == 1) {
+      const int o0 = t % din0;  // din0 == dout0
+      const int t2 = t / din0;
+      cc = t2 % Nc;
+      const int o2 = t2 / Nc;
+      bin = o0 + (long long)o2 * din0 * din1;
+      bout = o0 + (long long)o2 * dout0 * dout1;
+      sin_ = sout = din0;
+    } else {
+      const int plane = din0 * din1;  // == dout0 * dout1
+      const int pidx = t % plane;
+      cc = t / plane;
+      bin = bout = pidx;
+      sin_ = sout = plane;
+    }
+  }
+};
+
+template <typename T, int K, int AXIS, bool RESTRICT>
+__global__ void __launch_bounds__(kThreads) transfer_cell_kernel(const T* __restrict__ in, T* __restrict__ out,
                                                                  long long ld_in, long long ld_out, int din0, int din1,
-                                                                 int dout0, int dout1, int dout2, int accumulate,
+                                                                 int dout0, int dout1, int nthreads, int accumulate,
                                                                  const TransferParams P) {
+  constexpr int KP = K + 1;
   const int s = blockIdx.y;
-  const int nout = dout0 * dout1 * dout2;
-  const int k = P.k, Nc = P.Nc, p = k + 1;
-  const int st = (AXIS == 0) ? 1 : (AXIS == 1) ? din0 : din0 * din1;
-  const int ndc = (AXIS == 0) ? dout0 : (AXIS == 1) ? dout1 : dout2;
+  const int Nc = P.Nc;
   const T* __restrict__ src0 = in + s * ld_in;
   T* __restrict__ dst0 = out + s * ld_out;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nout; e += gridDim.x * blockDim.x) {
-    const int o0 = e % dout0;
-    const int t = e / dout0;
-    const int o1 = t % dout1, o2 = t / dout1;
-    int ca, base;
-    if (AXIS == 0) { ca = o0; base = o1 * din0 + o2 * din0 * din1; }
-    else if (AXIS == 1) { ca = o1; base = o0 + o2 * din0 * din1; }
-    else { ca = o2; base = o0 + o1 * din0; }
-    const T* src = src0 + base;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nthreads; t += gridDim.x * blockDim.x) {
+    int cc, si, so;
+    long long bi, bo;
+    LineMap<T, K, AXIS>::map(t, Nc, din0, din1, dout0, dout1, cc, bi, bo, si, so);
+    const T* src = src0 + bi;
+    T* dst = dst0 + bo;
     // arithmetic in the element type (FP32 for the FP32 multigrid)
-    const T* Pc = (sizeof(T) == 4) ? reinterpret_cast<const T*>(P.Pcf) : reinterpret_cast<const T*>(P.Pc);
-    T acc = T(0);
+#define IRK_PC(m, i) ((sizeof(T) == 4) ? (T)P.Pcf[(m) * KP + (i)] : (T)P.Pc[(m) * KP + (i)])
     if (RESTRICT) {
-      // coarse index ca = k*cc + i; fine nodes of coarse cell cc are 2k*cc + m, m = 0..2k
-      if (ca == 0 || ca == ndc - 1) continue;  // coarse boundary stays zero
-      const int cc = ca / k, i = ca - cc * k;
-      if (i != 0) {
-        for (int m = 0; m <= 2 * k; ++m) acc += Pc[m * p + i] * src[(2 * k * cc + m) * st];
-      } else {
-        for (int m = 0; m < 2 * k; ++m) acc += Pc[m * p + k] * src[(2 * k * (cc - 1) + m) * st];
-        for (int m = 0; m <= 2 * k; ++m) acc += Pc[m * p + 0] * src[(2 * k * cc + m) * st];
+      T f[4 * K + 1];  // fine nodes 2K(cc-1) .. 2K(cc+1); the first 2K only for the vertex, cc > 0
+#pragma unroll
+      for (int j = 0; j < 2 * K; ++j) f[j] = (cc > 0) ? src[(long long)(2 * K * (cc - 1) + j) * si] : T(0);
+#pragma unroll
+      for (int j = 2 * K; j <= 4 * K; ++j) f[j] = src[(long long)(2 * K * (cc - 1) + j) * si];
+      T r[K];
+      {
+        T acc = T(0);
+        if (cc > 0) {
+#pragma unroll
+          for (int m = 0; m < 2 * K; ++m) acc += IRK_PC(m, K) * f[m];
+#pragma unroll
+          for (int m = 0; m <= 2 * K; ++m) acc += IRK_PC(m, 0) * f[2 * K + m];
+        }
+        r[0] = acc;  // coarse boundary node 0 stays zero
       }
+#pragma unroll
+      for (int i = 1; i < K; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m <= 2 * K; ++m) acc += IRK_PC(m, i) * f[2 * K + m];
+        r[i] = acc;
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        T* d = dst + (long long)(K * cc + i) * so;
+        if (accumulate) *d += r[i];
+        else *d = r[i];
+      }
+      if (cc == Nc - 1 && !accumulate) dst[(long long)(K * Nc) * so] = T(0);  // coarse boundary node
     } else {
-      int cc = ca / (2 * k);
-      if (cc > Nc - 1) cc = Nc - 1;
-      const int m = ca - 2 * k * cc;
-      for (int i = 0; i <= k; ++i) acc += Pc[m * p + i] * src[(k * cc + i) * st];
+      T c[KP];
+#pragma unroll
+      for (int i = 0; i <= K; ++i) c[i] = src[(long long)(K * cc + i) * si];
+      const int mend = (cc == Nc - 1) ? 2 * K : 2 * K - 1;  // the last cell also owns the end node
+#pragma unroll
+      for (int m = 0; m <= 2 * K; ++m) {
+        if (m > mend) break;
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i <= K; ++i) acc += IRK_PC(m, i) * c[i];
+        T* d = dst + (long long)(2 * K * cc + m) * so;
+        if (accumulate) *d += acc;
+        else *d = acc;
+      }
     }
-    T* dst = dst0 + e;
-    if (accumulate) *dst += acc;
-    else *dst = acc;
+#undef IRK_PC
   }
 }
 
@@ -846,15 +917,33 @@ template <typename T>
 cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_in, long long ld_out, const int din[3],
                                  const int dout[3], int axis, int restrict_mode, int accumulate,
                                  const TransferParams& P, cudaStream_t st) {
-  const long long nout = (long long)dout[0] * dout[1] * dout[2];
-  dim3 grid(blocks_for(nout, 2), nstage);
-#define IRK_TR(AX, R) transfer_axis_kernel<T, AX, R><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], \
-                                                                             dout[0], dout[1], dout[2], accumulate, P)
-  if (restrict_mode) {
-    if (axis == 0) IRK_TR(0, true); else if (axis == 1) IRK_TR(1, true); else IRK_TR(2, true);
-  } else {
-    if (axis == 0) IRK_TR(0, false); else if (axis == 1) IRK_TR(1, false); else IRK_TR(2, false);
+  if (P.k < 1 || P.k > kMaxDeg || axis < 0 || axis > 2) return cudaErrorInvalidValue;
+  // threads: one per coarse cell of every grid line along `axis`
+  const long long others = (long long)dout[0] * dout[1] * dout[2] / (axis == 0 ? dout[0] : axis == 1 ? dout[1] : dout[2]);
+  const long long nthreads = others * P.Nc;
+  if (nthreads <= 0) return cudaSuccess;
+  if (nthreads > INT32_MAX) return cudaErrorInvalidValue;
+  dim3 grid(blocks_for(nthreads), nstage);
+#define IRK_TR(KK, AX, R)                                                                                  \
+  transfer_cell_kernel<T, KK, AX, R><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], dout[0], \
+                                                                dout[1], (int)nthreads, accumulate, P)
+#define IRK_TR_AX(KK)                                                          \
+  if (restrict_mode) {                                                         \
+    if (axis == 0) IRK_TR(KK, 0, true);                                        \
+    else if (axis == 1) IRK_TR(KK, 1, true);                                   \
+    else IRK_TR(KK, 2, true);                                                  \
+  } else {                                                                     \
+    if (axis == 0) IRK_TR(KK, 0, false);                                       \
+    else if (axis == 1) IRK_TR(KK, 1, false);                                  \
+    else IRK_TR(KK, 2, false);                                                 \
   }
+  switch (P.k) {
+    case 1: IRK_TR_AX(1); break;
+    case 2: IRK_TR_AX(2); break;
+    case 3: IRK_TR_AX(3); break;
+    default: IRK_TR_AX(4); break;
+  }
+#undef IRK_TR_AX
 #undef IRK_TR
   return cudaGetLastError();
 }

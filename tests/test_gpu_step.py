@@ -13,7 +13,7 @@ import torch
 import paper_2209_06700_gb300 as pkg
 from oracle.irk import FastDiag, Problem, step_fastdiag
 from oracle.tableau import lu_preconditioner_factors, real_jordan
-from synthetic import HEAT2D_K2_N16_Q2, HEAT3D_K4_N32_Q3, uniform_vectors, zero_boundary
+from synthetic import HEAT2D_K2_N16_Q2, HEAT3D_K2_N48_Q3, HEAT3D_K4_N32_Q3, heat3d_k3_n64, uniform_vectors, zero_boundary
 from tests.gpu_util import from_dev, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -150,3 +150,23 @@ def test_full_size_heat3d_k4_n32_q3_one_step():
     w = HEAT3D_K4_N32_Q3
     err, its = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=1)
     assert err <= YTOL, (err, its)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Q", [2, 3, 4, 5])
+def test_full_size_heat3d_k3_n64_one_step(Q):
+    """7,189,057 nodes, all Q stages batched, V-cycle replayed from a CUDA graph (side stream)."""
+    w = heat3d_k3_n64(Q)
+    err, its = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=1, stream=torch.cuda.Stream())
+    assert err <= YTOL, (err, its)
+
+
+@pytest.mark.slow
+def test_full_size_heat3d_k2_n48_q3_direct_diag_and_lu():
+    """912,673 nodes: the directly diagonalised variant (real block + PRESB pair) and the LU
+    variant both give the exact IRK step, two steps each."""
+    w = HEAT3D_K2_N48_Q3
+    err_lu, its_lu = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=2)
+    err_dg, its_dg = _run(w.dim, w.cells, w.degree, w.Q, w.tau, nsteps=2, variant=pkg.IRK_VARIANT_DIAG)
+    assert err_lu <= YTOL, (err_lu, its_lu)
+    assert err_dg <= YTOL, (err_dg, its_dg)

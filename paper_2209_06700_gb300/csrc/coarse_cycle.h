@@ -13,6 +13,7 @@ constexpr int kFusedMaxNodes = 4913;  // a level is fused when it has at most 17
 
 struct CoarseLevel {
   int N, n1, n;                         // cells per axis, nodes per axis, nodes
+  unsigned magic;                       // coarse_cycle_magic(n1): q / n1 by a high multiply
   float me[5][5], ke[5][5];             // element matrices scaled by h and 1/h
   float dmr[kMaxDeg], dkr[kMaxDeg];     // 1D diagonals by node position mod k
   float c1[kMaxChebDegree][kMaxQ], c2[kMaxChebDegree][kMaxQ];  // Chebyshev recurrence per step, block
@@ -32,6 +33,7 @@ struct CoarseParams {
 };
 
 size_t coarse_cycle_smem(const CoarseParams& P, int elem_size);
+unsigned coarse_cycle_magic(int n);   // ceil(2^32 / n) for n >= 2
 template <typename T>
 cudaError_t launch_coarse_cycle(const CoarseParams& P, int dim, int k, cudaStream_t st);
 

@@ -623,6 +623,7 @@ class MG final : public MGBase {
       C.N = L.g.N;
       C.n1 = L.g.n1;
       C.n = (int)L.g.n;
+      C.magic = coarse_cycle_magic(C.n1);
       for (int a = 0; a < 5; ++a)
         for (int b = 0; b < 5; ++b) { C.me[a][b] = (float)L.g.me[a][b]; C.ke[a][b] = (float)L.g.ke[a][b]; }
       for (int r = 0; r < kMaxDeg; ++r) { C.dmr[r] = (float)L.g.dmr[r]; C.dkr[r] = (float)L.g.dkr[r]; }

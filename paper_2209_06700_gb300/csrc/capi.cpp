@@ -20,6 +20,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "profiler.h"
@@ -73,98 +74,113 @@ CombineParams combine_params(int nout, int nin, const double* Da, const double* 
   return C;
 }
 
-// FP64-accurate operator launch on the fine mesh: float-float (default) or native FP64.
-// cat: PROF_APPLY64 for the stage operator, PROF_RHS for K y_n.
-Status launch_apply64(irk_problem* h, const double* u, int ns, const double* cm, const double* ck, int epi,
-                      const EpiParams<double>& E, int cat = PROF_APPLY64) {
-  if (h->opt.op_ff) {
-    OpParams<ff> P = make_op_params<ff>(h->fine, ns, cm, ck);
-    IRK_LAUNCH(cat, launch_op<ff>(h->dim, h->k, ns, u, P, epi, E, h->st));
-  } else {
-    OpParams<double> P = make_op_params<double>(h->fine, ns, cm, ck);
-    IRK_LAUNCH(cat, launch_op<double>(h->dim, h->k, ns, u, P, epi, E, h->st));
-  }
-  return Status::Ok();
-}
+// The outer solver's stage vectors are ff (float-float pairs, default: every FP64-accurate
+// operation on the FP32 pipe) or FP64 (op_ff = 0, the plain FP64 path).  Buffers are allocated
+// as 8-byte elements and viewed with the handle's storage type.
+template <typename S> S* as(double* p) { return reinterpret_cast<S*>(p); }
 
-// v = (Cm (x) M + Ck (x) K) u on the fine mesh, FP64, ns stage vectors
-Status apply_general(irk_problem* h, const double* u, double* v, int ns, const double* Cm, const double* Ck) {
-  if (ns > h->nslots) return Status::Err(IRK_EINVAL, "too many stage vectors for this handle");
-  EpiParams<double> E;
+// FP64-accurate operator launch on the fine mesh.  cat: PROF_APPLY64 for the stage operator,
+// PROF_RHS for K y_n.
+template <typename S>
+Status launch_apply64(irk_problem* h, const S* u, int ns, const double* cm, const double* ck, int epi, S* out,
+                      S* out2, int cat = PROF_APPLY64) {
+  using T = typename std::conditional<std::is_same<S, ff>::value, ff, double>::type;
+  OpParams<T> P = make_op_params<T>(h->fine, ns, cm, ck);
+  EpiParams<S> E;
   std::memset(&E, 0, sizeof(E));
-  E.out = h->Mu;
-  E.out2 = h->Ku;
-  IRK_TRY(launch_apply64(h, u, ns, nullptr, nullptr, EPI_DUAL, E));
-  CombineParams C = combine_params(ns, ns, Cm, Ck, ns);
-  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->Mu, h->Ku, v, h->fine.n, h->fine.ld, C, h->st));
+  E.out = out;
+  E.out2 = out2;
+  IRK_LAUNCH(cat, launch_op<T>(h->dim, h->k, ns, u, P, epi, E, h->st));
   return Status::Ok();
 }
 
-Status apply_calA(irk_problem* h, const double* u, double* v) {
+// v = (Cm (x) M + Ck (x) K) u on the fine mesh, FP64-accurate, ns stage vectors
+template <typename S>
+Status apply_general(irk_problem* h, const S* u, S* v, int ns, const double* Cm, const double* Ck) {
+  if (ns > h->nslots) return Status::Err(IRK_EINVAL, "too many stage vectors for this handle");
+  S* Mu = as<S>(h->Mu);
+  S* Ku = as<S>(h->Ku);
+  IRK_TRY(launch_apply64<S>(h, u, ns, nullptr, nullptr, EPI_DUAL, Mu, Ku));
+  CombineParams C = combine_params(ns, ns, Cm, Ck, ns);
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, S>(Mu, Ku, v, h->fine.n, h->fine.ld, C, h->st));
+  return Status::Ok();
+}
+
+template <typename S>
+Status apply_calA(irk_problem* h, const S* u, S* v) {
   const int Q = h->Q;
   std::vector<double> Ck((size_t)Q * Q, 0.0);
   for (int i = 0; i < Q; ++i) Ck[(size_t)i * Q + i] = h->tau;
-  return apply_general(h, u, v, Q, h->tab.Ainv.data(), Ck.data());
+  return apply_general<S>(h, u, v, Q, h->tab.Ainv.data(), Ck.data());
+}
+
+// copy-with-combination between the solver's stage vectors and an MG's fine buffers:
+// mg_b = (D (x) I) in (+ Db in2), out = (D (x) I) mg_x (+ Db add), cast to the MG precision
+template <typename S>
+Status to_mg_combine(irk_problem* h, MGBase* mg, const S* in, const S* in2, const CombineParams& C) {
+  const LevelGeom& g = h->fine;
+  if (mg->elem_size() == 4)
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, float>(in, in2, (float*)mg->fine_b(), g.n, g.ld, C, h->st));
+  else
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, double>(in, in2, (double*)mg->fine_b(), g.n, g.ld, C, h->st));
+  return Status::Ok();
+}
+template <typename S>
+Status from_mg_combine(irk_problem* h, MGBase* mg, S* out, const S* add, const CombineParams& C) {
+  const LevelGeom& g = h->fine;
+  if (mg->elem_size() == 4)
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<float, S, S>((const float*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
+  else
+    IRK_LAUNCH(PROF_COMBINE,
+               launch_combine<double, S, S>((const double*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
+  return Status::Ok();
 }
 
 // z = P^{-1} r (Eq. irk:P) with the configured MG precision
-Status precondition_lu(irk_problem* h, const double* r, double* z) {
+template <typename S>
+Status precondition_lu(irk_problem* h, const S* r, S* z) {
   const int Q = h->Q;
-  const LevelGeom& g = h->fine;
   CombineParams Cin = combine_params(Q, Q, h->tab.Sinv.data());
   CombineParams Cout = combine_params(Q, Q, h->tab.S.data());
-  if (h->mg->elem_size() == 4) {
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, float>(r, nullptr, (float*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
-    IRK_TRY(h->mg->vcycle_top(h->st, h->opt.use_graph != 0));
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<float, double>((const float*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
-  } else {
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(r, nullptr, (double*)h->mg->fine_b(), g.n, g.ld, Cin, h->st));
-    IRK_TRY(h->mg->vcycle_top(h->st, h->opt.use_graph != 0));
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>((const double*)h->mg->fine_x(), nullptr, z, g.n, g.ld, Cout, h->st));
-  }
-  return Status::Ok();
+  IRK_TRY(to_mg_combine<S>(h, h->mg.get(), r, nullptr, Cin));
+  IRK_TRY(h->mg->vcycle_top(h->st, h->opt.use_graph != 0));
+  return from_mg_combine<S>(h, h->mg.get(), z, nullptr, Cout);
 }
 
-// copy-with-cast between FP64 block vectors and an MG's fine buffer (1 vector)
-Status to_mg(irk_problem* h, MGBase* mg, const double* in, double scale_a, const double* in2, double scale_b) {
-  const LevelGeom& g = h->fine;
-  CombineParams C;
-  std::memset(&C, 0, sizeof(C));
-  C.nout = 1;
-  C.nina = 1;
-  C.Da[0] = scale_a;
-  C.ninb = in2 ? 1 : 0;
-  C.Db[0] = scale_b;
-  if (mg->elem_size() == 4)
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, float>(in, in2, (float*)mg->fine_b(), g.n, g.ld, C, h->st));
-  else
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(in, in2, (double*)mg->fine_b(), g.n, g.ld, C, h->st));
-  return Status::Ok();
-}
-
-Status from_mg(irk_problem* h, MGBase* mg, double* out, double sa, const double* add, double sb) {
-  const LevelGeom& g = h->fine;
+CombineParams scale_pair(double sa, bool with_b, double sb) {
   CombineParams C;
   std::memset(&C, 0, sizeof(C));
   C.nout = 1;
   C.nina = 1;
   C.Da[0] = sa;
-  C.ninb = add ? 1 : 0;
+  C.ninb = with_b ? 1 : 0;
   C.Db[0] = sb;
-  if (mg->elem_size() == 4)
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<float, double>((const float*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
-  else
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>((const double*)mg->fine_x(), add, out, g.n, g.ld, C, h->st));
-  return Status::Ok();
+  return C;
 }
 
-Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* loads, double* rhs) {
+// mg_b = sa in (+ sb in2)  /  out = sa mg_x (+ sb add), one vector
+template <typename S>
+Status to_mg(irk_problem* h, MGBase* mg, const S* in, double sa, const S* in2, double sb) {
+  return to_mg_combine<S>(h, mg, in, in2, scale_pair(sa, in2 != nullptr, sb));
+}
+template <typename S>
+Status from_mg(irk_problem* h, MGBase* mg, S* out, double sa, const S* add, double sb) {
+  return from_mg_combine<S>(h, mg, out, add, scale_pair(sa, add != nullptr, sb));
+}
+
+// rhs = (A^{-1} (x) I)(g - 1 (x) K y_n), y_n FP64 (the caller's vector)
+template <typename S>
+Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* loads, S* rhs) {
   const LevelGeom& g = h->fine;
   double zero = 0.0, one = 1.0;
-  EpiParams<double> E;
-  std::memset(&E, 0, sizeof(E));
-  E.out = h->Ky;
-  IRK_TRY(launch_apply64(h, y, 1, &zero, &one, EPI_STORE, E, PROF_RHS));
+  const S* yin;
+  if constexpr (std::is_same<S, ff>::value) {
+    IRK_LAUNCH(PROF_RHS, launch_to_ff(y, as<ff>(h->Mu), g.ld, h->st));
+    yin = as<ff>(h->Mu);
+  } else {
+    yin = y;
+  }
+  IRK_TRY(launch_apply64<S>(h, yin, 1, &zero, &one, EPI_STORE, as<S>(h->Ky), nullptr, PROF_RHS));
   RhsParams R;
   std::memset(&R, 0, sizeof(R));
   R.Q = h->Q;
@@ -175,16 +191,19 @@ Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* load
     const double t = t_n + h->tab.c[j] * h->tau;
     R.phi[j] = h->dim * pi * pi * std::cos(t) - std::sin(t);
   }
-  IRK_LAUNCH(PROF_RHS, launch_stage_rhs(g.grid(), R, h->Ky, h->G1, loads, rhs, h->st));
+  IRK_LAUNCH(PROF_RHS, launch_stage_rhs<S>(g.grid(), R, as<S>(h->Ky), h->G1, loads, rhs, h->st));
   return Status::Ok();
 }
 
+template <typename S>
 Status step_lu(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
-  IRK_TRY(stage_rhs(h, y, t_n, loads, h->rhs));
-  ApplyFn op = [h](const double* in, double* out) { return apply_calA(h, in, out); };
-  ApplyFn prec = [h](const double* in, double* out) { return precondition_lu(h, in, out); };
+  S* rhs = as<S>(h->rhs);
+  S* kst = as<S>(h->kst);
+  IRK_TRY(stage_rhs<S>(h, y, t_n, loads, rhs));
+  ApplyFn<S> op = [h](const S* in, S* out) { return apply_calA<S>(h, in, out); };
+  ApplyFn<S> prec = [h](const S* in, S* out) { return precondition_lu<S>(h, in, out); };
   FGMRESResult res;
-  IRK_TRY(fgmres_solve(h->fw, op, prec, h->rhs, h->kst, h->opt.rtol, h->opt.max_it, h->st, res));
+  IRK_TRY(fgmres_solve<S>(h->fw, op, prec, rhs, kst, h->opt.rtol, h->opt.max_it, h->st, res));
   if (stats) {
     stats->iterations = res.iterations;
     stats->vcycles = res.iterations;
@@ -192,17 +211,21 @@ Status step_lu(irk_problem* h, double* y, double t_n, const double* loads, irk_s
     stats->reorth_passes = res.reorth;
   }
   if (!res.converged) return Status::Err(IRK_ENOTCONV, "FGMRES did not converge");
-  IRK_LAUNCH(PROF_RHS, launch_update(h->fine.grid(), h->Q, h->kst, h->tab.b.data(), h->tau, y, h->st));
+  IRK_LAUNCH(PROF_RHS, launch_update<S>(h->fine.grid(), h->Q, kst, h->tab.b.data(), h->tau, y, h->st));
   return Status::Ok();
 }
 
+template <typename S>
 Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
   const int Q = h->Q;
   const LevelGeom& g = h->fine;
-  IRK_TRY(stage_rhs(h, y, t_n, loads, h->rhs));
+  S* rhs = as<S>(h->rhs);
+  S* tq = as<S>(h->tq);
+  S* kst = as<S>(h->kst);
+  IRK_TRY(stage_rhs<S>(h, y, t_n, loads, rhs));
   // rtilde = (T^{-1} (x) I) rhs  -> tq
   CombineParams Cin = combine_params(Q, Q, h->tab.Tinv.data());
-  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->rhs, nullptr, h->tq, g.n, g.ld, Cin, h->st));
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, S>(rhs, nullptr, tq, g.n, g.ld, Cin, h->st));
   int iters = 0, vc = 0, reo = 0;
   double worst = 0.0;
   for (size_t bi = 0; bi < h->tab.blocks.size(); ++bi) {
@@ -213,46 +236,46 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
     w.ns = ns;
     w.len = (long long)ns * g.ld;
     w.nb = reduction_blocks(w.len);
-    double* bvec = h->tq + (size_t)blk.offset * g.ld;
-    double* xvec = h->kst + (size_t)blk.offset * g.ld;
-    ApplyFn op, prec;
+    S* bvec = tq + (size_t)blk.offset * g.ld;
+    S* xvec = kst + (size_t)blk.offset * g.ld;
+    ApplyFn<S> op, prec;
     const double al = blk.alpha, be = blk.beta, tau = h->tau;
     if (!blk.pair) {
-      op = [h, al](const double* in, double* out) {
+      op = [h, al](const S* in, S* out) {
         const double Cm[1] = {al}, Ck[1] = {h->tau};
-        return apply_general(h, in, out, 1, Cm, Ck);
+        return apply_general<S>(h, in, out, 1, Cm, Ck);
       };
-      prec = [h, mg](const double* in, double* out) {
-        IRK_TRY(to_mg(h, mg, in, 1.0, nullptr, 0.0));
+      prec = [h, mg](const S* in, S* out) {
+        IRK_TRY(to_mg<S>(h, mg, in, 1.0, nullptr, 0.0));
         IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
-        return from_mg(h, mg, out, 1.0, nullptr, 0.0);
+        return from_mg<S>(h, mg, out, 1.0, nullptr, 0.0);
       };
     } else {
-      op = [h, al, be, tau](const double* in, double* out) {
+      op = [h, al, be, tau](const S* in, S* out) {
         const double Cm[4] = {al, -be, be, al}, Ck[4] = {tau, 0.0, 0.0, tau};
-        return apply_general(h, in, out, 2, Cm, Ck);
+        return apply_general<S>(h, in, out, 2, Cm, Ck);
       };
       // PRESB (Eq. presb:p): a = f + g; w1 = H^{-1} a; w2 = H^{-1}(g - beta M w1); out = (w1 - w2, w2)
-      prec = [h, mg, be](const double* in, double* out) {
+      prec = [h, mg, be](const S* in, S* out) {
         const LevelGeom& gg = h->fine;
-        const double* f = in;
-        const double* gv = in + gg.ld;
-        double* o1 = out;
-        double* o2 = out + gg.ld;
-        IRK_TRY(to_mg(h, mg, f, 1.0, gv, 1.0));
+        const S* f = in;
+        const S* gv = in + gg.ld;
+        S* o1 = out;
+        S* o2 = out + gg.ld;
+        IRK_TRY(to_mg<S>(h, mg, f, 1.0, gv, 1.0));
         IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
-        IRK_TRY(from_mg(h, mg, o1, 1.0, nullptr, 0.0));        // o1 = w1
-        // b2 = g - beta M w1: M w1 in FP64 through the fine operator (ns = 1)
+        IRK_TRY(from_mg<S>(h, mg, o1, 1.0, nullptr, 0.0));        // o1 = w1
+        // b2 = g - beta M w1: M w1 FP64-accurate through the fine operator (ns = 1)
         const double Cm[1] = {be}, Ck[1] = {0.0};
-        IRK_TRY(apply_general(h, o1, o2, 1, Cm, Ck));          // o2 = beta M w1
-        IRK_TRY(to_mg(h, mg, gv, 1.0, o2, -1.0));
+        IRK_TRY(apply_general<S>(h, o1, o2, 1, Cm, Ck));          // o2 = beta M w1
+        IRK_TRY(to_mg<S>(h, mg, gv, 1.0, o2, -1.0));
         IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
-        IRK_TRY(from_mg(h, mg, o2, 1.0, nullptr, 0.0));        // o2 = w2
-        return from_mg(h, mg, o1, -1.0, o1, 1.0);              // o1 = w1 - w2
+        IRK_TRY(from_mg<S>(h, mg, o2, 1.0, nullptr, 0.0));        // o2 = w2
+        return from_mg<S>(h, mg, o1, -1.0, o1, 1.0);              // o1 = w1 - w2
       };
     }
     FGMRESResult res;
-    IRK_TRY(fgmres_solve(w, op, prec, bvec, xvec, h->opt.rtol, h->opt.max_it, h->st, res));
+    IRK_TRY(fgmres_solve<S>(w, op, prec, bvec, xvec, h->opt.rtol, h->opt.max_it, h->st, res));
     iters += res.iterations;
     reo += res.reorth;
     vc += res.iterations * (blk.pair ? 2 : 1);
@@ -264,9 +287,27 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
   }
   // k = (T (x) I) x~
   CombineParams Cout = combine_params(Q, Q, h->tab.T.data());
-  IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(h->kst, nullptr, h->tq, g.n, g.ld, Cout, h->st));
+  IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, S>(kst, nullptr, tq, g.n, g.ld, Cout, h->st));
   if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; stats->reorth_passes = reo; }
-  IRK_LAUNCH(PROF_RHS, launch_update(g.grid(), Q, h->tq, h->tab.b.data(), h->tau, y, h->st));
+  IRK_LAUNCH(PROF_RHS, launch_update<S>(g.grid(), Q, tq, h->tab.b.data(), h->tau, y, h->st));
+  return Status::Ok();
+}
+
+Status step(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
+  const bool diag = (h->opt.variant == IRK_VARIANT_DIAG);
+  if (h->opt.op_ff) return diag ? step_diag<ff>(h, y, t_n, loads, stats) : step_lu<ff>(h, y, t_n, loads, stats);
+  return diag ? step_diag<double>(h, y, t_n, loads, stats) : step_lu<double>(h, y, t_n, loads, stats);
+}
+
+// The entry points below take FP64 vectors; with ff storage they go through the handle's
+// stage buffers tq (input) and kst (output), which irk_step uses only inside a step.
+template <typename F>
+Status with_ff_io(irk_problem* h, const double* in, long long nin, double* out, long long nout, F&& f) {
+  ff* a = as<ff>(h->tq);
+  ff* b = as<ff>(h->kst);
+  IRK_LAUNCH(PROF_COMBINE, launch_to_ff(in, a, nin, h->st));
+  IRK_TRY(f(a, b));
+  IRK_LAUNCH(PROF_COMBINE, launch_from_ff(b, out, nout, h->st));
   return Status::Ok();
 }
 
@@ -458,8 +499,7 @@ irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_loa
   return guarded(h, [&]() -> Status {
     if (!y) return Status::Err(IRK_EINVAL, "y is NULL");
     auto t0 = std::chrono::steady_clock::now();
-    Status s = (h->opt.variant == IRK_VARIANT_DIAG) ? step_diag(h, y, t_n, stage_load, stats)
-                                                     : step_lu(h, y, t_n, stage_load, stats);
+    Status s = step(h, y, t_n, stage_load, stats);
     IRK_CUDA(cudaStreamSynchronize(h->st));
     if (stats) stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return s;
@@ -596,28 +636,38 @@ irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out
 irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns, const double* Cm, const double* Ck) {
   return guarded(h, [&]() -> Status {
     if (!u || !v || !Cm || !Ck || ns < 1 || ns > kMaxQ) return Status::Err(IRK_EINVAL, "bad arguments");
-    return apply_general(h, u, v, ns, Cm, Ck);
+    if (ns > h->nslots) return Status::Err(IRK_EINVAL, "too many stage vectors for this handle");
+    if (!h->opt.op_ff) return apply_general<double>(h, u, v, ns, Cm, Ck);
+    const long long len = (long long)ns * h->fine.ld;
+    return with_ff_io(h, u, len, v, len, [&](const ff* a, ff* b) { return apply_general<ff>(h, a, b, ns, Cm, Ck); });
   });
 }
 
 irk_status irk_apply(irk_handle h, const double* u, double* v) {
   return guarded(h, [&]() -> Status {
     if (!u || !v) return Status::Err(IRK_EINVAL, "bad arguments");
-    return apply_calA(h, u, v);
+    if (!h->opt.op_ff) return apply_calA<double>(h, u, v);
+    const long long len = (long long)h->Q * h->fine.ld;
+    return with_ff_io(h, u, len, v, len, [&](const ff* a, ff* b) { return apply_calA<ff>(h, a, b); });
   });
 }
 
 irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs) {
   return guarded(h, [&]() -> Status {
     if (!y || !rhs) return Status::Err(IRK_EINVAL, "bad arguments");
-    return stage_rhs(h, y, t_n, nullptr, rhs);
+    if (!h->opt.op_ff) return stage_rhs<double>(h, y, t_n, nullptr, rhs);
+    IRK_TRY(stage_rhs<ff>(h, y, t_n, nullptr, as<ff>(h->kst)));
+    IRK_LAUNCH(PROF_RHS, launch_from_ff(as<ff>(h->kst), rhs, (long long)h->Q * h->fine.ld, h->st));
+    return Status::Ok();
   });
 }
 
 irk_status irk_precondition(irk_handle h, const double* r, double* z) {
   return guarded(h, [&]() -> Status {
     if (!r || !z) return Status::Err(IRK_EINVAL, "bad arguments");
-    return precondition_lu(h, r, z);
+    if (!h->opt.op_ff) return precondition_lu<double>(h, r, z);
+    const long long len = (long long)h->Q * h->fine.ld;
+    return with_ff_io(h, r, len, z, len, [&](const ff* a, ff* b) { return precondition_lu<ff>(h, a, b); });
   });
 }
 
@@ -672,7 +722,8 @@ irk_status irk_stage_combine(irk_handle h, const double* u, int nin, double* v, 
     if (!u || !v || !D || nin < 1 || nin > kMaxQ || nout < 1 || nout > kMaxQ)
       return Status::Err(IRK_EINVAL, "bad arguments");
     CombineParams C = combine_params(nout, nin, D);
-    IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double>(u, nullptr, v, h->fine.n, h->fine.ld, C, h->st));
+    IRK_LAUNCH(PROF_COMBINE,
+               launch_combine<double, double, double>(u, nullptr, v, h->fine.n, h->fine.ld, C, h->st));
     return Status::Ok();
   });
 }

@@ -4,10 +4,12 @@
 // preconditioned vectors Z because the preconditioner (one mixed-precision
 // V-cycle per block) is not a fixed linear map in floating point.
 // Classical Gram-Schmidt with a conditional second pass (Kahan-Parlett "twice
-// is enough", decided on the device); the dot products are deterministic
-// device reductions and the Hessenberg/Givens update runs on the host with
-// one device->host transfer per iteration.
+// is enough", decided on the device by the reduction that finishes |w'|^2);
+// the dot products are deterministic device reductions and the
+// Hessenberg/Givens update runs on the host with one device->host transfer per
+// iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -44,6 +46,7 @@ void pinned_block_release(double* p) {
 
 Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena, cudaStream_t stream) {
   if (m < 1 || m > 60) return Status::Err(IRK_EINVAL, "restart must be in 1..60");
+  static_assert(sizeof(ff) == sizeof(double), "ff vectors share the FP64 layout");
   w.ns = ns;
   w.m = m;
   w.ld = ld;
@@ -54,23 +57,51 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
   IRK_TRY(arena.alloc((void**)&w.tmp, (size_t)w.len * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.partial, (size_t)66 * w.nb * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.dvals, 256 * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&w.fvals, 256 * sizeof(ff)));
   if (!w.hvals) {
     w.hvals = pinned_block_acquire();
     if (!w.hvals) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
   }
+  // the constant 1 (restart residual b - A x) in both forms
+  const ff one{1.0f, 0.0f};
   w.hvals[255] = 1.0;
+  std::memcpy(&w.hvals[254], &one, sizeof(ff));
   IRK_CUDA(cudaMemcpyAsync(w.dvals + 255, w.hvals + 255, sizeof(double), cudaMemcpyHostToDevice, stream));
+  IRK_CUDA(cudaMemcpyAsync(w.fvals + 255, w.hvals + 254, sizeof(ff), cudaMemcpyHostToDevice, stream));
+  IRK_CUDA(cudaStreamSynchronize(stream));
   return Status::Ok();
 }
 
 namespace {
 
-// layout of dvals / hvals
-constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kN0 = 131, kY = 160, kOne = 255;
+// layout of dvals / fvals / hvals
+constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kN0 = 131, kRedo = 132, kInv = 133, kY = 160, kOne = 255;
 constexpr double kEta = 0.7;  // Kahan-Parlett threshold of the conditional second pass
 
-Status norm(FGMRESWork& w, const double* v, cudaStream_t st, double& out) {
-  IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial(v, w.len, w.partial, w.nb, st));
+template <typename S> typename Coef<S>::type* coefs(FGMRESWork& w);
+template <> double* coefs<double>(FGMRESWork& w) { return w.dvals; }
+template <> ff* coefs<ff>(FGMRESWork& w) { return w.fvals; }
+
+// y (host, FP64) -> device coefficients of the vector type, through the pinned block
+template <typename S> Status upload_y(FGMRESWork& w, const std::vector<double>& y, int kk, cudaStream_t st);
+template <> Status upload_y<double>(FGMRESWork& w, const std::vector<double>& y, int kk, cudaStream_t st) {
+  for (int i = 0; i < kk; ++i) w.hvals[kY + i] = y[i];
+  IRK_CUDA(cudaMemcpyAsync(w.dvals + kY, w.hvals + kY, kk * sizeof(double), cudaMemcpyHostToDevice, st));
+  return Status::Ok();
+}
+template <> Status upload_y<ff>(FGMRESWork& w, const std::vector<double>& y, int kk, cudaStream_t st) {
+  for (int i = 0; i < kk; ++i) {
+    ff v;
+    split_double(y[i], &v.hi, &v.lo);
+    std::memcpy(&w.hvals[kY + i], &v, sizeof(ff));
+  }
+  IRK_CUDA(cudaMemcpyAsync(w.fvals + kY, w.hvals + kY, kk * sizeof(ff), cudaMemcpyHostToDevice, st));
+  return Status::Ok();
+}
+
+template <typename S>
+Status norm(FGMRESWork& w, const S* v, cudaStream_t st, double& out) {
+  IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial<S>(v, w.len, w.partial, w.nb, st));
   IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
   IRK_CUDA(cudaMemcpyAsync(w.hvals + kNrm, w.dvals + kNrm, sizeof(double), cudaMemcpyDeviceToHost, st));
   IRK_CUDA(cudaStreamSynchronize(st));
@@ -80,20 +111,25 @@ Status norm(FGMRESWork& w, const double* v, cudaStream_t st, double& out) {
 
 }  // namespace
 
-Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const double* b, double* x,
-                    double rtol, int max_it, cudaStream_t st, FGMRESResult& res) {
+template <typename S>
+Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec, const S* b, S* x, double rtol,
+                    int max_it, cudaStream_t st, FGMRESResult& res) {
   res = FGMRESResult();
   const long long len = w.len;
   const int m = w.m;
-  IRK_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(double), st));
+  S* V = reinterpret_cast<S*>(w.V);
+  S* Z = reinterpret_cast<S*>(w.Z);
+  S* tmp = reinterpret_cast<S*>(w.tmp);
+  typename Coef<S>::type* cf = coefs<S>(w);
+  IRK_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(S), st));
   double bnorm;
-  IRK_TRY(norm(w, b, st, bnorm));
+  IRK_TRY(norm<S>(w, b, st, bnorm));
   if (!std::isfinite(bnorm)) return Status::Err(IRK_ENUMERIC, "non-finite right-hand side");
   if (bnorm == 0.0) { res.converged = true; return Status::Ok(); }
   const double target = rtol * bnorm;
   // first cycle: r = b (x0 = 0)
   double beta = bnorm;
-  IRK_LAUNCH(PROF_KRYLOV, launch_scale(b, 1.0 / beta, w.V, len, st));
+  IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(b, 1.0 / beta, V, len, st));
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   int total = 0;
   while (true) {
@@ -102,31 +138,42 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const
     int jlast = -1;
     bool stop = false;
     for (int j = 0; j < m; ++j) {
-      double* Vj = w.V + (size_t)j * len;
-      double* Zj = w.Z + (size_t)j * len;
-      double* wv = w.V + (size_t)(j + 1) * len;
+      S* Vj = V + (size_t)j * len;
+      S* Zj = Z + (size_t)j * len;
+      S* wv = V + (size_t)(j + 1) * len;
       IRK_TRY(prec(Vj, Zj));
       IRK_TRY(op(Zj, wv));
       // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
       const int nv = j + 1;
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot(w.V, len, nv, wv, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH1, st));
+      ReduceExtra x1;
+      x1.out_ff = w.fvals + kH1;
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH1, st, 0, &x1));
       // dvals[kH1 + nv] = |w|^2, copied aside before pass 2 overwrites row nv
       IRK_CUDA(cudaMemcpyAsync(w.dvals + kN0, w.dvals + kH1 + nv, sizeof(double), cudaMemcpyDeviceToDevice, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot(w.V, len, nv, w.dvals + kH1, wv, w.tmp, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH2, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth(w.V, len, nv, w.dvals + kH2, w.tmp, wv, len, w.dvals + kN0,
-                                               w.dvals + kH2 + nv, kEta, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
-      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kN0 + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      ReduceExtra x2;
+      x2.out_ff = w.fvals + kH2;
+      x2.decide_flag = w.dvals + kRedo;  // second pass when |w'|^2 < eta^2 |w|^2
+      x2.decide_ref = w.dvals + kN0;
+      x2.decide_row = nv;
+      x2.eta2 = kEta * kEta;
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, w.nb, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH2, st, 0, &x2));
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, tmp, wv, len, w.partial,
+                                                  w.nb, st));
+      ReduceExtra x3;
+      x3.inv = w.dvals + kInv;
+      x3.inv_ff = w.fvals + kInv;
+      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1, &x3));
+      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       IRK_CUDA(cudaStreamSynchronize(st));
       const double hn = w.hvals[kNrm];
       if (!std::isfinite(hn)) return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
-      const bool redo = w.hvals[kH2 + nv] < kEta * kEta * w.hvals[kN0];
+      const bool redo = w.hvals[kRedo] != 0.0;
       res.reorth += redo ? 1 : 0;
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + (redo ? w.hvals[kH2 + i] : 0.0);
       H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_inv(wv, w.dvals + kNrm, wv, len, st));
+      if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_dev<S>(wv, cf + kInv, wv, len, st));
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -155,23 +202,27 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const
       for (int c = i + 1; c < kk; ++c) s -= H[(size_t)i * m + c] * y[c];
       y[i] = s / H[(size_t)i * m + i];
     }
-    for (int i = 0; i < kk; ++i) w.hvals[kY + i] = y[i];
-    IRK_CUDA(cudaMemcpyAsync(w.dvals + kY, w.hvals + kY, kk * sizeof(double), cudaMemcpyHostToDevice, st));
-    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(w.Z, len, kk, w.dvals + kY, 1.0, x, len, st));
+    IRK_TRY(upload_y<S>(w, y, kk, st));
+    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy<S>(Z, len, kk, cf + kY, 1.0, x, len, st));
     if (stop) break;
     // restart with the explicit residual
-    IRK_TRY(op(x, w.tmp));
-    IRK_LAUNCH(PROF_KRYLOV, launch_scale(w.tmp, -1.0, w.tmp, len, st));
-    // tmp = b - A x  (dvals[kOne] holds the constant 1)
-    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy(b, 0, 1, w.dvals + kOne, 1.0, w.tmp, len, st));
-    IRK_TRY(norm(w, w.tmp, st, beta));
+    IRK_TRY(op(x, tmp));
+    IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(tmp, -1.0, tmp, len, st));
+    // tmp = b - A x  (coefficient slot kOne holds the constant 1)
+    IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy<S>(b, 0, 1, cf + kOne, 1.0, tmp, len, st));
+    IRK_TRY(norm<S>(w, tmp, st, beta));
     if (!std::isfinite(beta)) return Status::Err(IRK_ENUMERIC, "non-finite restart residual");
     if (beta <= target) { res.converged = true; res.rel_residual = beta / bnorm; break; }
-    IRK_LAUNCH(PROF_KRYLOV, launch_scale(w.tmp, 1.0 / beta, w.V, len, st));
+    IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(tmp, 1.0 / beta, V, len, st));
   }
   IRK_CUDA(cudaStreamSynchronize(st));
   res.iterations = total;
   return Status::Ok();
 }
+
+template Status fgmres_solve<double>(FGMRESWork&, const ApplyFn<double>&, const ApplyFn<double>&, const double*,
+                                     double*, double, int, cudaStream_t, FGMRESResult&);
+template Status fgmres_solve<ff>(FGMRESWork&, const ApplyFn<ff>&, const ApplyFn<ff>&, const ff*, ff*, double, int,
+                                 cudaStream_t, FGMRESResult&);
 
 }  // namespace irk

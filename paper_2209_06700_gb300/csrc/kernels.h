@@ -11,12 +11,12 @@ constexpr int kMaxStages = 16;   // per-launch stage slots (Q <= 9, 2x2 DIAG blo
 constexpr int kMaxDeg = 4;       // Q_k degree k <= 4
 
 // Float-float value hi + lo (|lo| <= ulp(hi) / 2): about 48 significant bits computed on the
-// FP32 pipe.  Used for the FP64-accurate operator apply; stored in memory as FP64.
-struct ff {
+// FP32 pipe.  The FP64-accurate stage operator and the Krylov vectors use it; a vector of ff is
+// stored as pairs (8 bytes per value, 8-byte aligned, the size of FP64).
+struct alignas(8) ff {
   float hi, lo;
 };
 template <typename T> struct Storage { using type = T; };
-template <> struct Storage<ff> { using type = double; };
 
 // Geometry and coefficients of one tensor-product operator launch
 //   v_s = cm[s] M u_s + ck[s] K u_s          (s = blockIdx.z, one stage per CTA)
@@ -70,11 +70,21 @@ struct CombineParams {  // out_i = sum_j Da[i][j] a_j (+ sum_j Db[i][j] b_j)
   double Da[kMaxQ * kMaxQ];
   double Db[kMaxQ * kMaxQ];
   unsigned nza[kMaxQ], nzb[kMaxQ];  // bit j of row i: coefficient (i, j) is nonzero (set by the launcher)
+  float Dah[kMaxQ * kMaxQ], Dal[kMaxQ * kMaxQ], Dbh[kMaxQ * kMaxQ], Dbl[kMaxQ * kMaxQ];  // ff split (launcher)
 };
-// Tin/Tout in {float,double}; a [nina][ld], b [ninb][ld] (may be null), out [nout][ld];
-// n elements per vector are processed.
-template <typename Tin, typename Tout>
-cudaError_t launch_combine(const Tin* a, const double* b, Tout* out, long long n, long long ld,
+
+// Storage types of the outer solver's stage vectors: double (plain FP64 path) or ff.  Coef<S> is
+// the type of the device-side coefficients those kernels read (h of Gram-Schmidt, 1/norm, y).
+template <typename S> struct Coef { using type = double; };
+template <> struct Coef<ff> { using type = ff; };
+
+// hi + lo split of an FP64 coefficient on the host
+void split_double(double d, float* hi, float* lo);
+
+// a [nina][ld] of Ta, b [ninb][ld] of Tb (may be null), out [nout][ld] of Tout; n elements per vector.
+// Arithmetic in ff when any of the three is ff, else FP64.
+template <typename Ta, typename Tb, typename Tout>
+cudaError_t launch_combine(const Ta* a, const Tb* b, Tout* out, long long n, long long ld,
                            const CombineParams& C, cudaStream_t st);
 
 struct GridInfo {      // node grid of one level
@@ -96,57 +106,82 @@ cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, c
 // Deterministic start vector of the Lanczos estimate: 0.5 + hash(node) / 2^53 on interior nodes, zero
 // elsewhere, identical for every block.
 cudaError_t launch_hash_fill(const GridInfo& g, int nstage, double* x, cudaStream_t st);
-// out = x * D^{-1/2} (inv_sqrt = 1) or out = x * D (inv_sqrt = 0), interior nodes.
-template <typename T>
-cudaError_t launch_diag_scale(const GridInfo& g, int nstage, const T* x, T* out, const DiagParams<T>& D,
+// out = x * D^{-1/2} (inv_sqrt = 1) or out = x * D (inv_sqrt = 0), interior nodes; the factor in
+// FP32, the product in FP64 (Tin, Tout in {float, double, ff}: float with float only).
+template <typename Tin, typename Tout>
+cudaError_t launch_diag_scale(const GridInfo& g, int nstage, const Tin* x, Tout* out, const DiagParams<double>& D,
                               int inv_sqrt, cudaStream_t st);
 
 struct RhsParams {
   int Q;
   double Ainv[kMaxQ * kMaxQ];
   double phi[kMaxQ];
+  float Ainvh[kMaxQ * kMaxQ], Ainvl[kMaxQ * kMaxQ], phih[kMaxQ], phil[kMaxQ];  // ff split (launcher)
 };
 // rhs_i = sum_j Ainv[i][j] (load_j - Ky); load_j = phi_j (G1 (x) G1 (x) G1) (built-in source)
-// or the user stage loads (device [Q][ld]) when loads != nullptr.
-cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const double* Ky, const double* G1,
-                             const double* loads, double* rhs, cudaStream_t st);
-// y += tau sum_i b_i k_i
-cudaError_t launch_update(const GridInfo& g, int Q, const double* kst, const double* bw, double tau,
+// or the user stage loads (device [Q][ld], FP64) when loads != nullptr.  Ky, rhs of type S.
+template <typename S>
+cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky, const double* G1,
+                             const double* loads, S* rhs, cudaStream_t st);
+// y += tau sum_i b_i k_i  (k of type S, y FP64)
+template <typename S>
+cudaError_t launch_update(const GridInfo& g, int Q, const S* kst, const double* bw, double tau,
                           double* y, cudaStream_t st);
+// FP64 <-> ff copies of n values
+cudaError_t launch_to_ff(const double* in, ff* out, long long n, cudaStream_t st);
+cudaError_t launch_from_ff(const ff* in, double* out, long long n, cudaStream_t st);
 // y = prod sin(pi x_a) * ct at nodes (x1d: node coordinates of one grid line, device)
 cudaError_t launch_interpolate(const GridInfo& g, const double* x1d, double ct, double* y,
                                cudaStream_t st);
 
 // Deterministic reductions over long vectors of length n (fixed block count from n).
 int reduction_blocks(long long n);
-// partial[i][nb] = partial dot(V_i, w), V_i = V + i * vstride, i < nv
+// partial[i][nb] = partial dot(V_i, w), V_i = V + i * vstride, i < nv (FP64 vectors)
 cudaError_t launch_multidot(const double* V, long long vstride, int nv, const double* w, long long n,
                             double* partial, int nb, cudaStream_t st);
+// Optional outputs of a reduction, written by the block that finishes the row.
+struct ReduceExtra {
+  ff* out_ff = nullptr;               // ff copy of each row result
+  double* inv = nullptr;              // 1 / (row 0 result), 0 when the result is 0
+  ff* inv_ff = nullptr;               // the same in ff
+  double* decide_flag = nullptr;      // 1.0 when (row decide_row) < eta2 * decide_ref[0], else 0.0
+  const double* decide_ref = nullptr;
+  int decide_row = -1;
+  double eta2 = 0.0;
+};
 // out[i] = sum_b partial[i][b] (fixed order); with take_sqrt, out[i] = sqrt(sum)
 cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double* out, cudaStream_t st,
-                                   int take_sqrt = 0);
-// partial[0][nb] = partial sum of w^2
-cudaError_t launch_norm2_partial(const double* w, long long n, double* partial, int nb, cudaStream_t st);
-// w -= sum_i h[i] V_i   (h on the device)
-cudaError_t launch_multi_axpy(const double* V, long long vstride, int nv, const double* h, double sign,
-                              double* w, long long n, cudaStream_t st);
-// out = w * (1 / nrm[0])
-cudaError_t launch_scale_inv(const double* w, const double* nrm, double* out, long long n, cudaStream_t st);
-// out = a * x
-cudaError_t launch_scale(const double* x, double a, double* out, long long n, cudaStream_t st);
-// Fused Gram-Schmidt passes (classical Gram-Schmidt with the "twice is enough" test of Kahan
-// and Parlett); partial has rows [0, nv] x nb:
-//  gs_dot      : partial[i] = dot(V_i, w) (i < nv), partial[nv] = |w|^2
-//  gs_axpy_dot : w_out = w_in - sum_i h[i] V_i; partial[i] = dot(V_i, w_out), partial[nv] = |w_out|^2
-//  gs_reorth   : if |w_mid|^2 < eta^2 |w|^2 (device scalars norm2_mid, norm2_in): w_out = w_in - sum h[i] V_i,
-//                else w_out = w_in; partial[0] = |w_out|^2
-cudaError_t launch_gs_dot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
-                          int nb, cudaStream_t st);
-cudaError_t launch_gs_axpy_dot(const double* V, long long vstride, int nv, const double* h, const double* w_in,
-                               double* w_out, long long n, double* partial, int nb, cudaStream_t st);
-cudaError_t launch_gs_reorth(const double* V, long long vstride, int nv, const double* h, const double* w_in,
-                             double* w_out, long long n, const double* norm2_in, const double* norm2_mid, double eta,
-                             double* partial, int nb, cudaStream_t st);
+                                   int take_sqrt = 0, const ReduceExtra* extra = nullptr);
+// Vector work of FGMRES on stage vectors of type S (double or ff); reductions produce FP64
+// partial sums per block (rows of nb).
+//  norm2_partial: partial[0] = |w|^2
+//  multi_axpy   : w += sign sum_i h[i] V_i          (h on the device, Coef<S>)
+//  scale_dev    : out = inv[0] w                    (inv on the device, Coef<S>; out may alias w)
+//  scale        : out = a x                         (a from the host)
+//  gs_dot       : partial[i] = dot(V_i, w) (i < nv), partial[nv] = |w|^2
+//  gs_axpy_dot  : w_out = w_in - sum_i h[i] V_i; partial[i] = dot(V_i, w_out), partial[nv] = |w_out|^2
+//  gs_reorth    : w_out = w_in - sum_i h[i] V_i if *redo_flag != 0 (second pass of classical
+//                 Gram-Schmidt, "twice is enough" of Kahan and Parlett), else w_out = w_in;
+//                 partial[0] = |w_out|^2
+template <typename S>
+cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int nb, cudaStream_t st);
+template <typename S>
+cudaError_t launch_multi_axpy(const S* V, long long vstride, int nv, const typename Coef<S>::type* h, double sign,
+                              S* w, long long n, cudaStream_t st);
+template <typename S>
+cudaError_t launch_scale_dev(const S* w, const typename Coef<S>::type* inv, S* out, long long n, cudaStream_t st);
+template <typename S>
+cudaError_t launch_scale(const S* x, double a, S* out, long long n, cudaStream_t st);
+template <typename S>
+cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, long long n, double* partial, int nb,
+                          cudaStream_t st);
+template <typename S>
+cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
+                               const S* w_in, S* w_out, long long n, double* partial, int nb, cudaStream_t st);
+template <typename S>
+cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
+                             const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int nb,
+                             cudaStream_t st);
 
 // Block-wise helpers (ns vectors of n elements at stride ld), coefficients on the device:
 //  block_dot:   partial[s][nb] = partial sums of a_s . b_s

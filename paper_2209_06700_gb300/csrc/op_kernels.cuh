@@ -27,75 +27,19 @@
 //
 // Arithmetic goes through dev::mad / mul / add so that one body serves FP32
 // (multigrid), FP64 and float-float (T = ff: FP64-accurate apply on the FP32
-// pipe, inputs split hi/lo on load, outputs merged to FP64 on store).
+// pipe, vectors stored as ff pairs).
 #pragma once
+#include "ffmath.cuh"
 #include "kernels.h"
 
 namespace irk {
 namespace dev {
 
-// ---------------------------------------------------------------- arithmetic helpers
-template <typename T> __device__ __forceinline__ T zero() { return T(0); }
-template <> __device__ __forceinline__ ff zero<ff>() { return ff{0.f, 0.f}; }
-
-// float-float: error-free sums with the round-to-nearest intrinsics (never contracted into FMA)
-__device__ __forceinline__ ff ff_renorm(float s, float e) {
-  const float hi = __fadd_rn(s, e);
-  return ff{hi, __fsub_rn(e, __fsub_rn(hi, s))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bb = __fsub_rn(s, a.hi);
-  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  return ff_renorm(s, e);
-}
-// a + c v: the product c.hi v.hi is split exactly by an FMA, the cross terms are plain FP32
-__device__ __forceinline__ ff ff_mad(ff a, ff c, ff v) {
-  const float p = __fmul_rn(c.hi, v.hi);
-  float pe = __fmaf_rn(c.hi, v.hi, -p);
-  pe = __fmaf_rn(c.hi, v.lo, pe);
-  pe = __fmaf_rn(c.lo, v.hi, pe);
-  const float s = __fadd_rn(a.hi, p);
-  const float bb = __fsub_rn(s, a.hi);
-  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  e = __fadd_rn(e, __fadd_rn(a.lo, pe));
-  return ff_renorm(s, e);
-}
-__device__ __forceinline__ ff ff_mul(ff c, ff v) {
-  const float p = __fmul_rn(c.hi, v.hi);
-  float pe = __fmaf_rn(c.hi, v.hi, -p);
-  pe = __fmaf_rn(c.hi, v.lo, pe);
-  pe = __fmaf_rn(c.lo, v.hi, pe);
-  return ff_renorm(p, pe);
-}
-
-__device__ __forceinline__ float mad(float a, float c, float v) { return fmaf(c, v, a); }
-__device__ __forceinline__ double mad(double a, double c, double v) { return fma(c, v, a); }
-__device__ __forceinline__ ff mad(ff a, ff c, ff v) { return ff_mad(a, c, v); }
-__device__ __forceinline__ float mul(float c, float v) { return c * v; }
-__device__ __forceinline__ double mul(double c, double v) { return c * v; }
-__device__ __forceinline__ ff mul(ff c, ff v) { return ff_mul(c, v); }
-__device__ __forceinline__ float add(float a, float b) { return a + b; }
-__device__ __forceinline__ double add(double a, double b) { return a + b; }
-__device__ __forceinline__ ff add(ff a, ff b) { return ff_add(a, b); }
-
-__device__ __forceinline__ float shfl_up(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ double shfl_up(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ ff shfl_up(ff v) {
-  return ff{__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1)};
-}
-
-// load from storage (FP64 values are split into hi + lo for ff) and store back
-template <typename T> __device__ __forceinline__ T load(const typename Storage<T>::type* p) { return __ldg(p); }
-template <> __device__ __forceinline__ ff load<ff>(const double* p) {
-  const double d = __ldg(p);
-  const float hi = __double2float_rn(d);
-  return ff{hi, __double2float_rn(d - (double)hi)};
-}
+// load from storage and store back (ff vectors are stored as ff pairs, 8 bytes per value)
+template <typename T> __device__ __forceinline__ T load(const typename Storage<T>::type* p) { return ldg<T>(p); }
 __device__ __forceinline__ float to_storage(float v) { return v; }
 __device__ __forceinline__ double to_storage(double v) { return v; }
-__device__ __forceinline__ double to_storage(ff v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ ff to_storage(ff v) { return v; }
 
 // ---------------------------------------------------------------- epilogues
 // One interior output node (stage s, flat offset o).  CHEB needs invD = 1/diag(cm M + ck K).
@@ -378,7 +322,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
         const int x = K * cell + m;
         if (x < 1) continue;
         const long long idx = ((long long)z * n1 + yrow) * n1 + x;
-        S invD = S(0);
+        S invD{};
         if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
         dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, accA[m][mo], accB[m][mo], invD);
       }
@@ -494,7 +438,7 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
         const int x = K * cell + m;
         if (x < 1) continue;
         const long long idx = (long long)y * n1 + x;
-        S invD = S(0);
+        S invD{};
         if constexpr (EPI == EPI_CHEB) invD = dev::inv_diag<S, 2>(E, (S)P.cm[s], (S)P.ck[s], m, mo, 0);
         dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, accA[m][mo], accB[m][mo], invD);
       }

@@ -112,15 +112,18 @@ struct MGConfig {
 Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,
                std::unique_ptr<MGBase>& out);
 
-// Right-preconditioned flexible GMRES (FP64) on ns stage vectors of stride ld.
+// Right-preconditioned flexible GMRES on ns stage vectors of stride ld.  The vectors are stored
+// as 8-byte elements of type S: double (plain FP64 path) or ff (float-float, FP32 pipe); the
+// Hessenberg matrix, Givens rotations and small solves run on the host in FP64.
 struct FGMRESWork {
   int ns = 0, m = 0;
   long long ld = 0, len = 0;  // len = ns * ld
-  double* V = nullptr;        // (m+1) x len
+  double* V = nullptr;        // (m+1) x len elements of S
   double* Z = nullptr;        // m x len
-  double* tmp = nullptr;      // len (restart residual)
-  double* partial = nullptr;  // 64 x nb
-  double* dvals = nullptr;    // device scalars: h1[64], h2[64], nrm, y[64]
+  double* tmp = nullptr;      // len (restart residual, second Gram-Schmidt pass)
+  double* partial = nullptr;  // 66 x nb
+  double* dvals = nullptr;    // device scalars: h1[65], h2[65], norms, decision, y[64], 1
+  ff* fvals = nullptr;        // the same scalars split into ff (the ff kernels' coefficients)
   double* hvals = nullptr;    // pinned host mirror
   int nb = 0;
 };
@@ -131,9 +134,11 @@ void pinned_block_release(double* p);
 
 struct FGMRESResult { int iterations = 0; int reorth = 0; double rel_residual = 0; bool converged = false; };
 
-using ApplyFn = std::function<Status(const double* in, double* out)>;
+template <typename S>
+using ApplyFn = std::function<Status(const S* in, S* out)>;
 
-Status fgmres_solve(FGMRESWork& w, const ApplyFn& op, const ApplyFn& prec, const double* b, double* x,
-                    double rtol, int max_it, cudaStream_t st, FGMRESResult& res);
+template <typename S>
+Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec, const S* b, S* x, double rtol,
+                    int max_it, cudaStream_t st, FGMRESResult& res);
 
 }  // namespace irk

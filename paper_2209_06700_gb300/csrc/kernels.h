@@ -27,7 +27,9 @@ struct OpParams {
   int N, n1;           // cells per axis, nodes per axis (k N + 1)
   long long ld;        // elements between stage vectors
   int zc;              // streaming chunk, in cells (0: chosen by the launcher)
-  int ntile_y;         // 3D: number of y tiles (grid.y = ntile_y * chunks)
+  int ntile_y;         // 3D: number of y tiles (grid.y = ntile_y * nch, chunk index fastest)
+  int nch;             // 3D: number of z chunks (set by the launcher)
+  int cluster;         // 3D: 1 = the nch chunks of a tile form a thread-block cluster (set by the launcher)
   T me[kMaxDeg + 1][kMaxDeg + 1];
   T ke[kMaxDeg + 1][kMaxDeg + 1];
   T yvm[2 * kMaxDeg + 1], yvk[2 * kMaxDeg + 1];  // banded taps of a vertex row, offsets -k..k

@@ -22,13 +22,21 @@
 //    vertex node merged with the left neighbour by a warp shuffle;
 //  * z contraction: cell-wise "push" into k+1 register accumulators per
 //    owned node; a z-cell's k planes are complete, and emitted through the
-//    fused epilogue, once its upper vertex plane has been pushed.
+//    fused epilogue, once its upper vertex plane has been pushed;
+//  * z chunks: the vertex plane between two chunks takes contributions from
+//    the cells on both sides.  When the chunks of a tile run as one thread-
+//    block cluster, each CTA streams only its own cells, keeps its bottom
+//    vertex plane back, and adds the lower chunk's top contributions read from
+//    that CTA's shared memory (distributed shared memory) after a cluster
+//    barrier; otherwise a chunk re-streams the cell below it.
 // Boundary nodes (homogeneous Dirichlet) are read as zero and never written.
 //
 // Arithmetic goes through dev::mad / mul / add so that one body serves FP32
 // (multigrid), FP64 and float-float (T = ff: FP64-accurate apply on the FP32
 // pipe, vectors stored as ff pairs).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "ffmath.cuh"
 #include "kernels.h"
 
@@ -209,18 +217,23 @@ __device__ __forceinline__ void zstep(int r, int c, int cstart, int c0, const Op
 
 }  // namespace dev
 
-template <int K> struct Tile3D { static constexpr int CY = (K == 1) ? 8 : (K == 2) ? 4 : 2; };
+// Tile of a 3D CTA: CXS cells in x per warp segment (32, or 16 / 8 on meshes with fewer cells, so
+// that no lane idles), 32 / CXS node rows per warp, K * CY node rows in y; the thread count is the
+// same for every CXS.
+template <int K> struct Warps3D { static constexpr int value = K * ((K == 1) ? 8 : (K == 2) ? 4 : 2); };
+template <int K, int CXS> struct Tile3D { static constexpr int CY = Warps3D<K>::value * (32 / CXS) / K; };
 // resident CTAs per SM requested from the register allocator (FP32: 3 -> 24 warps per SM)
 template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 1; };
 
 // ---------------------------------------------------------------- 3D kernel
-template <typename T, int K, int EPI>
-__global__ void __launch_bounds__(32 * K * Tile3D<K>::CY, MinBlocks<T>::value)
+template <typename T, int K, int EPI, int CXS>
+__global__ void __launch_bounds__(32 * Warps3D<K>::value, MinBlocks<T>::value)
 op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
             const EpiParams<typename Storage<T>::type> E) {
   using S = typename Storage<T>::type;
-  constexpr int CY = Tile3D<K>::CY;
-  constexpr int CX = 32, TY = K * CY, NT = 32 * TY;
+  constexpr int RPW = 32 / CXS;  // node rows per warp
+  constexpr int CY = Tile3D<K, CXS>::CY;
+  constexpr int CX = CXS, TY = K * CY, NT = 32 * Warps3D<K>::value;
   constexpr int CW = CX + 2, SL = K * CW;
   constexpr int HY = TY + K + 1, HX = K * CX + K + 1;
   constexpr int NLD = HY * HX;
@@ -234,15 +247,18 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = P.N, n1 = P.n1;
   const int cx0 = blockIdx.x * CX;
-  const int ty = blockIdx.y % P.ntile_y, zchunk = blockIdx.y / P.ntile_y;
+  const int zchunk = blockIdx.y % P.nch, ty = blockIdx.y / P.nch;
   const int y0 = K * CY * ty, x0 = K * cx0;
   const int s = blockIdx.z;
   const S* __restrict__ us = u + (long long)s * P.ld;
   const T cm = P.cm[s], ck = P.ck[s];
+  const bool clustered = P.cluster != 0;
   const int c0 = zchunk * P.zc;
-  if (c0 >= N) return;
+  if (!clustered && c0 >= N) return;  // a cluster's chunks are all non-empty (launcher)
   const int c1 = min(N, c0 + P.zc);
-  const int cstart = max(c0 - 1, 0);
+  const int cstart = clustered ? c0 : max(c0 - 1, 0);
+  const bool hold_bottom = clustered && c0 > 0;  // bottom vertex plane waits for the lower chunk
+  __shared__ T shold[(EPI == EPI_DUAL ? 2 : 1) * K * NT];
   const long long plane = (long long)n1 * n1;
 
   for (int i = tid; i < HY * SL; i += NT) su[i] = dev::zero<T>();  // padding slots stay zero
@@ -280,30 +296,43 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       if (soff[q] >= 0) su[soff[q]] = pf[q];
   };
   auto ypass = [&]() {
-    const int ro = w % K;
-    const T* colbase = su + (w + K) * SL;
-    for (int sl = lane; sl < SL; sl += 32) {
-      T g = dev::zero<T>(), h = dev::zero<T>();
-      dev::ytaps_dispatch<T, K>(ro, colbase + sl, SL, P, g, h);
-      sg[w * SL + sl] = g;
-      sh[w * SL + sl] = h;
+#pragma unroll 1
+    for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows, one at a time (warp-uniform tap row)
+      const int yr = w * RPW + rr;
+      const int ro = yr % K;
+      const T* colbase = su + (yr + K) * SL;
+      for (int sl = lane; sl < SL; sl += 32) {
+        T g = dev::zero<T>(), h = dev::zero<T>();
+        dev::ytaps_dispatch<T, K>(ro, colbase + sl, SL, P, g, h);
+        sg[yr * SL + sl] = g;
+        sh[yr * SL + sl] = h;
+      }
     }
   };
+  const int seg = lane / CXS, lx = lane - seg * CXS;
+  const int trow = w * RPW + seg;  // this thread's node row in the tile
   auto xpass = [&](T (&R)[K], T (&Pp)[K]) {
-    const T* g = sg + w * SL;
-    const T* h = sh + w * SL;
+    const T* g = sg + trow * SL;
+    const T* h = sh + trow * SL;
     T r[K + 1], p[K + 1];
-    dev::xcell<T, K, true, CW>(g, h, lane + 1, P, r, p);
+    dev::xcell<T, K, true, CW>(g, h, lx + 1, P, r, p);
     T rl = dev::shfl_up(r[K]);
     T pl = dev::shfl_up(p[K]);
-    if (lane == 0) dev::xcell_top<T, K, true, CW>(g, h, 0, P, rl, pl);
+    if (lx == 0) {  // the cell left of the tile: none at the domain's left boundary
+      if (cx0 > 0) {
+        dev::xcell_top<T, K, true, CW>(g, h, 0, P, rl, pl);
+      } else {
+        rl = dev::zero<T>();
+        pl = dev::zero<T>();
+      }
+    }
     r[0] = dev::add(r[0], rl);
     p[0] = dev::add(p[0], pl);
 #pragma unroll
     for (int m = 0; m < K; ++m) { R[m] = r[m]; Pp[m] = p[m]; }
   };
-  const int yrow = y0 + w;
-  const int cell = cx0 + lane;
+  const int yrow = y0 + trow;
+  const int cell = cx0 + lx;
   const bool row_ok = (yrow >= 1 && yrow <= n1 - 2) && (cell < N);
   T accA[K][K + 1], accB[K][K + 1];
 #pragma unroll
@@ -311,21 +340,30 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
 #pragma unroll
     for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = dev::zero<T>(); accB[m][mo] = dev::zero<T>(); }
 
+  auto emit_node = [&](int z, int m, int mo, T va, T vb) {
+    const int x = K * cell + m;
+    if (x < 1) return;
+    const long long idx = ((long long)z * n1 + yrow) * n1 + x;
+    S invD{};
+    if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
+    dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, va, vb, invD);
+  };
   auto emit = [&](int cz) {
     if (!row_ok) return;
 #pragma unroll
     for (int mo = 0; mo < K; ++mo) {
       const int z = K * cz + mo;
       if (z < 1) continue;
+      if (mo == 0 && hold_bottom && cz == c0) {  // completed after the cluster exchange
 #pragma unroll
-      for (int m = 0; m < K; ++m) {
-        const int x = K * cell + m;
-        if (x < 1) continue;
-        const long long idx = ((long long)z * n1 + yrow) * n1 + x;
-        S invD{};
-        if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
-        dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, accA[m][mo], accB[m][mo], invD);
+        for (int m = 0; m < K; ++m) {
+          shold[m * NT + tid] = accA[m][0];
+          if constexpr (DUAL) shold[(K + m) * NT + tid] = accB[m][0];
+        }
+        continue;
       }
+#pragma unroll
+      for (int m = 0; m < K; ++m) emit_node(z, m, mo, accA[m][mo], accB[m][mo]);
     }
   };
 
@@ -355,6 +393,33 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     xpass(R, Pp);
     dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
     if (c1 - 1 >= c0) emit(c1 - 1);
+  }
+  if (clustered) {
+    // accA[.][K] (accB) now hold the last cell's contributions to the vertex plane above the
+    // chunk: publish them in this CTA's (now idle) staging buffers for the chunk above
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      sg[m * NT + tid] = accA[m][K];
+      if constexpr (DUAL) sh[m * NT + tid] = accB[m][K];
+    }
+    cluster.sync();
+    if (hold_bottom && row_ok) {
+      const unsigned below = cluster.block_rank() - 1;
+      const T* ca = cluster.map_shared_rank(sg, below);
+      const T* cb = DUAL ? cluster.map_shared_rank(sh, below) : nullptr;
+      const int z = K * c0;
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const T va = dev::add(shold[m * NT + tid], ca[m * NT + tid]);
+        T vb = dev::zero<T>();
+        if constexpr (DUAL) vb = dev::add(shold[(K + m) * NT + tid], cb[m * NT + tid]);
+        emit_node(z, m, 0, va, vb);
+      }
+    }
+    cluster.sync();  // the chunk above has read this CTA's shared memory
   }
 }
 
@@ -503,26 +568,113 @@ inline int pick_zc(int N, long long base_ctas, long long slots, int K) {
   return best;
 }
 
+constexpr int kMaxClusterChunks = 16;  // z chunks per thread-block cluster (above 8: non-portable size)
+
+// Clusters of nch CTAs of this kernel that fit on the device at once (0: not launchable as a cluster).
+template <typename Kern>
+int max_active_clusters(Kern kern, int nch, int threads, dim3 grid) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = nch;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (nch > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T, int K, int EPI, int CXS>
+cudaError_t launch_op3d(int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                        const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
+  const int cx = CXS, cy = Tile3D<K, CXS>::CY;
+  const int ntx = (P.N + cx - 1) / cx;
+  OpParams<T> Q = P;
+  {
+    auto kern = op3d_kernel<T, K, EPI, CXS>;
+    const int threads = 32 * Warps3D<K>::value;
+    static int occ = 0;
+    if (occ == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
+      if (occ < 1) occ = 1;
+    }
+    // per kernel: clusters of nch chunks that fit at once (-1: not yet asked)
+    static int clusters_fit[kMaxClusterChunks + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                                      -1, -1, -1, -1, -1, -1, -1, -1};
+    Q.ntile_y = (P.N + cy - 1) / cy;
+    const long long base = (long long)ntx * Q.ntile_y * nstage;
+    const long long slots = (long long)occ * device_sm_count();
+    // candidates: chunked with a re-streamed cell below (any nch), or clustered (2 <= nch <= 16,
+    // no re-streamed cell, resident as whole clusters)
+    int best_zc = P.N, best_cl = 0;
+    long long best_cost = -1;
+    for (int zc = 1; zc <= P.N; ++zc) {
+      if (P.zc > 0 && zc != P.zc) continue;
+      const int nch = (P.N + zc - 1) / zc;
+      {
+        const long long waves = (base * nch + slots - 1) / slots;
+        const long long cost = waves * ((long long)K * (zc + (nch > 1 ? 1 : 0)) + 1);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_zc = zc; best_cl = 0; }
+      }
+      if (nch >= 2 && nch <= kMaxClusterChunks && (P.N % zc == 0 || nch * zc - P.N < zc)) {
+        if (clusters_fit[nch] < 0)
+          clusters_fit[nch] = max_active_clusters(kern, nch, threads, dim3(ntx, Q.ntile_y * nch, nstage));
+        if (clusters_fit[nch] > 0) {
+          const long long waves = (base + clusters_fit[nch] - 1) / clusters_fit[nch];
+          const long long cost = waves * ((long long)K * zc + 1);
+          if (cost < best_cost) { best_cost = cost; best_zc = zc; best_cl = 1; }
+        }
+      }
+    }
+    Q.zc = best_zc;
+    Q.nch = (P.N + Q.zc - 1) / Q.zc;
+    Q.cluster = best_cl;
+    dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
+    if (!Q.cluster) {
+      kern<<<grid, threads, 0, st>>>(u, Q, E);
+      return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = Q.nch;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, u, Q, E);
+  }
+}
+
 template <typename T, int K, int EPI>
 cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
                         const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
-  int cx, cy;
-  op_tile_shape_impl(dim, K, &cx, &cy);
-  const int ntx = (P.N + cx - 1) / cx;
-  OpParams<T> Q = P;
   if (dim == 3) {
-    const int threads = 32 * K * cy;
-    static int occ = 0;
-    if (occ == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op3d_kernel<T, K, EPI>, threads, 0);
-      if (occ < 1) occ = 1;
+    // FP32 (multigrid levels of every size): narrower warp segments on meshes of at most 16 cells
+    if constexpr (sizeof(T) == 4) {
+      if (P.N <= 8) return launch_op3d<T, K, EPI, 8>(nstage, u, P, E, st);
+      if (P.N <= 16) return launch_op3d<T, K, EPI, 16>(nstage, u, P, E, st);
     }
-    Q.ntile_y = (P.N + cy - 1) / cy;
-    if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * Q.ntile_y * nstage, (long long)occ * device_sm_count(), K);
-    const int nch = (P.N + Q.zc - 1) / Q.zc;
-    dim3 grid(ntx, Q.ntile_y * nch, nstage);
-    op3d_kernel<T, K, EPI><<<grid, threads, 0, st>>>(u, Q, E);
+    return launch_op3d<T, K, EPI, 32>(nstage, u, P, E, st);
   } else {
+    int cx, cy;
+    op_tile_shape_impl(dim, K, &cx, &cy);
+    const int ntx = (P.N + cx - 1) / cx;
+    OpParams<T> Q = P;
     static int occ = 0;
     if (occ == 0) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op2d_kernel<T, K, EPI>, 64, 0);

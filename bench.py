@@ -436,6 +436,7 @@ def main():
                 "roofline": roof,
                 "roofline_smoother": roof_sm,
                 "category_ms_one_step": {k: round(v[0], 4) for k, v in cat_ms.items()},
+                "autotune": pkg.autotune_report().splitlines(),
                 "clocks": clk}
         if world == 1 and not args.no_fp64_baseline:
             line["gpu_fp64_per_stage_baseline"] = fp64_per_stage_baseline(w, cheb, units)

@@ -76,6 +76,9 @@ typedef struct {
   int shared_cheb;    /* 1: one Chebyshev interval for all blocks (batched mode of Sec. 5.4) */
   int op_ff;          /* FP64-accurate operator apply: 1 float-float on the FP32 pipe (default,
                          about 48 significant bits; |values| within 1e-30..1e30), 0 native FP64 */
+  int autotune;       /* 1: time the 3D operator kernels' launch shapes (tile width, z chunk,
+                         cluster) at create on the handle's own buffers and keep the fastest,
+                         process-wide per kernel and size (default 1); 0: cost model only */
 } irk_options;
 
 typedef struct {
@@ -177,6 +180,13 @@ long long irk_stage_stride(irk_handle h);     /* elements between stage vectors 
 int irk_num_levels(irk_handle h);
 const char* irk_strerror(irk_status s);
 const char* irk_last_error(irk_handle h);
+
+/* Text report of the launch shapes chosen by the autotuner so far in this process, one line
+ * per kernel and size ("<kernel> k=.. <epilogue> N=.. stages=..: cxs=.. zc=.. cluster=.. <us>
+ * (model ...)").  Writes at most len-1 bytes and a terminating NUL into buf (buf may be NULL);
+ * returns the full length of the report.  No paper counterpart (implementation detail of the
+ * batched launches of Sec. 5.4). */
+int irk_autotune_report(char* buf, int len);
 
 /* y (device, irk_ndofs doubles) <- nodal interpolant of prod sin(pi x_a) cos t. */
 irk_status irk_interpolate_initial(irk_handle h, double* y, double t);

@@ -10,7 +10,8 @@ from . import _capi
 from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkRequest, IrkResult,
                     IrkServeOptions, IrkStats, TABLEAU_FIELDS, check, lib)
 
-__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "lib", "options", "serve", "solve_batch"]
+__all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "autotune_report", "lib", "options", "serve",
+           "solve_batch"]
 
 
 def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, **solver_opts):
@@ -61,6 +62,14 @@ def solve_batch(solvers, ys, t_ns):
     per = (ctypes.c_int * n)()
     status = lib().irk_solve_batch(hs, yp, ts, n, per)
     return status, list(per)
+
+
+def autotune_report():
+    """Launch shapes chosen so far by the operator autotuner (one line per kernel and size)."""
+    n = lib().irk_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().irk_autotune_report(buf, n + 1)
+    return buf.value.decode()
 
 
 def _ptr(t):

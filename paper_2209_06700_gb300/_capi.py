@@ -27,7 +27,7 @@ class IrkOptions(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("variant", ctypes.c_int), ("mg_precision", ctypes.c_int),
                 ("batched", ctypes.c_int), ("use_graph", ctypes.c_int), ("eig_steps", ctypes.c_int),
                 ("smoothing_range", ctypes.c_double), ("eig_safety", ctypes.c_double),
-                ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int)]
+                ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class IrkRequest(ctypes.Structure):
@@ -73,6 +73,7 @@ SIGNATURES = {
     "irk_num_levels": (_I, [_H]),
     "irk_strerror": (ctypes.c_char_p, [_I]),
     "irk_last_error": (ctypes.c_char_p, [_H]),
+    "irk_autotune_report": (_I, [ctypes.c_char_p, _I]),
     "irk_interpolate_initial": (_I, [_H, _P, _D]),
     "irk_get_tableau": (_I, [_H, _I, ctypes.POINTER(_D)]),
     "irk_get_cheb_interval": (_I, [_H, _I, _I, ctypes.POINTER(_D)]),

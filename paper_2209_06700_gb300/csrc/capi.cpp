@@ -311,6 +311,36 @@ Status with_ff_io(irk_problem* h, const double* in, long long nin, double* out, 
   return Status::Ok();
 }
 
+// Launch shapes of the FP64-accurate fine-mesh operator: the stage operator (DUAL epilogue, Q
+// stages, or the DIAG blocks' 1 and 2) and K y_n (STORE, 1 stage), timed on the handle's stage
+// buffers before they hold data.
+template <typename S>
+Status autotune_stage_operator_t(irk_problem* h) {
+  using T = typename std::conditional<std::is_same<S, ff>::value, ff, double>::type;
+  const LevelGeom& g = h->fine;
+  std::vector<int> counts{h->Q};
+  if (h->opt.variant == IRK_VARIANT_DIAG) counts = {1, 2};
+  std::vector<double> one(kMaxStages, 1.0);
+  for (int ns : counts) {
+    OpParams<T> P = make_op_params<T>(g, ns, one.data(), one.data());
+    EpiParams<S> E;
+    std::memset(&E, 0, sizeof(E));
+    E.out = as<S>(h->Mu);
+    E.out2 = as<S>(h->Ku);
+    IRK_CUDA(tune_op<T>(h->dim, h->k, ns, as<S>(h->kst), P, EPI_DUAL, E, h->st));
+  }
+  OpParams<T> P1 = make_op_params<T>(g, 1, one.data(), one.data());
+  EpiParams<S> E1;
+  std::memset(&E1, 0, sizeof(E1));
+  E1.out = as<S>(h->Ky);
+  IRK_CUDA(tune_op<T>(h->dim, h->k, 1, as<S>(h->kst), P1, EPI_STORE, E1, h->st));
+  return Status::Ok();
+}
+
+Status autotune_stage_operator(irk_problem* h) {
+  return h->opt.op_ff ? autotune_stage_operator_t<ff>(h) : autotune_stage_operator_t<double>(h);
+}
+
 Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt, void* stream,
               irk_problem* h) {
   if (!mesh) return Status::Err(IRK_EINVAL, "mesh is NULL");
@@ -400,6 +430,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   mc.cheb_degree = o.cheb_degree; mc.eig_steps = o.eig_steps;
   mc.smoothing_range = o.smoothing_range; mc.eig_safety = o.eig_safety;
   mc.shared_cheb = o.shared_cheb; mc.batched = o.batched; mc.precision = o.mg_precision;
+  mc.autotune = o.autotune;
   // LU blocks (also used by the per-step entry points of the C ABI)
   mc.nb = Q;
   mc.cm = h->tab.lam;
@@ -417,6 +448,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
     }
     IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena, h->st));
   }
+  if (o.autotune) IRK_TRY(autotune_stage_operator(h));
   IRK_CUDA(cudaStreamSynchronize(h->st));
   return Status::Ok();
 }
@@ -466,6 +498,7 @@ void irk_default_options(irk_options* o) {
   o->eig_safety = 1.2;
   o->shared_cheb = 0;
   o->op_ff = 1;
+  o->autotune = 1;
 }
 
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,
@@ -590,6 +623,8 @@ const char* irk_strerror(irk_status s) {
 }
 
 const char* irk_last_error(irk_handle h) { return h ? h->last_err.c_str() : "NULL handle"; }
+
+int irk_autotune_report(char* buf, int len) { return tune_report(buf, len); }
 
 irk_status irk_interpolate_initial(irk_handle h, double* y, double t) {
   return guarded(h, [&]() -> Status {

@@ -63,6 +63,19 @@ cudaError_t launch_op(int dim, int k, int nstage, const typename Storage<T>::typ
 // Tile shape used by launch_op (cells per CTA in x and y) for a degree k.
 void op_tile_shape(int dim, int k, int* cx, int* cy);
 
+// Autotuning of a 3D operator launch: times the candidate launch shapes (warp-segment width,
+// z chunk, thread-block cluster) on this call's arguments and keeps the fastest for every later
+// launch of the same kernel with the same cells per axis and stage count (process-wide).  The
+// call's outputs must be scratch: the candidates run repeatedly.  Returns at once when the
+// shape is known, for 2D, during stream capture, and for small launches (model shape kept).
+template <typename T>
+cudaError_t tune_op(int dim, int k, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                    int epi, const EpiParams<typename Storage<T>::type>& E, cudaStream_t st);
+// Registry of the tuned shapes (tune.cpp): one line per tuned kernel and size.
+void tune_record(const char* kernel, int k, int epi, int N, int nstage, int cxs, int zc, int cluster,
+                 double us, double us_model, int model_cxs, int model_zc, int model_cluster);
+int tune_report(char* buf, int len);
+
 // ---------------- pointwise / vector kernels (vec.cu) ----------------
 
 constexpr int kMaxQ = 9;  // stage-combination matrices are at most 9 x 9

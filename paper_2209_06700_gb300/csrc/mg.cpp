@@ -274,7 +274,35 @@ class MG final : public MGBase {
     IRK_TRY(setup_coarse());
     IRK_TRY(setup_chebyshev(st));
     IRK_TRY(setup_fused());
+    if (cfg_.autotune) IRK_TRY(autotune(st));
     IRK_CUDA(cudaStreamSynchronize(st));
+    return Status::Ok();
+  }
+
+  // Launch shapes of the level operators (Chebyshev step and residual, batched blocks), timed on
+  // the levels' own buffers before they hold data (process-wide cache; see tune_op).
+  Status autotune(cudaStream_t st) {
+    if (!cfg_.batched) return Status::Ok();
+    const int nb = cfg_.nb;
+    const int last = fused_ ? lc_ : levels() - 1;
+    for (int l = 0; l < last; ++l) {
+      Lvl& L = lv_[l];
+      OpParams<T> P = make_op_params<T>(L.g, nb, cfg_.cm.data(), ck_.data());
+      EpiParams<T> E;
+      std::memset(&E, 0, sizeof(E));
+      E.out = L.xb;
+      E.b = L.b;
+      E.xj = L.xa;
+      for (int s = 0; s < nb; ++s) { E.c1[s] = (T)L.c1[cfg_.cheb_degree > 1 ? 1 : 0][s]; E.c2[s] = (T)L.c2[0][s]; }
+      for (int r = 0; r < kMaxDeg; ++r) { E.dmr[r] = (T)L.g.dmr[r]; E.dkr[r] = (T)L.g.dkr[r]; }
+      IRK_CUDA(tune_op<T>(cfg_.dim, cfg_.k, nb, L.xa, P, EPI_CHEB, E, st));
+      IRK_CUDA(tune_op<T>(cfg_.dim, cfg_.k, nb, L.xa, P, EPI_RESID, E, st));
+    }
+    // the buffers used as scratch above start from zero again
+    for (int l = 0; l < last; ++l) {
+      const size_t vb = (size_t)nb * lv_[l].g.ld * sizeof(T);
+      IRK_CUDA(cudaMemsetAsync(lv_[l].xb, 0, vb, st));
+    }
     return Status::Ok();
   }
 

@@ -16,4 +16,15 @@ cudaError_t launch_op<float>(int dim, int k, int nstage, const float* u, const O
   }
 }
 
+template <>
+cudaError_t tune_op<float>(int dim, int k, int nstage, const float* u, const OpParams<float>& P, int epi,
+                         const EpiParams<float>& E, cudaStream_t st) {
+  switch (epi) {
+    case EPI_STORE: return tune_op_e<float, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_RESID: return tune_op_e<float, EPI_RESID>(dim, k, nstage, u, P, E, st);
+    case EPI_CHEB: return tune_op_e<float, EPI_CHEB>(dim, k, nstage, u, P, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace irk

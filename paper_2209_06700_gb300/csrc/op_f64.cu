@@ -15,4 +15,16 @@ cudaError_t launch_op<double>(int dim, int k, int nstage, const double* u, const
   }
 }
 
+template <>
+cudaError_t tune_op<double>(int dim, int k, int nstage, const double* u, const OpParams<double>& P, int epi,
+                         const EpiParams<double>& E, cudaStream_t st) {
+  switch (epi) {
+    case EPI_STORE: return tune_op_e<double, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_DUAL: return tune_op_e<double, EPI_DUAL>(dim, k, nstage, u, P, E, st);
+    case EPI_RESID: return tune_op_e<double, EPI_RESID>(dim, k, nstage, u, P, E, st);
+    case EPI_CHEB: return tune_op_e<double, EPI_CHEB>(dim, k, nstage, u, P, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace irk

@@ -15,4 +15,14 @@ cudaError_t launch_op<ff>(int dim, int k, int nstage, const ff* u, const OpParam
   }
 }
 
+template <>
+cudaError_t tune_op<ff>(int dim, int k, int nstage, const ff* u, const OpParams<ff>& P, int epi,
+                         const EpiParams<ff>& E, cudaStream_t st) {
+  switch (epi) {
+    case EPI_STORE: return tune_op_e<ff, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_DUAL: return tune_op_e<ff, EPI_DUAL>(dim, k, nstage, u, P, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace irk

@@ -37,6 +37,10 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+#include <vector>
+
 #include "ffmath.cuh"
 #include "kernels.h"
 
@@ -112,6 +116,25 @@ __device__ __forceinline__ void ytaps_dispatch(int r, const T* col, int stride, 
   if constexpr (R < K) {
     if (r == R) ytaps<T, K, R>(col, stride, P, g, h);
     else ytaps_dispatch<T, K, R + 1>(r, col, stride, P, g, h);
+  }
+}
+
+// One staged row of y taps (slots lane, lane + 32, ... < SL) with the tap row R fixed for the loop.
+template <typename T, int K, int SL, int R>
+__device__ __forceinline__ void yrow(const T* colbase, const OpParams<T>& P, T* gout, T* hout, int lane) {
+  for (int sl = lane; sl < SL; sl += 32) {
+    T g = zero<T>(), h = zero<T>();
+    ytaps<T, K, R>(colbase + sl, SL, P, g, h);
+    gout[sl] = g;
+    hout[sl] = h;
+  }
+}
+template <typename T, int K, int SL, int R = 0>
+__device__ __forceinline__ void yrow_dispatch(int r, const T* colbase, const OpParams<T>& P, T* gout, T* hout,
+                                              int lane) {
+  if constexpr (R < K) {
+    if (r == R) yrow<T, K, SL, R>(colbase, P, gout, hout, lane);
+    else yrow_dispatch<T, K, SL, R + 1>(r, colbase, P, gout, hout, lane);
   }
 }
 
@@ -340,13 +363,16 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
 #pragma unroll
     for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = dev::zero<T>(); accB[m][mo] = dev::zero<T>(); }
 
+  // the thread's output nodes (z, yrow, K cell + m) sit at rowbase + z * n1^2 + m in stage s
+  // (32-bit offsets within a stage vector; the stage offset is uniform across the CTA)
+  const int rowbase = yrow * n1 + K * cell;
+  const int plane32 = n1 * n1;
+  const long long sbase = (long long)s * P.ld;
   auto emit_node = [&](int z, int m, int mo, T va, T vb) {
-    const int x = K * cell + m;
-    if (x < 1) return;
-    const long long idx = ((long long)z * n1 + yrow) * n1 + x;
+    if (m == 0 && cell == 0) return;  // x = 0: boundary node
     S invD{};
     if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
-    dev::epilogue<T, EPI>(E, (long long)s * P.ld + idx, s, va, vb, invD);
+    dev::epilogue<T, EPI>(E, sbase + (rowbase + z * plane32 + m), s, va, vb, invD);
   };
   auto emit = [&](int cz) {
     if (!row_ok) return;
@@ -535,6 +561,11 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   }
 }
 
+template <typename T> const char* tune_kernel_name();
+template <> inline const char* tune_kernel_name<float>() { return "op3d<float>"; }
+template <> inline const char* tune_kernel_name<double>() { return "op3d<double>"; }
+template <> inline const char* tune_kernel_name<ff>() { return "op3d<ff>"; }
+
 inline void op_tile_shape_impl(int dim, int k, int* cx, int* cy) {
   if (dim == 2) { *cx = 64; *cy = 1; return; }
   *cx = 32;
@@ -595,97 +626,238 @@ int max_active_clusters(Kern kern, int nch, int threads, dim3 grid) {
   return n;
 }
 
+// Launch shape of the 3D kernel: warp-segment width (cells), z chunk (cells), cluster mode.
+struct OpShape {
+  int cxs = 32, zc = 1, cluster = 0;
+};
+
+// Per kernel instantiation: occupancy and cluster fit, queried once.
 template <typename T, int K, int EPI, int CXS>
-cudaError_t launch_op3d(int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
-                        const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
-  const int cx = CXS, cy = Tile3D<K, CXS>::CY;
-  const int ntx = (P.N + cx - 1) / cx;
-  OpParams<T> Q = P;
-  {
-    auto kern = op3d_kernel<T, K, EPI, CXS>;
-    const int threads = 32 * Warps3D<K>::value;
-    static int occ = 0;
-    if (occ == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
-      if (occ < 1) occ = 1;
+struct Op3dInfo {
+  static int occ() {
+    static int o = 0;
+    if (o == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, op3d_kernel<T, K, EPI, CXS>, 32 * Warps3D<K>::value, 0);
+      if (o < 1) o = 1;
     }
-    // per kernel: clusters of nch chunks that fit at once (-1: not yet asked)
-    static int clusters_fit[kMaxClusterChunks + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1,
-                                                      -1, -1, -1, -1, -1, -1, -1, -1};
-    Q.ntile_y = (P.N + cy - 1) / cy;
-    const long long base = (long long)ntx * Q.ntile_y * nstage;
-    const long long slots = (long long)occ * device_sm_count();
-    // candidates: chunked with a re-streamed cell below (any nch), or clustered (2 <= nch <= 16,
-    // no re-streamed cell, resident as whole clusters)
-    int best_zc = P.N, best_cl = 0;
-    long long best_cost = -1;
-    for (int zc = 1; zc <= P.N; ++zc) {
-      if (P.zc > 0 && zc != P.zc) continue;
-      const int nch = (P.N + zc - 1) / zc;
-      {
-        const long long waves = (base * nch + slots - 1) / slots;
-        const long long cost = waves * ((long long)K * (zc + (nch > 1 ? 1 : 0)) + 1);
-        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best_zc = zc; best_cl = 0; }
-      }
-      if (nch >= 2 && nch <= kMaxClusterChunks && (P.N % zc == 0 || nch * zc - P.N < zc)) {
-        if (clusters_fit[nch] < 0)
-          clusters_fit[nch] = max_active_clusters(kern, nch, threads, dim3(ntx, Q.ntile_y * nch, nstage));
-        if (clusters_fit[nch] > 0) {
-          const long long waves = (base + clusters_fit[nch] - 1) / clusters_fit[nch];
-          const long long cost = waves * ((long long)K * zc + 1);
-          if (cost < best_cost) { best_cost = cost; best_zc = zc; best_cl = 1; }
-        }
-      }
-    }
-    Q.zc = best_zc;
-    Q.nch = (P.N + Q.zc - 1) / Q.zc;
-    Q.cluster = best_cl;
-    dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
-    if (!Q.cluster) {
-      kern<<<grid, threads, 0, st>>>(u, Q, E);
-      return cudaGetLastError();
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(threads);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1;
-    attr[0].val.clusterDim.y = Q.nch;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, u, Q, E);
+    return o;
   }
+  // clusters of nch chunks that fit on the device at once (0: not launchable as a cluster)
+  static int clusters_fit(int nch, dim3 grid) {
+    static int fit[kMaxClusterChunks + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1,
+                                             -1, -1, -1, -1, -1, -1, -1, -1};
+    if (nch < 2 || nch > kMaxClusterChunks) return 0;
+    if (fit[nch] < 0) fit[nch] = max_active_clusters(op3d_kernel<T, K, EPI, CXS>, nch, 32 * Warps3D<K>::value, grid);
+    return fit[nch];
+  }
+};
+
+// Cost model: waves x planes streamed per CTA (a chunk off the bottom re-streams the cell below it
+// unless its tile's chunks form a cluster).
+template <typename T, int K, int EPI, int CXS>
+OpShape model_shape(int N, int nstage) {
+  using I = Op3dInfo<T, K, EPI, CXS>;
+  const int ntx = (N + CXS - 1) / CXS, nty = (N + Tile3D<K, CXS>::CY - 1) / Tile3D<K, CXS>::CY;
+  const long long base = (long long)ntx * nty * nstage;
+  const long long slots = (long long)I::occ() * device_sm_count();
+  OpShape best;
+  best.cxs = CXS;
+  long long best_cost = -1;
+  for (int zc = 1; zc <= N; ++zc) {
+    const int nch = (N + zc - 1) / zc;
+    const long long waves = (base * nch + slots - 1) / slots;
+    const long long cost = waves * ((long long)K * (zc + (nch > 1 ? 1 : 0)) + 1);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best.zc = zc; best.cluster = 0; }
+    const int fit = I::clusters_fit(nch, dim3(ntx, nty * nch, nstage));
+    if (fit > 0) {
+      const long long cw = (base + fit - 1) / fit;
+      const long long ccost = cw * ((long long)K * zc + 1);
+      if (ccost < best_cost) { best_cost = ccost; best.zc = zc; best.cluster = 1; }
+    }
+  }
+  return best;
+}
+
+template <typename T, int K, int EPI, int CXS>
+cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                         const EpiParams<typename Storage<T>::type>& E, cudaStream_t st, const OpShape& sh) {
+  auto kern = op3d_kernel<T, K, EPI, CXS>;
+  const int threads = 32 * Warps3D<K>::value;
+  OpParams<T> Q = P;
+  const int ntx = (P.N + CXS - 1) / CXS;
+  Q.ntile_y = (P.N + Tile3D<K, CXS>::CY - 1) / Tile3D<K, CXS>::CY;
+  Q.zc = sh.zc;
+  Q.nch = (P.N + Q.zc - 1) / Q.zc;
+  Q.cluster = sh.cluster;
+  dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
+  if (!Q.cluster) {
+    kern<<<grid, threads, 0, st>>>(u, Q, E);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = Q.nch;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, u, Q, E);
+}
+
+// Process-wide autotuned shapes per kernel instantiation, keyed by (cells per axis, stages).
+template <typename T, int K, int EPI>
+struct OpTuned {
+  static std::mutex& mu() { static std::mutex m; return m; }
+  static std::map<long long, OpShape>& table() { static std::map<long long, OpShape> t; return t; }
+  static long long key(int N, int ns) { return ((long long)N << 8) | ns; }
+  static bool find(int N, int ns, OpShape& out) {
+    std::lock_guard<std::mutex> lock(mu());
+    auto it = table().find(key(N, ns));
+    if (it == table().end()) return false;
+    out = it->second;
+    return true;
+  }
+  static void put(int N, int ns, const OpShape& sh) {
+    std::lock_guard<std::mutex> lock(mu());
+    table()[key(N, ns)] = sh;
+  }
+};
+
+template <typename T> constexpr bool narrow_tiles() { return sizeof(T) == 4; }  // FP32 levels only
+inline int default_cxs(int N) { return N <= 8 ? 8 : (N <= 16 ? 16 : 32); }
+
+template <typename T, int K, int EPI>
+OpShape default_shape(int N, int nstage) {
+  if constexpr (narrow_tiles<T>()) {
+    const int c = default_cxs(N);
+    if (c == 8) return model_shape<T, K, EPI, 8>(N, nstage);
+    if (c == 16) return model_shape<T, K, EPI, 16>(N, nstage);
+  }
+  return model_shape<T, K, EPI, 32>(N, nstage);
+}
+
+template <typename T, int K, int EPI>
+cudaError_t launch_by_shape(int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                            const EpiParams<typename Storage<T>::type>& E, cudaStream_t st, const OpShape& sh) {
+  if constexpr (narrow_tiles<T>()) {
+    if (sh.cxs == 8) return launch_shape<T, K, EPI, 8>(nstage, u, P, E, st, sh);
+    if (sh.cxs == 16) return launch_shape<T, K, EPI, 16>(nstage, u, P, E, st, sh);
+  }
+  return launch_shape<T, K, EPI, 32>(nstage, u, P, E, st, sh);
 }
 
 template <typename T, int K, int EPI>
 cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
                         const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
   if (dim == 3) {
-    // FP32 (multigrid levels of every size): narrower warp segments on meshes of at most 16 cells
-    if constexpr (sizeof(T) == 4) {
-      if (P.N <= 8) return launch_op3d<T, K, EPI, 8>(nstage, u, P, E, st);
-      if (P.N <= 16) return launch_op3d<T, K, EPI, 16>(nstage, u, P, E, st);
-    }
-    return launch_op3d<T, K, EPI, 32>(nstage, u, P, E, st);
-  } else {
-    int cx, cy;
-    op_tile_shape_impl(dim, K, &cx, &cy);
-    const int ntx = (P.N + cx - 1) / cx;
-    OpParams<T> Q = P;
-    static int occ = 0;
-    if (occ == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op2d_kernel<T, K, EPI>, 64, 0);
-      if (occ < 1) occ = 1;
-    }
-    if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * nstage, (long long)occ * device_sm_count(), K);
-    const int nch = (P.N + Q.zc - 1) / Q.zc;
-    dim3 grid(ntx, nch, nstage);
-    op2d_kernel<T, K, EPI><<<grid, 64, 0, st>>>(u, Q, E);
+    OpShape sh;
+    if (!OpTuned<T, K, EPI>::find(P.N, nstage, sh)) sh = default_shape<T, K, EPI>(P.N, nstage);
+    return launch_by_shape<T, K, EPI>(nstage, u, P, E, st, sh);
   }
+  int cx, cy;
+  op_tile_shape_impl(dim, K, &cx, &cy);
+  const int ntx = (P.N + cx - 1) / cx;
+  OpParams<T> Q = P;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, op2d_kernel<T, K, EPI>, 64, 0);
+    if (occ < 1) occ = 1;
+  }
+  if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * nstage, (long long)occ * device_sm_count(), K);
+  const int nch = (P.N + Q.zc - 1) / Q.zc;
+  dim3 grid(ntx, nch, nstage);
+  op2d_kernel<T, K, EPI><<<grid, 64, 0, st>>>(u, Q, E);
   return cudaGetLastError();
+}
+
+// Autotuner of the 3D launch shape: times the candidate shapes (segment width, z chunk, cluster
+// mode) of this kernel on the call's own arguments and keeps the fastest for every later launch
+// of the same kernel, cells per axis and stage count.  The call's outputs must be scratch (the
+// candidates run repeatedly); levels below kTuneMinNodes stage-nodes keep the model's shape.
+constexpr long long kTuneMinNodes = 1 << 18;
+
+template <typename T, int K, int EPI>
+cudaError_t tune_op_k(int dim, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                      const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
+  if (dim != 3) return cudaSuccess;
+  OpShape known;
+  if (OpTuned<T, K, EPI>::find(P.N, nstage, known)) return cudaSuccess;
+  const long long nodes = (long long)P.n1 * P.n1 * P.n1 * nstage;
+  const OpShape model = default_shape<T, K, EPI>(P.N, nstage);
+  if (nodes < kTuneMinNodes) {
+    OpTuned<T, K, EPI>::put(P.N, nstage, model);
+    return cudaSuccess;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return cudaSuccess;
+  // candidates: the model's segment width (and 32 for FP32 levels), every distinct chunk count,
+  // with and without a cluster where one fits
+  std::vector<OpShape> cands;
+  std::vector<int> widths = {model.cxs};
+  if (model.cxs != 32) widths.push_back(32);
+  for (int cxs : widths) {
+    int last_nch = -1;
+    for (int zc = 1; zc <= P.N; ++zc) {
+      const int nch = (P.N + zc - 1) / zc;
+      if (nch == last_nch) continue;
+      last_nch = nch;
+      OpShape c;
+      c.cxs = cxs;
+      c.zc = zc;
+      c.cluster = 0;
+      cands.push_back(c);
+      if (nch >= 2 && nch <= kMaxClusterChunks) {
+        c.cluster = 1;
+        cands.push_back(c);
+      }
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cudaGetLastError(); }
+  OpShape best = model;
+  float best_ms = -1.f, model_ms = -1.f;
+  for (const OpShape& c : cands) {
+    if (c.cluster) {  // skip cluster shapes the device cannot hold
+      const int cy = (c.cxs == 8) ? Tile3D<K, 8>::CY : (c.cxs == 16) ? Tile3D<K, 16>::CY : Tile3D<K, 32>::CY;
+      const int nch = (P.N + c.zc - 1) / c.zc;
+      const dim3 grid((P.N + c.cxs - 1) / c.cxs, ((P.N + cy - 1) / cy) * nch, nstage);
+      int fit = 0;
+      if constexpr (narrow_tiles<T>()) {
+        fit = (c.cxs == 8) ? Op3dInfo<T, K, EPI, 8>::clusters_fit(nch, grid)
+              : (c.cxs == 16) ? Op3dInfo<T, K, EPI, 16>::clusters_fit(nch, grid)
+                              : Op3dInfo<T, K, EPI, 32>::clusters_fit(nch, grid);
+      } else {
+        fit = Op3dInfo<T, K, EPI, 32>::clusters_fit(nch, grid);
+      }
+      if (fit <= 0) continue;
+    }
+    if (launch_by_shape<T, K, EPI>(nstage, u, P, E, st, c) != cudaSuccess) {  // warm-up
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2; ++r) launch_by_shape<T, K, EPI>(nstage, u, P, E, st, c);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms *= 0.5f;
+    if (c.cxs == model.cxs && c.zc == model.zc && c.cluster == model.cluster) model_ms = ms;
+    if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  OpTuned<T, K, EPI>::put(P.N, nstage, best);
+  tune_record(tune_kernel_name<T>(), K, EPI, P.N, nstage, best.cxs, best.zc, best.cluster, 1e3 * best_ms,
+              model_ms < 0.f ? -1.0 : 1e3 * model_ms, model.cxs, model.zc, model.cluster);
+  return cudaSuccess;
 }
 
 template <typename T, int EPI>
@@ -700,4 +872,16 @@ cudaError_t launch_op_e(int dim, int k, int nstage, const typename Storage<T>::t
   }
 }
 
+
+template <typename T, int EPI>
+cudaError_t tune_op_e(int dim, int k, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
+                      const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
+  switch (k) {
+    case 1: return tune_op_k<T, 1, EPI>(dim, nstage, u, P, E, st);
+    case 2: return tune_op_k<T, 2, EPI>(dim, nstage, u, P, E, st);
+    case 3: return tune_op_k<T, 3, EPI>(dim, nstage, u, P, E, st);
+    case 4: return tune_op_k<T, 4, EPI>(dim, nstage, u, P, E, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 }  // namespace irk

@@ -107,6 +107,7 @@ struct MGConfig {
   int shared_cheb;
   int batched;
   int precision;             // 32 or 64
+  int autotune = 1;          // time the level operators' launch shapes at setup
 };
 
 Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,

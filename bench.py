@@ -253,6 +253,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-baseline-requests", type=int, default=512)
     ap.add_argument("--op-ff", type=int, default=1, choices=[0, 1], help="float-float (1) or native FP64 (0) operator")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="time the operator launch shapes at create (1) or keep the cost model's (0)")
     ap.add_argument("--cheb-degree", type=int, default=None)
     ap.add_argument("--smoothing-range", type=float, default=None)
     ap.add_argument("--eig-safety", type=float, default=None)
@@ -289,7 +291,7 @@ def main():
     cheb = w.cheb_degree if args.cheb_degree is None else args.cheb_degree
     s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=cheb,
                    mg_precision=args.mg_precision, batched=0 if args.per_stage else 1, variant=variant,
-                   op_ff=args.op_ff, **extra)
+                   op_ff=args.op_ff, autotune=args.autotune, **extra)
     lib = _capi.lib()
     y = s.vector()
     with torch.cuda.stream(stream):

@@ -154,7 +154,9 @@ typedef struct {
   irk_options solver;         /* solver options of every request */
 } irk_serve_options;
 
-/* Default serving options: 16 slots, automatic budget, real time, solver defaults with restart 16. */
+/* Default serving options: 16 slots, automatic budget, real time, solver defaults with restart 16
+ * and autotune 0 (concurrent requests would time each other's kernels; the cost model's launch
+ * shapes, or shapes tuned earlier in the process, are used). */
 void irk_default_serve_options(irk_serve_options* opt);
 
 /* Serve `count` requests with continuous batching (not in the paper: the serving form of this

@@ -55,6 +55,10 @@ extern "C" void irk_default_serve_options(irk_serve_options* o) {
   o->realtime = 1;
   irk_default_options(&o->solver);
   o->solver.restart = 16;
+  // requests run concurrently: launch-shape timings taken while other requests' kernels share
+  // the device would be noise, so served handles keep the cost model's shapes (or shapes tuned
+  // earlier in the process)
+  o->solver.autotune = 0;
 }
 
 extern "C" irk_status irk_serve(const irk_request* reqs, int count, const irk_serve_options* opt_in,

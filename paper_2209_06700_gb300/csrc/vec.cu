@@ -53,17 +53,30 @@ __device__ __forceinline__ T diag_at(const DiagParams<T>& D, int s, int dim, int
 }
 
 // ------------------------------------------------------------ Chebyshev start, diag scaling
+// One CTA per grid row (y, z) of one block: the row's K values c / diag by in-cell x position are
+// formed once in shared memory, then x = (c / D) b along the row (interior nodes only).
 template <typename T>
 __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
   const int s = blockIdx.y;
-  const int n = (int)g.n;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    int ix, iy, iz;
-    coords(e, g.dim, g.n1, ix, iy, iz);
-    if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
-    const long long o = s * g.ld + e;
-    x[o] = D.c[s] * b[o] / diag_at(D, s, g.dim, g.k, ix, iy, iz);
+  const int n1 = g.n1, r = blockIdx.x;
+  const int iy = (g.dim == 3) ? r % n1 : r, iz = (g.dim == 3) ? r / n1 : 1;
+  if (iy < 1 || iy > n1 - 2 || (g.dim == 3 && (iz < 1 || iz > n1 - 2))) return;
+  __shared__ T sc[kMaxDeg];
+  if (threadIdx.x < g.k) {
+    const int rx = threadIdx.x, ry = iy % g.k, rz = iz % g.k;
+    const T mx = D.dmr[rx], kx = D.dkr[rx], my = D.dmr[ry], ky = D.dkr[ry];
+    T d;
+    if (g.dim == 3) {
+      const T mz = D.dmr[rz], kz = D.dkr[rz];
+      d = D.cm[s] * (mx * my * mz) + D.ck[s] * (kx * my * mz + mx * ky * mz + mx * my * kz);
+    } else {
+      d = D.cm[s] * (mx * my) + D.ck[s] * (kx * my + mx * ky);
+    }
+    sc[rx] = D.c[s] / d;
   }
+  __syncthreads();
+  const long long o = s * g.ld + (long long)r * n1;
+  for (int ix = 1 + threadIdx.x; ix <= n1 - 2; ix += blockDim.x) x[o + ix] = sc[ix % g.k] * b[o + ix];
 }
 
 template <typename Tin, typename Tout>
@@ -309,6 +322,58 @@ __global__ void __launch_bounds__(kThreads) transfer_cell_kernel(const T* __rest
   }
 }
 
+// x-axis passes (the contiguous axis) by rows: one warp per grid row stages the row in shared
+// memory with coalesced loads and writes its outputs consecutively; coefficients from shared
+// memory (they differ from lane to lane).  Rows up to row_max<T>() nodes (4 KB per warp).
+template <typename T> struct RowMax { static constexpr int value = 4096 / (int)sizeof(T); };
+template <typename T, int K, bool RESTRICT>
+__global__ void __launch_bounds__(kThreads) transfer_x_rows_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                                   long long ld_in, long long ld_out, int nin,
+                                                                   int nout, int rows, int accumulate,
+                                                                   const TransferParams P) {
+  constexpr int KP = K + 1, NW = kThreads / 32;
+  __shared__ T srow[NW][RowMax<T>::value];
+  __shared__ T spc[(2 * K + 1) * KP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < (2 * K + 1) * KP; i += blockDim.x)
+    spc[i] = (sizeof(T) == 4) ? (T)P.Pcf[i] : (T)P.Pc[i];
+  __syncthreads();
+  const int s = blockIdx.y;
+  const int row = blockIdx.x * NW + w;
+  if (row >= rows) return;
+  const T* src = in + s * ld_in + (long long)row * nin;
+  T* dst = out + s * ld_out + (long long)row * nout;
+  T* f = srow[w];
+  for (int j = lane; j < nin; j += 32) f[j] = src[j];
+  __syncwarp();
+  const int Nc = P.Nc;
+  for (int o = lane; o < nout; o += 32) {
+    T acc = T(0);
+    if (RESTRICT) {  // coarse node o
+      if (o > 0 && o < nout - 1) {
+        const int cc = o / K, i = o - cc * K;
+        if (i != 0) {
+#pragma unroll
+          for (int m = 0; m <= 2 * K; ++m) acc += spc[m * KP + i] * f[2 * K * cc + m];
+        } else {
+#pragma unroll
+          for (int m = 0; m < 2 * K; ++m) acc += spc[m * KP + K] * f[2 * K * (cc - 1) + m];
+#pragma unroll
+          for (int m = 0; m <= 2 * K; ++m) acc += spc[m * KP] * f[2 * K * cc + m];
+        }
+      }
+    } else {  // fine node o
+      int cc = o / (2 * K);
+      if (cc > Nc - 1) cc = Nc - 1;
+      const int m = o - 2 * K * cc;
+#pragma unroll
+      for (int i = 0; i <= K; ++i) acc += spc[m * KP + i] * f[K * cc + i];
+    }
+    if (accumulate) dst[o] += acc;
+    else dst[o] = acc;
+  }
+}
+
 // ------------------------------------------------------------ coarse solve
 template <typename T>
 __global__ void coarse_solve_kernel(const T* __restrict__ b, T* __restrict__ x, long long ld,
@@ -367,8 +432,8 @@ __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, in
 // ============================================================ launchers
 template <typename T>
 cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, const DiagParams<T>& D, cudaStream_t st) {
-  dim3 grid(blocks_for(g.n, 2), nstage);
-  cheb_first_kernel<T><<<grid, kThreads, 0, st>>>(g, b, x, D);
+  dim3 grid(g.dim == 3 ? g.n1 * g.n1 : g.n1, nstage);
+  cheb_first_kernel<T><<<grid, 128, 0, st>>>(g, b, x, D);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_first<float>(const GridInfo&, int, const float*, float*, const DiagParams<float>&,
@@ -439,6 +504,24 @@ cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_i
   const long long nthreads = others * P.Nc;
   if (nthreads <= 0) return cudaSuccess;
   if (nthreads > INT32_MAX) return cudaErrorInvalidValue;
+  if (axis == 0 && !restrict_mode && din[0] <= RowMax<T>::value) {  // prolongation rows via shared memory
+    const int rows = dout[1] * dout[2];
+    dim3 rgrid((rows + kThreads / 32 - 1) / (kThreads / 32), nstage);
+#define IRK_TX(KK, R)                                                                                          \
+  transfer_x_rows_kernel<T, KK, R><<<rgrid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], dout[0], rows, \
+                                                                accumulate, P)
+#define IRK_TX_K(KK) \
+  if (restrict_mode) IRK_TX(KK, true); else IRK_TX(KK, false);
+    switch (P.k) {
+      case 1: IRK_TX_K(1); break;
+      case 2: IRK_TX_K(2); break;
+      case 3: IRK_TX_K(3); break;
+      default: IRK_TX_K(4); break;
+    }
+#undef IRK_TX_K
+#undef IRK_TX
+    return cudaGetLastError();
+  }
   dim3 grid(blocks_for(nthreads), nstage);
 #define IRK_TR(KK, AX, R)                                                                                  \
   transfer_cell_kernel<T, KK, AX, R><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], dout[0], \

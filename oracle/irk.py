@@ -91,15 +91,20 @@ def apply_calA(prob, u, C=None, beta=None):
     return C @ Mu + beta * Ku
 
 
-def step_direct(prob, y_n, t_n, return_stages=False):
-    """Exact step by a sparse direct solve of the Kronecker stage system (interior DoFs)."""
+def step_direct(prob, y_n, t_n, return_stages=False, stage_loads=None):
+    """Exact step by a sparse direct solve of the Kronecker stage system (interior DoFs).
+
+    stage_loads: optional (Q, n) array g(t_n + c_i tau) replacing the built-in source."""
     mesh = prob.mesh
     M, K = assemble(mesh)
     MI, keep = interior_restrict(mesh, M)
     KI, _ = interior_restrict(mesh, K)
     Q, tau = prob.Q, prob.tau
     big = sp.kron(sp.identity(Q), MI) + tau * sp.kron(sp.csr_matrix(prob.A), KI)
-    rhs = prob.stage_rhs_kron(y_n, t_n)[:, keep].reshape(-1)
+    if stage_loads is None:
+        rhs = prob.stage_rhs_kron(y_n, t_n)[:, keep].reshape(-1)
+    else:
+        rhs = (np.asarray(stage_loads) - prob.apply_K(y_n)[None, :])[:, keep].reshape(-1)
     kk = spla.spsolve(big.tocsc(), rhs).reshape(Q, -1)
     y1 = y_n.copy()
     y1[keep] = y_n[keep] + tau * (prob.b @ kk)
@@ -158,15 +163,20 @@ class FastDiag:
         return out
 
 
-def step_fastdiag(prob, y_n, t_n, fd=None):
-    """Exact IRK step per mode: (I + tau mu A) khat = phi(t_n + c tau) Ghat - mu yhat 1."""
+def step_fastdiag(prob, y_n, t_n, fd=None, stage_loads=None):
+    """Exact IRK step per mode: (I + tau mu A) khat = ghat_i - mu yhat 1, ghat_i the modal stage loads
+    (phi(t_n + c_i tau) Ghat for the built-in source, or the given (Q, n) stage_loads)."""
     fd = FastDiag(prob) if fd is None else fd
     Q, tau = prob.Q, prob.tau
     yhat = fd.to_modal_state(y_n).reshape(-1)
-    Ghat = fd.to_modal_load(prob.G).reshape(-1)
     mu = fd.mu.reshape(-1)
-    phis = np.array([phi_time(prob.d, t_n + ci * tau) for ci in prob.c])
-    rhs = phis[None, :] * Ghat[:, None] - (mu * yhat)[:, None]          # (nmodes, Q)
+    if stage_loads is None:
+        Ghat = fd.to_modal_load(prob.G).reshape(-1)
+        phis = np.array([phi_time(prob.d, t_n + ci * tau) for ci in prob.c])
+        ghat = phis[None, :] * Ghat[:, None]                             # (nmodes, Q)
+    else:
+        ghat = np.stack([fd.to_modal_load(g).reshape(-1) for g in np.asarray(stage_loads)], axis=1)
+    rhs = ghat - (mu * yhat)[:, None]                                    # (nmodes, Q)
     mats = np.eye(Q)[None, :, :] + tau * mu[:, None, None] * prob.A[None, :, :]
     khat = np.linalg.solve(mats, rhs[:, :, None])[:, :, 0]
     y1hat = yhat + tau * khat @ prob.b

@@ -79,6 +79,9 @@ typedef struct {
   int autotune;       /* 1: time the 3D operator kernels' launch shapes (tile width, z chunk,
                          cluster) at create on the handle's own buffers and keep the fastest,
                          process-wide per kernel and size (default 1); 0: cost model only */
+  int pair_precond;   /* DIAG variant, 2x2 pair blocks: 0 PRESB (Eq. presb:p, two V-cycles on
+                         (alpha+beta) M + tau K, default); 1 one V-cycle on the coupled 2x2 system
+                         itself (Sec. 6, GMG applied directly to Eq. complex:twobytwo) */
 } irk_options;
 
 typedef struct {

@@ -27,7 +27,8 @@ class IrkOptions(ctypes.Structure):
                 ("cheb_degree", ctypes.c_int), ("variant", ctypes.c_int), ("mg_precision", ctypes.c_int),
                 ("batched", ctypes.c_int), ("use_graph", ctypes.c_int), ("eig_steps", ctypes.c_int),
                 ("smoothing_range", ctypes.c_double), ("eig_safety", ctypes.c_double),
-                ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("pair_precond", ctypes.c_int)]
 
 
 class IrkRequest(ctypes.Structure):

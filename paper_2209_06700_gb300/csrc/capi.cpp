@@ -250,6 +250,19 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
         IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
         return from_mg<S>(h, mg, out, 1.0, nullptr, 0.0);
       };
+    } else if (h->opt.pair_precond == 1) {
+      op = [h, al, be, tau](const S* in, S* out) {
+        const double Cm[4] = {al, -be, be, al}, Ck[4] = {tau, 0.0, 0.0, tau};
+        return apply_general<S>(h, in, out, 2, Cm, Ck);
+      };
+      // one V-cycle on the coupled system [[alpha M + tau K, -beta M], [beta M, alpha M + tau K]]
+      prec = [h, mg](const S* in, S* out) {
+        const double I2[4] = {1.0, 0.0, 0.0, 1.0};
+        const CombineParams C = combine_params(2, 2, I2);
+        IRK_TRY(to_mg_combine<S>(h, mg, in, nullptr, C));
+        IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
+        return from_mg_combine<S>(h, mg, out, nullptr, C);
+      };
     } else {
       op = [h, al, be, tau](const S* in, S* out) {
         const double Cm[4] = {al, -be, be, al}, Ck[4] = {tau, 0.0, 0.0, tau};
@@ -278,7 +291,7 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
     IRK_TRY(fgmres_solve<S>(w, op, prec, bvec, xvec, h->opt.rtol, h->opt.max_it, h->st, res));
     iters += res.iterations;
     reo += res.reorth;
-    vc += res.iterations * (blk.pair ? 2 : 1);
+    vc += res.iterations * ((blk.pair && h->opt.pair_precond == 0) ? 2 : 1);
     worst = std::max(worst, res.rel_residual);
     if (!res.converged) {
       if (stats) { stats->iterations = iters; stats->vcycles = vc; stats->rel_residual = worst; stats->reorth_passes = reo; }
@@ -355,7 +368,8 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   const irk_options& o = h->opt;
   if (!(o.rtol > 0) || o.max_it < 1 || o.restart < 1 || o.restart > 60 || o.cheb_degree < 1 || o.cheb_degree > 16 ||
       (o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
-      o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1))
+      o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1) ||
+      (o.pair_precond != 0 && o.pair_precond != 1))
     return Status::Err(IRK_EINVAL, "invalid options");
   if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
   h->dim = mesh->dim;
@@ -442,6 +456,12 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
       md.nb = 1;
       md.shared_cheb = 0;
       md.cm = {blk.pair ? blk.alpha + blk.beta : blk.alpha};
+      if (blk.pair && o.pair_precond == 1) {  // one V-cycle on the coupled 2x2 block
+        md.nb = 2;
+        md.batched = 1;
+        md.cm = {blk.alpha, blk.alpha};
+        md.coupled_beta = blk.beta;
+      }
       std::unique_ptr<MGBase> m;
       IRK_TRY(make_mg(md, h->el, h->arena, h->st, m));
       h->mg_diag.push_back(std::move(m));
@@ -499,6 +519,7 @@ void irk_default_options(irk_options* o) {
   o->shared_cheb = 0;
   o->op_ff = 1;
   o->autotune = 1;
+  o->pair_precond = 0;
 }
 
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,

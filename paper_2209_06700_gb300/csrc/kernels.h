@@ -228,6 +228,7 @@ struct FdParams {
   int ni;                   // interior nodes per axis
   double tau;
   double cm[kMaxStages];
+  double beta;              // coupled 2x2 systems (launch_fd_scale_coupled): coupling coefficient
 };
 // out = transform of `in` along `axis` on the interior grid: out[..i..] = sum_j Mt[i][j] in[..j..]
 template <typename Tin, typename Tout>
@@ -236,6 +237,26 @@ cudaError_t launch_fd_axis(const Tin* in, Tout* out, int nstage, long long ld, i
 // t[interior] *= 1 / (cm_s + tau (mu_a + mu_b (+ mu_c)))
 cudaError_t launch_fd_scale(double* t, int nstage, long long ld, int n1, int dim, const double* mu,
                             const FdParams& P, cudaStream_t st);
+// The coupled 2x2 system [[A, -beta M], [beta M, A]], A = cm[0] M + tau K, in modal coordinates:
+// per mode (t0, t1) <- [[a, -beta], [beta, a]]^{-1} (t0, t1), a = cm[0] + tau mu; t0 at t, t1 at t + ld.
+cudaError_t launch_fd_scale_coupled(double* t, long long ld, int n1, int dim, const double* mu, const FdParams& P,
+                                    cudaStream_t st);
+
+// Level operator of the coupled 2x2 system [[A, -beta M], [beta M, A]] (A = cm M + ck K; a 2x2
+// block of Eq. complex:twobytwo) from the products M x_s, K x_s of its two components (s = 0, 1,
+// at stride ld), fused with the residual or the Chebyshev step around point-Jacobi, the point
+// being a node with its two components: D2 = [[d, -beta m], [beta m, d]], d = diag(A), m = diag(M):
+//   cheb = 0: out = b - A2 x
+//   cheb = 1: out = x + c1 (x - xold) + c2 D2^{-1} (b - A2 x), xold read from out (zero when xold_zero)
+//   cheb = 2: out = c2 D2^{-1} b (first step from x = 0; mx, kx, x unused).  Interior nodes only.
+struct CoupledParams {
+  double cm, ck, beta, c1, c2;
+  double dmr[kMaxDeg], dkr[kMaxDeg];
+  int cheb, xold_zero;
+};
+template <typename T>
+cudaError_t launch_coupled_update(const GridInfo& g, const T* mx, const T* kx, const T* x, const T* b, T* out,
+                                  const CoupledParams& C, cudaStream_t st);
 
 // Dense coarse solve per stage: x[map] = Ainv_s b[map] (FP64 inverse), zero elsewhere untouched.
 template <typename T>

@@ -235,6 +235,7 @@ class MG final : public MGBase {
   struct Lvl {
     LevelGeom g;
     T *b = nullptr, *xa = nullptr, *xb = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
+    T *mx = nullptr, *kx = nullptr;  // coupled mode: M x and K x of both components
     long long ld1 = 0, ld2 = 0;   // strides of t1, t2
     T* cur = nullptr;             // buffer holding the level's current iterate
     std::vector<double> lo, hi;   // Chebyshev interval per block
@@ -243,8 +244,14 @@ class MG final : public MGBase {
 
   MG(const MGConfig& c, const Element1D& e, DeviceArena& a) : cfg_(c), el_(e), arena_(a) {}
 
+  // Coupled mode: the two blocks are the components of [[A, -beta M], [beta M, A]] (a 2x2 block of
+  // the real form of Eq. irk:Ainv, Sec. 6) and one V-cycle acts on the coupled system.
+  bool coupled() const { return cfg_.coupled_beta != 0.0; }
+
   Status setup(cudaStream_t st) {
     st_ = st;
+    if (coupled() && (cfg_.nb != 2 || !cfg_.batched || cfg_.cm.size() != 2 || cfg_.cm[0] != cfg_.cm[1]))
+      return Status::Err(IRK_EINVAL, "coupled multigrid needs two batched components with one mass coefficient");
     // level sizes: N, N/2, ... while even and the coarse mesh keeps an interior node
     std::vector<int> sizes{cfg_.N};
     const int nmin = (cfg_.k == 1) ? 2 : 1;
@@ -259,6 +266,10 @@ class MG final : public MGBase {
       IRK_TRY(arena_.alloc((void**)&L.xa, vb));
       IRK_TRY(arena_.alloc((void**)&L.xb, vb));
       IRK_TRY(arena_.alloc((void**)&L.r, vb));
+      if (coupled()) {
+        IRK_TRY(arena_.alloc((void**)&L.mx, vb));
+        IRK_TRY(arena_.alloc((void**)&L.kx, vb));
+      }
       L.cur = L.xa;
       if (l + 1 < sizes.size()) {
         const long long nf = L.g.n1, nc = (long long)cfg_.k * sizes[l + 1] + 1;
@@ -282,7 +293,7 @@ class MG final : public MGBase {
   // Launch shapes of the level operators (Chebyshev step and residual, batched blocks), timed on
   // the levels' own buffers before they hold data (process-wide cache; see tune_op).
   Status autotune(cudaStream_t st) {
-    if (!cfg_.batched) return Status::Ok();
+    if (!cfg_.batched || coupled()) return Status::Ok();
     const int nb = cfg_.nb;
     const int last = fused_ ? lc_ : levels() - 1;
     for (int l = 0; l < last; ++l) {
@@ -391,7 +402,33 @@ class MG final : public MGBase {
     return Status::Ok();
   }
 
+  // coupled level operator: M x and K x of both components in one launch, then the pointwise
+  // coupling fused with the residual (cheb = 0) or the Chebyshev step (cheb = 1, step j; cheb = 2,
+  // the first step from zero, needs no operator)
+  Status coupled_apply(int l, const T* x, const T* b, T* out, int cheb, int j, bool xold_zero, cudaStream_t st) {
+    Lvl& L = lv_[l];
+    EpiParams<T> E;
+    std::memset(&E, 0, sizeof(E));
+    E.out = L.mx;
+    E.out2 = L.kx;
+    OpParams<T> P = make_op_params<T>(L.g, 2, cfg_.cm.data(), ck_.data());
+    if (cheb != 2)
+      IRK_LAUNCH(l == 0 ? PROF_MG_OP_FINE : PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, 2, x, P, EPI_DUAL, E, st));
+    CoupledParams C;
+    std::memset(&C, 0, sizeof(C));
+    C.cm = cfg_.cm[0];
+    C.ck = cfg_.tau;
+    C.beta = cfg_.coupled_beta;
+    C.cheb = cheb;
+    C.xold_zero = xold_zero ? 1 : 0;
+    if (cheb) { C.c1 = L.c1[j][0]; C.c2 = L.c2[j][0]; }
+    for (int r = 0; r < kMaxDeg; ++r) { C.dmr[r] = L.g.dmr[r]; C.dkr[r] = L.g.dkr[r]; }
+    IRK_LAUNCH(PROF_MG_POINT, launch_coupled_update<T>(L.g.grid(), L.mx, L.kx, x, b, out, C, st));
+    return Status::Ok();
+  }
+
   Status residual(int l, const void* b, const void* x, void* r, cudaStream_t st) override {
+    if (coupled()) return coupled_apply(l, (const T*)x, (const T*)b, (T*)r, 0, 0, false, st);
     Lvl& L = lv_[l];
     EpiParams<T> E;
     std::memset(&E, 0, sizeof(E));
@@ -478,7 +515,10 @@ class MG final : public MGBase {
       IRK_LAUNCH(PROF_COARSE, launch_fd_axis<double, double>(t[cur], t[1 - cur], nb, g.ld, n1, dim, a, fd_Vt_, ni, st));
       cur = 1 - cur;
     }
-    IRK_LAUNCH(PROF_COARSE, launch_fd_scale(t[cur], nb, g.ld, n1, dim, fd_mu_, fd_params_, st));
+    if (coupled())
+      IRK_LAUNCH(PROF_COARSE, launch_fd_scale_coupled(t[cur], g.ld, n1, dim, fd_mu_, fd_params_, st));
+    else
+      IRK_LAUNCH(PROF_COARSE, launch_fd_scale(t[cur], nb, g.ld, n1, dim, fd_mu_, fd_params_, st));
     for (int a = 0; a + 1 < dim; ++a) {
       IRK_LAUNCH(PROF_COARSE, launch_fd_axis<double, double>(t[cur], t[1 - cur], nb, g.ld, n1, dim, a, fd_V_, ni, st));
       cur = 1 - cur;
@@ -542,10 +582,14 @@ class MG final : public MGBase {
     T* oth = (cur == L.xa) ? L.xb : L.xa;
     int j0 = 0;
     if (from_zero) {
-      std::vector<double> c(nb);
-      for (int s = 0; s < nb; ++s) c[s] = L.c2[0][s];
-      DiagParams<T> D = make_diag_params<T>(L.g, nb, cfg_.cm.data(), ck_.data(), c.data());
-      IRK_LAUNCH(PROF_MG_POINT, launch_cheb_first<T>(L.g.grid(), nb, b, cur, D, st));
+      if (coupled()) {
+        IRK_TRY(coupled_apply(l, nullptr, b, cur, 2, 0, true, st));
+      } else {
+        std::vector<double> c(nb);
+        for (int s = 0; s < nb; ++s) c[s] = L.c2[0][s];
+        DiagParams<T> D = make_diag_params<T>(L.g, nb, cfg_.cm.data(), ck_.data(), c.data());
+        IRK_LAUNCH(PROF_MG_POINT, launch_cheb_first<T>(L.g.grid(), nb, b, cur, D, st));
+      }
       j0 = 1;
     }
     for (int j = j0; j < m; ++j) {
@@ -558,7 +602,8 @@ class MG final : public MGBase {
       for (int r = 0; r < kMaxDeg; ++r) { E.dmr[r] = (T)L.g.dmr[r]; E.dkr[r] = (T)L.g.dkr[r]; }
       // x_{j-1} is zero only for the second step of a smoothing that started from zero
       E.xold_zero = (from_zero && j == 1) || j == 0;
-      IRK_TRY(op(l, cur, EPI_CHEB, E, st));
+      if (coupled()) IRK_TRY(coupled_apply(l, cur, b, oth, 1, j, E.xold_zero != 0, st));
+      else IRK_TRY(op(l, cur, EPI_CHEB, E, st));
       std::swap(cur, oth);
     }
     L.cur = cur;
@@ -571,7 +616,7 @@ class MG final : public MGBase {
     nci_ = 1;
     for (int a = 0; a < dim; ++a) nci_ *= ni;
     if (nci_ < 1) return Status::Err(IRK_EINVAL, "coarsest mesh has no interior node");
-    use_fd_ = nci_ > kDenseCoarseMax;
+    use_fd_ = nci_ > kDenseCoarseMax || coupled();  // the coupled system is solved mode by mode
     // 1D assembled interior matrices on the coarsest mesh
     const int k = cfg_.k, p = k + 1;
     std::vector<double> M1((size_t)n1 * n1, 0.0), K1((size_t)n1 * n1, 0.0);
@@ -631,7 +676,8 @@ class MG final : public MGBase {
   // launch (FP32 multigrid, batched blocks, dense coarsest solve, at least two fused levels).
   Status setup_fused() {
     fused_ = false;
-    if (sizeof(T) != 4 || !cfg_.batched || use_fd_ || cfg_.cheb_degree > kMaxChebDegree || cfg_.nb > kMaxQ)
+    if (sizeof(T) != 4 || !cfg_.batched || use_fd_ || coupled() || cfg_.cheb_degree > kMaxChebDegree ||
+        cfg_.nb > kMaxQ)
       return Status::Ok();
     int lc = levels() - 1;
     while (lc > 0 && lv_[lc - 1].g.n <= kFusedMaxNodes) --lc;
@@ -747,6 +793,7 @@ class MG final : public MGBase {
     fd_params_.ni = ni;
     fd_params_.tau = cfg_.tau;
     for (int s = 0; s < cfg_.nb && s < kMaxStages; ++s) fd_params_.cm[s] = cfg_.cm[s];
+    fd_params_.beta = cfg_.coupled_beta;
     return Status::Ok();
   }
 

@@ -1,4 +1,5 @@
-// FP32 operator launches (multigrid level operators, Chebyshev smoother, residual).
+// FP32 operator launches (multigrid level operators, Chebyshev smoother, residual, and the dual
+// products M x, K x of the coupled 2x2 level operator).
 #include "op_kernels.cuh"
 
 namespace irk {
@@ -10,6 +11,7 @@ cudaError_t launch_op<float>(int dim, int k, int nstage, const float* u, const O
                              const EpiParams<float>& E, cudaStream_t st) {
   switch (epi) {
     case EPI_STORE: return launch_op_e<float, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_DUAL: return launch_op_e<float, EPI_DUAL>(dim, k, nstage, u, P, E, st);
     case EPI_RESID: return launch_op_e<float, EPI_RESID>(dim, k, nstage, u, P, E, st);
     case EPI_CHEB: return launch_op_e<float, EPI_CHEB>(dim, k, nstage, u, P, E, st);
     default: return cudaErrorInvalidValue;
@@ -21,6 +23,7 @@ cudaError_t tune_op<float>(int dim, int k, int nstage, const float* u, const OpP
                          const EpiParams<float>& E, cudaStream_t st) {
   switch (epi) {
     case EPI_STORE: return tune_op_e<float, EPI_STORE>(dim, k, nstage, u, P, E, st);
+    case EPI_DUAL: return tune_op_e<float, EPI_DUAL>(dim, k, nstage, u, P, E, st);
     case EPI_RESID: return tune_op_e<float, EPI_RESID>(dim, k, nstage, u, P, E, st);
     case EPI_CHEB: return tune_op_e<float, EPI_CHEB>(dim, k, nstage, u, P, E, st);
     default: return cudaErrorInvalidValue;

@@ -108,6 +108,7 @@ struct MGConfig {
   int batched;
   int precision;             // 32 or 64
   int autotune = 1;          // time the level operators' launch shapes at setup
+  double coupled_beta = 0.0; // != 0: nb = 2 components of [[A, -beta M], [beta M, A]], A = cm M + tau K
 };
 
 Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,

@@ -427,6 +427,75 @@ __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, in
   }
 }
 
+__global__ void fd_scale_coupled_kernel(double* __restrict__ t, long long ld, int n1, int dim,
+                                        const double* __restrict__ mu, const FdParams P) {
+  const int ni = P.ni;
+  const int total = (dim == 3) ? ni * ni * ni : ni * ni;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int a0 = e % ni, a1 = (e / ni) % ni, a2 = (dim == 3) ? e / (ni * ni) : 0;
+    double m = mu[a0] + mu[a1];
+    int idx = (a0 + 1) + (a1 + 1) * n1;
+    if (dim == 3) { m += mu[a2]; idx += (a2 + 1) * n1 * n1; }
+    const double a = P.cm[0] + P.tau * m, bt = P.beta;
+    const double den = a * a + bt * bt;
+    const double t0 = t[idx], t1 = t[ld + idx];
+    t[idx] = (a * t0 + bt * t1) / den;
+    t[ld + idx] = (a * t1 - bt * t0) / den;
+  }
+}
+
+template <typename T>
+__global__ void coupled_update_kernel(GridInfo g, const T* __restrict__ mx, const T* __restrict__ kx,
+                                      const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ out,
+                                      const CoupledParams C) {
+  const int n = (int)g.n;
+  const T cm = (T)C.cm, ck = (T)C.ck, beta = (T)C.beta, c1 = (T)C.c1, c2 = (T)C.c2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(e, g.dim, g.n1, ix, iy, iz);
+    if (!interior(g.dim, g.n1, ix, iy, iz)) continue;
+    const long long o0 = e, o1 = g.ld + e;
+    T r0, r1;
+    if (C.cheb == 2) {  // first step from x = 0: the residual is b
+      r0 = b[o0];
+      r1 = b[o1];
+    } else {
+      const T m0 = mx[o0], m1 = mx[o1];
+      const T a0 = cm * m0 + ck * kx[o0] - beta * m1;
+      const T a1 = cm * m1 + ck * kx[o1] + beta * m0;
+      r0 = b[o0] - a0;
+      r1 = b[o1] - a1;
+    }
+    if (C.cheb == 0) {
+      out[o0] = r0;
+      out[o1] = r1;
+      continue;
+    }
+    // nodal 2x2 block of the coupled system: [[d, -beta m], [beta m, d]], d = diag(A), m = diag(M)
+    const int rx = ix % g.k, ry = iy % g.k, rz = iz % g.k;
+    double md, kd;
+    if (g.dim == 3) {
+      md = C.dmr[rx] * C.dmr[ry] * C.dmr[rz];
+      kd = C.dkr[rx] * C.dmr[ry] * C.dmr[rz] + C.dmr[rx] * C.dkr[ry] * C.dmr[rz] + C.dmr[rx] * C.dmr[ry] * C.dkr[rz];
+    } else {
+      md = C.dmr[rx] * C.dmr[ry];
+      kd = C.dkr[rx] * C.dmr[ry] + C.dmr[rx] * C.dkr[ry];
+    }
+    const T d = (T)(C.cm * md + C.ck * kd), bm = (T)(C.beta * md);
+    const T den = d * d + bm * bm;
+    const T z0 = (d * r0 + bm * r1) / den, z1 = (d * r1 - bm * r0) / den;
+    if (C.cheb == 2) {
+      out[o0] = c2 * z0;
+      out[o1] = c2 * z1;
+      continue;
+    }
+    const T x0 = x[o0], x1 = x[o1];
+    const T p0 = C.xold_zero ? T(0) : out[o0], p1 = C.xold_zero ? T(0) : out[o1];
+    out[o0] = x0 + c1 * (x0 - p0) + c2 * z0;
+    out[o1] = x1 + c1 * (x1 - p1) + c2 * z1;
+  }
+}
+
 }  // namespace
 
 // ============================================================ launchers
@@ -592,5 +661,23 @@ template cudaError_t launch_coarse_solve<float>(const float*, float*, int, long 
                                                 cudaStream_t);
 template cudaError_t launch_coarse_solve<double>(const double*, double*, int, long long, const double*, const int*, int,
                                                  cudaStream_t);
+
+cudaError_t launch_fd_scale_coupled(double* t, long long ld, int n1, int dim, const double* mu, const FdParams& P,
+                                    cudaStream_t st) {
+  const long long total = (dim == 3) ? (long long)P.ni * P.ni * P.ni : (long long)P.ni * P.ni;
+  fd_scale_coupled_kernel<<<blocks_for(total), kThreads, 0, st>>>(t, ld, n1, dim, mu, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coupled_update(const GridInfo& g, const T* mx, const T* kx, const T* x, const T* b, T* out,
+                                  const CoupledParams& C, cudaStream_t st) {
+  coupled_update_kernel<T><<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, mx, kx, x, b, out, C);
+  return cudaGetLastError();
+}
+template cudaError_t launch_coupled_update<float>(const GridInfo&, const float*, const float*, const float*,
+                                                  const float*, float*, const CoupledParams&, cudaStream_t);
+template cudaError_t launch_coupled_update<double>(const GridInfo&, const double*, const double*, const double*,
+                                                   const double*, double*, const CoupledParams&, cudaStream_t);
 
 }  // namespace irk

@@ -109,6 +109,16 @@ def test_step_diag_presb(dim, N, k, Q, tau, prec):
     assert err <= YTOL, (err, its)
 
 
+@pytest.mark.parametrize("dim,N,k,Q,tau", [(3, 8, 2, 2, 1e-3), (3, 8, 2, 3, 1e-3), (2, 16, 3, 4, 1e-2),
+                                           (3, 6, 3, 5, 1e-3)])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_step_diag_coupled_gmg(dim, N, k, Q, tau, prec):
+    """DIAG variant with one V-cycle on each coupled 2x2 block instead of PRESB (Sec. 6)."""
+    err, its = _run(dim, N, k, Q, tau, nsteps=2, variant=pkg.IRK_VARIANT_DIAG, mg_precision=prec, pair_precond=1)
+    assert err <= YTOL, (err, its)
+    assert max(its) < 80, its
+
+
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_step_on_a_side_stream(use_graph):
     """On a non-default stream the V-cycle is replayed from a captured CUDA graph (after one eager run)."""

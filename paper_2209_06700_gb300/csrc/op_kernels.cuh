@@ -248,6 +248,18 @@ template <int K, int CXS> struct Tile3D { static constexpr int CY = Warps3D<K>::
 // resident CTAs per SM requested from the register allocator (FP32: 3 -> 24 warps per SM)
 template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 1; };
 
+// Shared-memory layout of the 3D kernel (dynamic): two staged planes, two y-pass outputs (g, h),
+// the held bottom plane of a cluster chunk, and the 1/D table of the Chebyshev epilogue.
+template <typename T, int K, int EPI, int CXS>
+struct Op3dSmem {
+  static constexpr int CY = Tile3D<K, CXS>::CY, TY = K * CY, NT = 32 * Warps3D<K>::value;
+  static constexpr int CW = CXS + 2, SL = K * CW, HY = TY + K + 1;
+  static constexpr int SU = HY * SL, SG = TY * SL, SHOLD = (EPI == EPI_DUAL ? 2 : 1) * K * NT;
+  static constexpr int SINV = (EPI == EPI_CHEB) ? K * K * K : 1;
+  static constexpr size_t bytes =
+      (size_t)(2 * SU + 4 * SG + SHOLD) * sizeof(T) + (size_t)SINV * sizeof(typename Storage<T>::type);
+};
+
 // ---------------------------------------------------------------- 3D kernel
 template <typename T, int K, int EPI, int CXS>
 __global__ void __launch_bounds__(32 * Warps3D<K>::value, MinBlocks<T>::value)
@@ -262,10 +274,15 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   constexpr int NLD = HY * HX;
   constexpr int PF = (NLD + NT - 1) / NT;
   constexpr bool DUAL = (EPI == EPI_DUAL);
-  __shared__ T su[HY * SL];
-  __shared__ T sg[TY * SL];
-  __shared__ T sh[TY * SL];
-  __shared__ S sinvd[(EPI == EPI_CHEB) ? K * K * K : 1];  // 1/D by (x, y, z) mod k
+  using L = Op3dSmem<T, K, EPI, CXS>;
+  extern __shared__ __align__(16) unsigned char op_smem[];
+  T* const su2 = reinterpret_cast<T*>(op_smem);  // two staged planes (double buffer)
+  T* const sg2 = su2 + 2 * L::SU;                 // two y-pass outputs g
+  T* const sh2 = sg2 + 2 * L::SG;                 // two y-pass outputs h
+  T* const shold = sh2 + 2 * L::SG;               // bottom plane held for the cluster exchange
+  S* const sinvd = reinterpret_cast<S*>(shold + L::SHOLD);  // 1/D by (x, y, z) mod k
+  T* const sg = sg2;  // buffer 0 doubles as the cluster exchange area
+  T* const sh = sh2;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int N = P.N, n1 = P.n1;
@@ -281,10 +298,9 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   const int c1 = min(N, c0 + P.zc);
   const int cstart = clustered ? c0 : max(c0 - 1, 0);
   const bool hold_bottom = clustered && c0 > 0;  // bottom vertex plane waits for the lower chunk
-  __shared__ T shold[(EPI == EPI_DUAL ? 2 : 1) * K * NT];
   const long long plane = (long long)n1 * n1;
 
-  for (int i = tid; i < HY * SL; i += NT) su[i] = dev::zero<T>();  // padding slots stay zero
+  for (int i = tid; i < 2 * HY * SL; i += NT) su2[i] = dev::zero<T>();  // padding slots stay zero
   if constexpr (EPI == EPI_CHEB) {
     if (tid < K * K * K) {
       const int rx = tid % K, ry = (tid / K) % K, rz = tid / (K * K);
@@ -313,12 +329,16 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
 #pragma unroll
     for (int q = 0; q < PF; ++q) pf[q] = (goff[q] >= 0) ? dev::load<T>(base + goff[q]) : dev::zero<T>();
   };
-  auto store_plane = [&]() {
+  auto store_plane = [&](int buf) {
+    T* su = su2 + buf * L::SU;
 #pragma unroll
     for (int q = 0; q < PF; ++q)
       if (soff[q] >= 0) su[soff[q]] = pf[q];
   };
-  auto ypass = [&]() {
+  auto ypass = [&](int buf) {
+    const T* su = su2 + buf * L::SU;
+    T* sgb = sg2 + buf * L::SG;
+    T* shb = sh2 + buf * L::SG;
 #pragma unroll 1
     for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows, one at a time (warp-uniform tap row)
       const int yr = w * RPW + rr;
@@ -327,16 +347,16 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       for (int sl = lane; sl < SL; sl += 32) {
         T g = dev::zero<T>(), h = dev::zero<T>();
         dev::ytaps_dispatch<T, K>(ro, colbase + sl, SL, P, g, h);
-        sg[yr * SL + sl] = g;
-        sh[yr * SL + sl] = h;
+        sgb[yr * SL + sl] = g;
+        shb[yr * SL + sl] = h;
       }
     }
   };
   const int seg = lane / CXS, lx = lane - seg * CXS;
   const int trow = w * RPW + seg;  // this thread's node row in the tile
-  auto xpass = [&](T (&R)[K], T (&Pp)[K]) {
-    const T* g = sg + trow * SL;
-    const T* h = sh + trow * SL;
+  auto xpass = [&](int buf, T (&R)[K], T (&Pp)[K]) {
+    const T* g = sg2 + buf * L::SG + trow * SL;
+    const T* h = sh2 + buf * L::SG + trow * SL;
     T r[K + 1], p[K + 1];
     dev::xcell<T, K, true, CW>(g, h, lx + 1, P, r, p);
     T rl = dev::shfl_up(r[K]);
@@ -393,30 +413,38 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     }
   };
 
+  // Two-stage pipeline over the planes z0 .. zlast with one barrier per plane: in the interval of
+  // plane zp the y pass of zp, the x pass and z push of zp - 1, the store of zp + 1 (prefetched one
+  // plane earlier) and the load of zp + 2 run together; planes alternate between two buffers.
+  const int z0 = K * cstart, zlast = K * c1;
   __syncthreads();
-  load_plane(K * cstart);
+  load_plane(z0);
+  store_plane(0);
+  load_plane(z0 + 1);
+  __syncthreads();
+  ypass(0);
+  store_plane(1);
+  if (z0 + 2 <= zlast) load_plane(z0 + 2);
+  __syncthreads();
   for (int c = cstart; c < c1; ++c) {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
-      const int zp = K * c + r;
-      store_plane();
-      __syncthreads();
-      load_plane(zp + 1);
-      ypass();
-      __syncthreads();
+      const int zp = K * c + r + 1;  // plane of this interval's y pass; x pass and z push: zp - 1
+      const int buf = (zp - z0) & 1;
+      ypass(buf);
       T R[K], Pp[K];
-      xpass(R, Pp);
+      xpass(buf ^ 1, R, Pp);
       dev::zstep<T, K, DUAL>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
+      if (zp + 1 <= zlast) {
+        store_plane(buf ^ 1);
+        if (zp + 2 <= zlast) load_plane(zp + 2);
+      }
+      __syncthreads();
     }
   }
-  // upper vertex plane of the last cell
-  store_plane();
-  __syncthreads();
-  ypass();
-  __syncthreads();
-  {
+  {  // upper vertex plane of the last cell
     T R[K], Pp[K];
-    xpass(R, Pp);
+    xpass((zlast - z0) & 1, R, Pp);
     dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
     if (c1 - 1 >= c0) emit(c1 - 1);
   }
@@ -603,10 +631,11 @@ constexpr int kMaxClusterChunks = 16;  // z chunks per thread-block cluster (abo
 
 // Clusters of nch CTAs of this kernel that fit on the device at once (0: not launchable as a cluster).
 template <typename Kern>
-int max_active_clusters(Kern kern, int nch, int threads, dim3 grid) {
+int max_active_clusters(Kern kern, int nch, int threads, dim3 grid, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 1;
@@ -631,13 +660,29 @@ struct OpShape {
   int cxs = 32, zc = 1, cluster = 0;
 };
 
-// Per kernel instantiation: occupancy and cluster fit, queried once.
+// Per kernel instantiation: dynamic shared memory (opted in once above the 48 KB default),
+// occupancy and cluster fit, queried once.
 template <typename T, int K, int EPI, int CXS>
 struct Op3dInfo {
+  static constexpr size_t smem = Op3dSmem<T, K, EPI, CXS>::bytes;
+  static bool smem_ready() {
+    static int ok = -1;
+    if (ok < 0) {
+      ok = 1;
+      if (smem > 48 * 1024 &&
+          cudaFuncSetAttribute(op3d_kernel<T, K, EPI, CXS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        ok = 0;
+      }
+    }
+    return ok == 1;
+  }
   static int occ() {
     static int o = 0;
     if (o == 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, op3d_kernel<T, K, EPI, CXS>, 32 * Warps3D<K>::value, 0);
+      smem_ready();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, op3d_kernel<T, K, EPI, CXS>, 32 * Warps3D<K>::value, smem);
       if (o < 1) o = 1;
     }
     return o;
@@ -647,7 +692,10 @@ struct Op3dInfo {
     static int fit[kMaxClusterChunks + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1,
                                              -1, -1, -1, -1, -1, -1, -1, -1};
     if (nch < 2 || nch > kMaxClusterChunks) return 0;
-    if (fit[nch] < 0) fit[nch] = max_active_clusters(op3d_kernel<T, K, EPI, CXS>, nch, 32 * Warps3D<K>::value, grid);
+    if (fit[nch] < 0) {
+      smem_ready();
+      fit[nch] = max_active_clusters(op3d_kernel<T, K, EPI, CXS>, nch, 32 * Warps3D<K>::value, grid, smem);
+    }
     return fit[nch];
   }
 };
@@ -681,8 +729,10 @@ OpShape model_shape(int N, int nstage) {
 template <typename T, int K, int EPI, int CXS>
 cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
                          const EpiParams<typename Storage<T>::type>& E, cudaStream_t st, const OpShape& sh) {
+  using I = Op3dInfo<T, K, EPI, CXS>;
   auto kern = op3d_kernel<T, K, EPI, CXS>;
   const int threads = 32 * Warps3D<K>::value;
+  if (!I::smem_ready()) return cudaErrorInvalidValue;
   OpParams<T> Q = P;
   const int ntx = (P.N + CXS - 1) / CXS;
   Q.ntile_y = (P.N + Tile3D<K, CXS>::CY - 1) / Tile3D<K, CXS>::CY;
@@ -691,12 +741,13 @@ cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const O
   Q.cluster = sh.cluster;
   dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
   if (!Q.cluster) {
-    kern<<<grid, threads, 0, st>>>(u, Q, E);
+    kern<<<grid, threads, I::smem, st>>>(u, Q, E);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = I::smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

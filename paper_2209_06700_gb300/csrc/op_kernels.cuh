@@ -242,17 +242,23 @@ __device__ __forceinline__ void zstep(int r, int c, int cstart, int c0, const Op
 
 // Tile of a 3D CTA: CXS cells in x per warp segment (32, or 16 / 8 on meshes with fewer cells, so
 // that no lane idles), 32 / CXS node rows per warp, K * CY node rows in y; the thread count is the
-// same for every CXS.
-template <int K> struct Warps3D { static constexpr int value = K * ((K == 1) ? 8 : (K == 2) ? 4 : 2); };
-template <int K, int CXS> struct Tile3D { static constexpr int CY = Warps3D<K>::value * (32 / CXS) / K; };
+// same for every CXS.  FP32 CTAs hold 8 warps (K = 3: 6) and run 3 per SM; the FP64-accurate
+// kernels, limited to one 8-warp CTA per SM by their register use, use CTAs of half the rows so
+// that two of them share an SM and one computes while the other waits at its barrier.
+template <typename T, int K> struct Warps3D {
+  static constexpr int value = K * ((K == 1) ? 8 : (K == 2) ? 4 : 2) / (sizeof(T) == 4 ? 1 : 2);
+};
+template <typename T, int K, int CXS> struct Tile3D {
+  static constexpr int CY = Warps3D<T, K>::value * (32 / CXS) / K;
+};
 // resident CTAs per SM requested from the register allocator (FP32: 3 -> 24 warps per SM)
-template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 1; };
+template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 2; };
 
 // Shared-memory layout of the 3D kernel (dynamic): two staged planes, two y-pass outputs (g, h),
 // the held bottom plane of a cluster chunk, and the 1/D table of the Chebyshev epilogue.
 template <typename T, int K, int EPI, int CXS>
 struct Op3dSmem {
-  static constexpr int CY = Tile3D<K, CXS>::CY, TY = K * CY, NT = 32 * Warps3D<K>::value;
+  static constexpr int CY = Tile3D<T, K, CXS>::CY, TY = K * CY, NT = 32 * Warps3D<T, K>::value;
   static constexpr int CW = CXS + 2, SL = K * CW, HY = TY + K + 1;
   static constexpr int SU = HY * SL, SG = TY * SL, SHOLD = (EPI == EPI_DUAL ? 2 : 1) * K * NT;
   static constexpr int SINV = (EPI == EPI_CHEB) ? K * K * K : 1;
@@ -262,13 +268,13 @@ struct Op3dSmem {
 
 // ---------------------------------------------------------------- 3D kernel
 template <typename T, int K, int EPI, int CXS>
-__global__ void __launch_bounds__(32 * Warps3D<K>::value, MinBlocks<T>::value)
+__global__ void __launch_bounds__(32 * Warps3D<T, K>::value, MinBlocks<T>::value)
 op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
             const EpiParams<typename Storage<T>::type> E) {
   using S = typename Storage<T>::type;
   constexpr int RPW = 32 / CXS;  // node rows per warp
-  constexpr int CY = Tile3D<K, CXS>::CY;
-  constexpr int CX = CXS, TY = K * CY, NT = 32 * Warps3D<K>::value;
+  constexpr int CY = Tile3D<T, K, CXS>::CY;
+  constexpr int CX = CXS, TY = K * CY, NT = 32 * Warps3D<T, K>::value;
   constexpr int CW = CX + 2, SL = K * CW;
   constexpr int HY = TY + K + 1, HX = K * CX + K + 1;
   constexpr int NLD = HY * HX;
@@ -682,7 +688,7 @@ struct Op3dInfo {
     static int o = 0;
     if (o == 0) {
       smem_ready();
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, op3d_kernel<T, K, EPI, CXS>, 32 * Warps3D<K>::value, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, op3d_kernel<T, K, EPI, CXS>, 32 * Warps3D<T, K>::value, smem);
       if (o < 1) o = 1;
     }
     return o;
@@ -694,7 +700,7 @@ struct Op3dInfo {
     if (nch < 2 || nch > kMaxClusterChunks) return 0;
     if (fit[nch] < 0) {
       smem_ready();
-      fit[nch] = max_active_clusters(op3d_kernel<T, K, EPI, CXS>, nch, 32 * Warps3D<K>::value, grid, smem);
+      fit[nch] = max_active_clusters(op3d_kernel<T, K, EPI, CXS>, nch, 32 * Warps3D<T, K>::value, grid, smem);
     }
     return fit[nch];
   }
@@ -705,7 +711,7 @@ struct Op3dInfo {
 template <typename T, int K, int EPI, int CXS>
 OpShape model_shape(int N, int nstage) {
   using I = Op3dInfo<T, K, EPI, CXS>;
-  const int ntx = (N + CXS - 1) / CXS, nty = (N + Tile3D<K, CXS>::CY - 1) / Tile3D<K, CXS>::CY;
+  const int ntx = (N + CXS - 1) / CXS, nty = (N + Tile3D<T, K, CXS>::CY - 1) / Tile3D<T, K, CXS>::CY;
   const long long base = (long long)ntx * nty * nstage;
   const long long slots = (long long)I::occ() * device_sm_count();
   OpShape best;
@@ -731,11 +737,11 @@ cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const O
                          const EpiParams<typename Storage<T>::type>& E, cudaStream_t st, const OpShape& sh) {
   using I = Op3dInfo<T, K, EPI, CXS>;
   auto kern = op3d_kernel<T, K, EPI, CXS>;
-  const int threads = 32 * Warps3D<K>::value;
+  const int threads = 32 * Warps3D<T, K>::value;
   if (!I::smem_ready()) return cudaErrorInvalidValue;
   OpParams<T> Q = P;
   const int ntx = (P.N + CXS - 1) / CXS;
-  Q.ntile_y = (P.N + Tile3D<K, CXS>::CY - 1) / Tile3D<K, CXS>::CY;
+  Q.ntile_y = (P.N + Tile3D<T, K, CXS>::CY - 1) / Tile3D<T, K, CXS>::CY;
   Q.zc = sh.zc;
   Q.nch = (P.N + Q.zc - 1) / Q.zc;
   Q.cluster = sh.cluster;
@@ -875,7 +881,7 @@ cudaError_t tune_op_k(int dim, int nstage, const typename Storage<T>::type* u, c
   std::vector<OpShape> ok;
   for (const OpShape& c : cands) {
     if (c.cluster) {
-      const int cy = (c.cxs == 8) ? Tile3D<K, 8>::CY : (c.cxs == 16) ? Tile3D<K, 16>::CY : Tile3D<K, 32>::CY;
+      const int cy = (c.cxs == 8) ? Tile3D<T, K, 8>::CY : (c.cxs == 16) ? Tile3D<T, K, 16>::CY : Tile3D<T, K, 32>::CY;
       const int nch = (P.N + c.zc - 1) / c.zc;
       const dim3 grid((P.N + c.cxs - 1) / c.cxs, ((P.N + cy - 1) / cy) * nch, nstage);
       int fit = 0;

@@ -204,6 +204,45 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def other_workloads(steps=3):
+    """The remaining configurations, each timed like the headline one (CUDA events on the solver's
+    stream after one warm-up step, inputs resident): the 64^3 degree-3 problem for Q = 2..5, and the
+    48^3 degree-2 Q=3 problem in the LU and directly diagonalised variants."""
+    import torch
+    import paper_2209_06700_gb300 as pkg
+    cases = [(heat3d_k3_n64(Q), "lu") for Q in (2, 3, 4, 5)]
+    cases += [(HEAT3D_K2_N48_Q3, "lu"), (HEAT3D_K2_N48_Q3, "diag"), (HEAT3D_K2_N48_Q3, "diag-gmg2x2")]
+    out = {}
+    for w, var in cases:
+        stream = torch.cuda.Stream()
+        opts = dict(cheb_degree=w.cheb_degree)
+        if var != "lu":
+            opts["variant"] = pkg.IRK_VARIANT_DIAG
+        if var == "diag-gmg2x2":
+            opts["pair_precond"] = 1
+        s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, **opts)
+        try:
+            y = s.vector()
+            with torch.cuda.stream(stream):
+                s.interpolate_initial(y, 0.0)
+            s.step(y, 0.0)
+            its = []
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(steps):
+                its.append(s.step(y, (i + 1) * w.tau).iterations)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+        finally:
+            s.close()
+        units = w.Q * w.n_interior
+        out[f"{w.name}_{var}"] = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                                  "fgmres_iterations": sum(its) / len(its), "stage_dofs": units}
+    return out
+
+
 def fp64_per_stage_baseline(w, cheb, units, steps=3):
     """The same step on the plain GPU path: native FP64 operator, FP64 V-cycle, one launch per
     stage, no graph replay.  Timed with CUDA events on its stream after one warm-up step."""
@@ -248,6 +287,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-fp64-baseline", action="store_true", help="skip the per-stage FP64 GPU step baseline")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the 64^3 degree-3 and 48^3 degree-2 configurations")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -442,6 +483,8 @@ def main():
                 "clocks": clk}
         if world == 1 and not args.no_fp64_baseline:
             line["gpu_fp64_per_stage_baseline"] = fp64_per_stage_baseline(w, cheb, units)
+        if world == 1 and not args.no_other_workloads:
+            line["other_workloads"] = other_workloads()
         if world == 1 and not args.no_serve:
             line["serving"] = serving_measure(args.serve_requests)
             # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)

@@ -5,9 +5,9 @@
 // V-cycle per block) is not a fixed linear map in floating point.
 // Classical Gram-Schmidt with a conditional second pass (Kahan-Parlett "twice
 // is enough", decided on the device by the reduction that finishes |w'|^2);
-// the dot products are deterministic device reductions and the
-// Hessenberg/Givens update runs on the host with one device->host transfer per
-// iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
+// the dot products are deterministic device reductions, finished inside each
+// Gram-Schmidt kernel by its last block, and the Hessenberg/Givens update runs
+// on the host with one device->host transfer per iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -58,6 +58,8 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
   IRK_TRY(arena.alloc((void**)&w.partial, (size_t)66 * w.nb * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.dvals, 256 * sizeof(double)));
   IRK_TRY(arena.alloc((void**)&w.fvals, 256 * sizeof(ff)));
+  IRK_TRY(arena.alloc((void**)&w.count, 64 * sizeof(unsigned)));
+  IRK_CUDA(cudaMemsetAsync(w.count, 0, 64 * sizeof(unsigned), stream));
   if (!w.hvals) {
     w.hvals = pinned_block_acquire();
     if (!w.hvals) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
@@ -101,8 +103,12 @@ template <> Status upload_y<ff>(FGMRESWork& w, const std::vector<double>& y, int
 
 template <typename S>
 Status norm(FGMRESWork& w, const S* v, cudaStream_t st, double& out) {
-  IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial<S>(v, w.len, w.partial, w.nb, st));
-  IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1));
+  int nb = w.nb;
+  RowSink R;
+  R.out = w.dvals + kNrm;
+  R.count = w.count;
+  R.take_sqrt = 1;
+  IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial<S>(v, w.len, w.partial, nb, R, st));
   IRK_CUDA(cudaMemcpyAsync(w.hvals + kNrm, w.dvals + kNrm, sizeof(double), cudaMemcpyDeviceToHost, st));
   IRK_CUDA(cudaStreamSynchronize(st));
   out = w.hvals[kNrm];
@@ -122,6 +128,7 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
   S* tmp = reinterpret_cast<S*>(w.tmp);
   typename Coef<S>::type* cf = coefs<S>(w);
   IRK_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(S), st));
+  IRK_CUDA(cudaMemsetAsync(w.count, 0, sizeof(unsigned), st));  // in case a failed launch left it
   double bnorm;
   IRK_TRY(norm<S>(w, b, st, bnorm));
   if (!std::isfinite(bnorm)) return Status::Err(IRK_ENUMERIC, "non-finite right-hand side");
@@ -145,26 +152,36 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
       IRK_TRY(op(Zj, wv));
       // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
       const int nv = j + 1;
-      ReduceExtra x1;
-      x1.out_ff = w.fvals + kH1;
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH1, st, 0, &x1));
-      // dvals[kH1 + nv] = |w|^2, copied aside before pass 2 overwrites row nv
-      IRK_CUDA(cudaMemcpyAsync(w.dvals + kN0, w.dvals + kH1 + nv, sizeof(double), cudaMemcpyDeviceToDevice, st));
-      ReduceExtra x2;
-      x2.out_ff = w.fvals + kH2;
-      x2.decide_flag = w.dvals + kRedo;  // second pass when |w'|^2 < eta^2 |w|^2
-      x2.decide_ref = w.dvals + kN0;
-      x2.decide_row = nv;
-      x2.eta2 = kEta * kEta;
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, w.nb, st));
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, nv + 1, w.nb, w.dvals + kH2, st, 0, &x2));
+      // pass 1: h1 = V^T w and |w|^2 (row nv, kept aside in kN0 before pass 2 overwrites row nv)
+      RowSink r1;
+      r1.out = w.dvals + kH1;
+      r1.count = w.count;
+      r1.X.out_ff = w.fvals + kH1;
+      r1.X.copy_out = w.dvals + kN0;
+      r1.X.copy_row = nv;
+      int nb = w.nb;  // row capacity of w.partial in, blocks used out
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, nb, r1, st));
+      // w' = w - V h1, h2 = V^T w', |w'|^2; second pass when |w'|^2 < eta^2 |w|^2
+      RowSink r2;
+      r2.out = w.dvals + kH2;
+      r2.count = w.count;
+      r2.X.out_ff = w.fvals + kH2;
+      r2.X.decide_flag = w.dvals + kRedo;
+      r2.X.decide_ref = w.dvals + kN0;
+      r2.X.decide_row = nv;
+      r2.X.eta2 = kEta * kEta;
+      nb = w.nb;
+      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, nb, r2, st));
+      // w'' = w' - V h2 (if decided), |w''| and 1 / |w''|
+      RowSink r3;
+      r3.out = w.dvals + kNrm;
+      r3.count = w.count;
+      r3.take_sqrt = 1;
+      r3.X.inv = w.dvals + kInv;
+      r3.X.inv_ff = w.fvals + kInv;
+      nb = w.nb;
       IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, tmp, wv, len, w.partial,
-                                                  w.nb, st));
-      ReduceExtra x3;
-      x3.inv = w.dvals + kInv;
-      x3.inv_ff = w.fvals + kInv;
-      IRK_LAUNCH(PROF_KRYLOV, launch_reduce_partials(w.partial, 1, w.nb, w.dvals + kNrm, st, 1, &x3));
+                                                  nb, r3, st));
       IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       IRK_CUDA(cudaStreamSynchronize(st));
       const double hn = w.hvals[kNrm];

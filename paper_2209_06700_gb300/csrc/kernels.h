@@ -163,12 +163,25 @@ struct ReduceExtra {
   const double* decide_ref = nullptr;
   int decide_row = -1;
   double eta2 = 0.0;
+  double* copy_out = nullptr;         // copy_out[0] = the result of row copy_row
+  int copy_row = -1;
+};
+// Rows finished inside the kernel that produced their partials: every block adds its partials,
+// and the block that arrives last on *count sums each row over the blocks in a fixed order, writes
+// out[i] (sqrt with take_sqrt) and the extras, and resets *count to 0.
+struct RowSink {
+  double* out = nullptr;
+  unsigned* count = nullptr;
+  int take_sqrt = 0;
+  ReduceExtra X;
 };
 // out[i] = sum_b partial[i][b] (fixed order); with take_sqrt, out[i] = sqrt(sum)
 cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double* out, cudaStream_t st,
                                    int take_sqrt = 0, const ReduceExtra* extra = nullptr);
 // Vector work of FGMRES on stage vectors of type S (double or ff); reductions produce FP64
-// partial sums per block (rows of nb).
+// partial sums per block (rows of nb), finished by the kernel's last block into the RowSink.  nb is
+// in-out: at most nb blocks (the row capacity of partial), the blocks used (one full wave of the
+// kernel) on return.
 //  norm2_partial: partial[0] = |w|^2
 //  multi_axpy   : w += sign sum_i h[i] V_i          (h on the device, Coef<S>)
 //  scale_dev    : out = inv[0] w                    (inv on the device, Coef<S>; out may alias w)
@@ -179,7 +192,8 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
 //                 Gram-Schmidt, "twice is enough" of Kahan and Parlett), else w_out = w_in;
 //                 partial[0] = |w_out|^2
 template <typename S>
-cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int nb, cudaStream_t st);
+cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int& nb, const RowSink& R,
+                                 cudaStream_t st);
 template <typename S>
 cudaError_t launch_multi_axpy(const S* V, long long vstride, int nv, const typename Coef<S>::type* h, double sign,
                               S* w, long long n, cudaStream_t st);
@@ -188,15 +202,16 @@ cudaError_t launch_scale_dev(const S* w, const typename Coef<S>::type* inv, S* o
 template <typename S>
 cudaError_t launch_scale(const S* x, double a, S* out, long long n, cudaStream_t st);
 template <typename S>
-cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, long long n, double* partial, int nb,
-                          cudaStream_t st);
+cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, long long n, double* partial, int& nb,
+                          const RowSink& R, cudaStream_t st);
 template <typename S>
 cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
-                               const S* w_in, S* w_out, long long n, double* partial, int nb, cudaStream_t st);
+                               const S* w_in, S* w_out, long long n, double* partial, int& nb, const RowSink& R,
+                               cudaStream_t st);
 template <typename S>
 cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
-                             const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int nb,
-                             cudaStream_t st);
+                             const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int& nb,
+                             const RowSink& R, cudaStream_t st);
 
 // Block-wise helpers (ns vectors of n elements at stride ld), coefficients on the device:
 //  block_dot:   partial[s][nb] = partial sums of a_s . b_s

@@ -127,6 +127,7 @@ struct FGMRESWork {
   double* dvals = nullptr;    // device scalars: h1[65], h2[65], norms, decision, y[64], 1
   ff* fvals = nullptr;        // the same scalars split into ff (the ff kernels' coefficients)
   double* hvals = nullptr;    // pinned host mirror
+  unsigned* count = nullptr;  // arrival counter of the fused reductions (0 between kernels)
   int nb = 0;
 };
 

@@ -16,7 +16,10 @@
 // the host (CombineParams, scalars) or by the reduction that produced them
 // (ReduceExtra), so that no FP64 instruction runs per element.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "ffmath.cuh"
 #include "kernels.h"
@@ -32,6 +35,25 @@ inline int blocks_for(long long n, int per_thread = 1) {
   if (b < 1) b = 1;
   if (b > 152 * 32) b = 152 * 32;
   return (int)b;
+}
+
+// Blocks of one full wave of a grid-stride reduction kernel (its resident CTAs per SM x the SMs),
+// at most cap: a grid of 4.1 waves leaves most SMs idle during the last one, a single wave none.
+int wave_blocks(const void* kern, int cap) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> waves;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cap;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = waves.find({dev, kern});
+  if (it == waves.end()) {
+    int sms = 0, occ = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0) != cudaSuccess)
+      return cap;
+    it = waves.emplace(std::make_pair(dev, kern), std::max(1, sms * std::max(1, occ))).first;
+  }
+  return std::min(it->second, cap);
 }
 
 __device__ __forceinline__ void coords(int idx, int dim, int n1, int& x, int& y, int& z) {
@@ -80,6 +102,43 @@ __device__ __forceinline__ void block_partials(C (&acc)[NR], double* __restrict_
     for (int q = 1; q < kThreads / 32; ++q) x = dev::add(x, sred[threadIdx.x][q]);
     partial[(long long)threadIdx.x * nb + blockIdx.x] = dev::to_double(x);
   }
+}
+
+// Final value of row i of a reduction, with the optional extras (thread-level).
+__device__ __forceinline__ void finish_row(int i, double v, double* __restrict__ out, int take_sqrt,
+                                           const ReduceExtra& X) {
+  if (take_sqrt) v = sqrt(v);
+  out[i] = v;
+  if (X.out_ff) X.out_ff[i] = dev::from_double<ff>(v);
+  if (i == 0 && (X.inv || X.inv_ff)) {
+    const double r = (v > 0.0) ? 1.0 / v : 0.0;
+    if (X.inv) X.inv[0] = r;
+    if (X.inv_ff) X.inv_ff[0] = dev::from_double<ff>(r);
+  }
+  if (X.decide_flag && i == X.decide_row) X.decide_flag[0] = (v < X.eta2 * X.decide_ref[0]) ? 1.0 : 0.0;
+  if (X.copy_out && i == X.copy_row) X.copy_out[0] = v;
+}
+
+// After the block's partials are written: the block that finishes last (of nblocks) sums every
+// row over the nb blocks, one warp per row, each lane over blocks lane, lane + 32, ... then a
+// shuffle tree (a fixed order, whichever block comes last), and resets the counter.
+__device__ void finish_rows(const double* partial, int rows, int nb, unsigned nblocks, const RowSink& R) {
+  __shared__ bool last;
+  __threadfence();  // this block's partials are visible before its arrival is counted
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(R.count, 1u) == nblocks - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < rows; i += blockDim.x >> 5) {
+    double acc = 0.0;
+    for (int b = lane; b < nb; b += 32) acc += __ldcg(partial + (long long)i * nb + b);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) finish_row(i, acc, R.out, R.take_sqrt, R.X);
+  }
+  if (threadIdx.x == 0) *R.count = 0u;
 }
 
 // ------------------------------------------------------------ stage combination
@@ -226,7 +285,7 @@ template <typename S, int MODE>  // 0: dots of w_in;  1: w_out = w_in - V h, the
 __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, long long vstride, int nv,
                                                       const typename Coef<S>::type* __restrict__ h,
                                                       const S* __restrict__ w_in, S* __restrict__ w_out, int n,
-                                                      double* __restrict__ partial, int nb) {
+                                                      double* __restrict__ partial, int nb, const RowSink R) {
   using C = typename Coef<S>::type;
   constexpr int G = 8;
   const int i0 = blockIdx.y * G;
@@ -270,6 +329,7 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
     if (g < cnt) partial[(long long)(i0 + g) * nb + blockIdx.x] = dev::to_double(x);
     if (g == G && last) partial[(long long)nv * nb + blockIdx.x] = dev::to_double(x);
   }
+  finish_rows(partial, nv + 1, nb, gridDim.x * gridDim.y, R);
 }
 
 // Basis sizes up to 16: fully unrolled, one pass over the basis per kernel; in MODE 1 the
@@ -278,7 +338,7 @@ template <typename S, int MODE, int NV>
 __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict__ V, long long vstride,
                                                             const typename Coef<S>::type* __restrict__ h,
                                                             const S* __restrict__ w_in, S* __restrict__ w_out, int n,
-                                                            double* __restrict__ partial, int nb) {
+                                                            double* __restrict__ partial, int nb, const RowSink R) {
   using C = typename Coef<S>::type;
   C hr[NV];
   if (MODE == 1) {
@@ -303,6 +363,7 @@ __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict_
     acc[NV] = dev::mad(acc[NV], we, we);
   }
   block_partials<C, NV + 1>(acc, partial, nb, NV + 1);
+  finish_rows(partial, NV + 1, nb, gridDim.x, R);
 }
 
 // w_out = w_in - V h when the device flag says the first pass cancelled too much ("twice is
@@ -312,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
                                                              const typename Coef<S>::type* __restrict__ h,
                                                              const double* __restrict__ redo_flag,
                                                              const S* __restrict__ w_in, S* __restrict__ w_out, int n,
-                                                             double* __restrict__ partial) {
+                                                             double* __restrict__ partial, const RowSink R) {
   using C = typename Coef<S>::type;
   // the flag is 1.0 or 0.0: its bit pattern decides (no FP64 compare)
   const bool redo = __double_as_longlong(redo_flag[0]) != 0;
@@ -343,10 +404,11 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
     }
   }
   block_partials<C, 1>(acc, partial, gridDim.x, 1);
+  finish_rows(partial, 1, gridDim.x, gridDim.x, R);
 }
 
 template <typename S>
-__global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __restrict__ partial) {
+__global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __restrict__ partial, const RowSink R) {
   using C = typename Coef<S>::type;
   C acc[1] = {dev::zero<C>()};
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -354,6 +416,7 @@ __global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __res
     acc[0] = dev::mad(acc[0], v, v);
   }
   block_partials<C, 1>(acc, partial, gridDim.x, 1);
+  finish_rows(partial, 1, gridDim.x, gridDim.x, R);
 }
 
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out,
@@ -370,15 +433,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
   if (threadIdx.x == 0) {
     double v = 0.0;
     for (int q = 0; q < kThreads / 32; ++q) v += red[q];
-    if (take_sqrt) v = sqrt(v);
-    out[i] = v;
-    if (X.out_ff) X.out_ff[i] = dev::from_double<ff>(v);
-    if (i == 0 && (X.inv || X.inv_ff)) {
-      const double r = (v > 0.0) ? 1.0 / v : 0.0;
-      if (X.inv) X.inv[0] = r;
-      if (X.inv_ff) X.inv_ff[0] = dev::from_double<ff>(r);
-    }
-    if (X.decide_flag && i == X.decide_row) X.decide_flag[0] = (v < X.eta2 * X.decide_ref[0]) ? 1.0 : 0.0;
+    finish_row(i, v, out, take_sqrt, X);
   }
 }
 
@@ -541,8 +596,11 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
   return cudaGetLastError();
 }
 
-#define IRK_GSC(MODE, NVV, ...) \
-  case NVV: gs_small_kernel<S, MODE, NVV><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break;
+#define IRK_GSC(MODE, NVV, ...)                                                         \
+  case NVV:                                                                             \
+    nb = wave_blocks((const void*)gs_small_kernel<S, MODE, NVV>, nb);                   \
+    gs_small_kernel<S, MODE, NVV><<<nb, kThreads, 0, st>>>(__VA_ARGS__);                \
+    break;
 #define IRK_GS_SMALL(MODE, ...)                                                                            \
   switch (nv) {                                                                                           \
     IRK_GSC(MODE, 1, __VA_ARGS__) IRK_GSC(MODE, 2, __VA_ARGS__) IRK_GSC(MODE, 3, __VA_ARGS__)            \
@@ -550,34 +608,39 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
     IRK_GSC(MODE, 7, __VA_ARGS__) IRK_GSC(MODE, 8, __VA_ARGS__) IRK_GSC(MODE, 9, __VA_ARGS__)            \
     IRK_GSC(MODE, 10, __VA_ARGS__) IRK_GSC(MODE, 11, __VA_ARGS__) IRK_GSC(MODE, 12, __VA_ARGS__)         \
     IRK_GSC(MODE, 13, __VA_ARGS__) IRK_GSC(MODE, 14, __VA_ARGS__) IRK_GSC(MODE, 15, __VA_ARGS__)         \
-    default: gs_small_kernel<S, MODE, 16><<<nb, kThreads, 0, st>>>(__VA_ARGS__); break;                   \
+    default:                                                                                              \
+      nb = wave_blocks((const void*)gs_small_kernel<S, MODE, 16>, nb);                                    \
+      gs_small_kernel<S, MODE, 16><<<nb, kThreads, 0, st>>>(__VA_ARGS__);                                 \
+      break;                                                                                              \
   }
 
 template <typename S>
-cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, long long n, double* partial, int nb,
-                          cudaStream_t st) {
-  if (nv < 1 || nv > 64) return cudaErrorInvalidValue;
+cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, long long n, double* partial, int& nb,
+                          const RowSink& R, cudaStream_t st) {
+  if (nv < 1 || nv > 64 || !R.out || !R.count) return cudaErrorInvalidValue;
   using C = typename Coef<S>::type;
   if (nv <= 16) {
-    IRK_GS_SMALL(0, V, vstride, (const C*)nullptr, w, (S*)nullptr, (int)n, partial, nb);
+    IRK_GS_SMALL(0, V, vstride, (const C*)nullptr, w, (S*)nullptr, (int)n, partial, nb, R);
     return cudaGetLastError();
   }
+  nb = wave_blocks((const void*)gs_kernel<S, 0>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  gs_kernel<S, 0><<<grid, kThreads, 0, st>>>(V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb);
+  gs_kernel<S, 0><<<grid, kThreads, 0, st>>>(V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb, R);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const typename Coef<S>::type* h, const S* w_in,
-                               S* w_out, long long n, double* partial, int nb, cudaStream_t st) {
-  if (nv < 1 || nv > 64 || w_in == w_out) return cudaErrorInvalidValue;
+                               S* w_out, long long n, double* partial, int& nb, const RowSink& R, cudaStream_t st) {
+  if (nv < 1 || nv > 64 || w_in == w_out || !R.out || !R.count) return cudaErrorInvalidValue;
   if (nv <= 16) {
-    IRK_GS_SMALL(1, V, vstride, h, w_in, w_out, (int)n, partial, nb);
+    IRK_GS_SMALL(1, V, vstride, h, w_in, w_out, (int)n, partial, nb, R);
     return cudaGetLastError();
   }
   // group 0 writes w_out; the other groups recompute it for their dots
+  nb = wave_blocks((const void*)gs_kernel<S, 1>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  gs_kernel<S, 1><<<grid, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, partial, nb);
+  gs_kernel<S, 1><<<grid, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, partial, nb, R);
   return cudaGetLastError();
 }
 #undef IRK_GS_SMALL
@@ -585,26 +648,31 @@ cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const type
 
 template <typename S>
 cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
-                             const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int nb,
-                             cudaStream_t st) {
-  if (nv < 1 || nv > 64 || w_in == w_out) return cudaErrorInvalidValue;
+                             const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int& nb,
+                             const RowSink& R, cudaStream_t st) {
+  if (nv < 1 || nv > 64 || w_in == w_out || !R.out || !R.count) return cudaErrorInvalidValue;
   switch (nv) {
 #define IRK_GSR(NVV)                                                                                            \
   case NVV:                                                                                                     \
-    gs_reorth_kernel<S, NVV><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial); \
+    nb = wave_blocks((const void*)gs_reorth_kernel<S, NVV>, nb);                                                 \
+    gs_reorth_kernel<S, NVV><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R); \
     return cudaGetLastError();
     IRK_GSR(1) IRK_GSR(2) IRK_GSR(3) IRK_GSR(4) IRK_GSR(5) IRK_GSR(6) IRK_GSR(7) IRK_GSR(8)
     IRK_GSR(9) IRK_GSR(10) IRK_GSR(11) IRK_GSR(12) IRK_GSR(13) IRK_GSR(14) IRK_GSR(15) IRK_GSR(16)
 #undef IRK_GSR
     default: break;
   }
-  gs_reorth_kernel<S, 0><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial);
+  nb = wave_blocks((const void*)gs_reorth_kernel<S, 0>, nb);
+  gs_reorth_kernel<S, 0><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R);
   return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int nb, cudaStream_t st) {
-  norm2_kernel<S><<<nb, kThreads, 0, st>>>(w, n, partial);
+cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int& nb, const RowSink& R,
+                                 cudaStream_t st) {
+  if (!R.out || !R.count) return cudaErrorInvalidValue;
+  nb = wave_blocks((const void*)norm2_kernel<S>, nb);
+  norm2_kernel<S><<<nb, kThreads, 0, st>>>(w, n, partial, R);
   return cudaGetLastError();
 }
 
@@ -630,12 +698,13 @@ cudaError_t launch_scale(const S* x, double a, S* out, long long n, cudaStream_t
 }
 
 #define IRK_KRYLOV_INST(S)                                                                                        \
-  template cudaError_t launch_gs_dot<S>(const S*, long long, int, const S*, long long, double*, int, cudaStream_t); \
+  template cudaError_t launch_gs_dot<S>(const S*, long long, int, const S*, long long, double*, int&,              \
+                                        const RowSink&, cudaStream_t);                                             \
   template cudaError_t launch_gs_axpy_dot<S>(const S*, long long, int, const Coef<S>::type*, const S*, S*,          \
-                                             long long, double*, int, cudaStream_t);                              \
+                                             long long, double*, int&, const RowSink&, cudaStream_t);             \
   template cudaError_t launch_gs_reorth<S>(const S*, long long, int, const Coef<S>::type*, const double*,         \
-                                           const S*, S*, long long, double*, int, cudaStream_t);                  \
-  template cudaError_t launch_norm2_partial<S>(const S*, long long, double*, int, cudaStream_t);                  \
+                                           const S*, S*, long long, double*, int&, const RowSink&, cudaStream_t); \
+  template cudaError_t launch_norm2_partial<S>(const S*, long long, double*, int&, const RowSink&, cudaStream_t);  \
   template cudaError_t launch_multi_axpy<S>(const S*, long long, int, const Coef<S>::type*, double, S*,           \
                                             long long, cudaStream_t);                                             \
   template cudaError_t launch_scale_dev<S>(const S*, const Coef<S>::type*, S*, long long, cudaStream_t);          \

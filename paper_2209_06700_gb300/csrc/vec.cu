@@ -53,17 +53,20 @@ __device__ __forceinline__ T diag_at(const DiagParams<T>& D, int s, int dim, int
 }
 
 // ------------------------------------------------------------ Chebyshev start, diag scaling
-// One CTA per grid row (y, z) of one block: the row's K values c / diag by in-cell x position are
-// formed once in shared memory, then x = (c / D) b along the row (interior nodes only).
+// One warp per grid row (y, z) of one block, eight rows per CTA: the row's K values c / diag by
+// in-cell x position are formed once per warp, then x = (c / D) b along the row (interior nodes).
 template <typename T>
 __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
   const int s = blockIdx.y;
-  const int n1 = g.n1, r = blockIdx.x;
+  const int n1 = g.n1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nrows = (g.dim == 3) ? n1 * n1 : n1;
+  const int r = blockIdx.x * (blockDim.x >> 5) + w;
+  if (r >= nrows) return;
   const int iy = (g.dim == 3) ? r % n1 : r, iz = (g.dim == 3) ? r / n1 : 1;
   if (iy < 1 || iy > n1 - 2 || (g.dim == 3 && (iz < 1 || iz > n1 - 2))) return;
-  __shared__ T sc[kMaxDeg];
-  if (threadIdx.x < g.k) {
-    const int rx = threadIdx.x, ry = iy % g.k, rz = iz % g.k;
+  T sc = T(0);  // lane rx < k holds c / diag for in-cell x position rx
+  if (lane < g.k) {
+    const int rx = lane, ry = iy % g.k, rz = iz % g.k;
     const T mx = D.dmr[rx], kx = D.dkr[rx], my = D.dmr[ry], ky = D.dkr[ry];
     T d;
     if (g.dim == 3) {
@@ -72,11 +75,14 @@ __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __rest
     } else {
       d = D.cm[s] * (mx * my) + D.ck[s] * (kx * my + mx * ky);
     }
-    sc[rx] = D.c[s] / d;
+    sc = D.c[s] / d;
   }
-  __syncthreads();
   const long long o = s * g.ld + (long long)r * n1;
-  for (int ix = 1 + threadIdx.x; ix <= n1 - 2; ix += blockDim.x) x[o + ix] = sc[ix % g.k] * b[o + ix];
+  for (int x0 = 1; x0 <= n1 - 2; x0 += 32) {  // uniform trip count: every lane takes part in the shuffle
+    const int ix = x0 + lane;
+    const T f = __shfl_sync(0xffffffffu, sc, ix % g.k);
+    if (ix <= n1 - 2) x[o + ix] = f * b[o + ix];
+  }
 }
 
 template <typename Tin, typename Tout>
@@ -501,8 +507,9 @@ __global__ void coupled_update_kernel(GridInfo g, const T* __restrict__ mx, cons
 // ============================================================ launchers
 template <typename T>
 cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, const DiagParams<T>& D, cudaStream_t st) {
-  dim3 grid(g.dim == 3 ? g.n1 * g.n1 : g.n1, nstage);
-  cheb_first_kernel<T><<<grid, 128, 0, st>>>(g, b, x, D);
+  const int rows = (g.dim == 3) ? g.n1 * g.n1 : g.n1;
+  dim3 grid((rows + 7) / 8, nstage);
+  cheb_first_kernel<T><<<grid, 256, 0, st>>>(g, b, x, D);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_first<float>(const GridInfo&, int, const float*, float*, const DiagParams<float>&,

@@ -672,15 +672,16 @@ class MG final : public MGBase {
     return Status::Ok();
   }
 
-  // Fused coarse cycle: the lowest levels with at most kFusedMaxNodes nodes per block run in one
-  // launch (FP32 multigrid, batched blocks, dense coarsest solve, at least two fused levels).
+  // Fused coarse cycle: the lowest levels with at most kFusedMaxNodes3D (2D) nodes per block run in
+  // one launch (FP32 multigrid, batched blocks, dense coarsest solve, at least two fused levels).
   Status setup_fused() {
     fused_ = false;
     if (sizeof(T) != 4 || !cfg_.batched || use_fd_ || coupled() || cfg_.cheb_degree > kMaxChebDegree ||
         cfg_.nb > kMaxQ)
       return Status::Ok();
     int lc = levels() - 1;
-    while (lc > 0 && lv_[lc - 1].g.n <= kFusedMaxNodes) --lc;
+    const long long maxn = (cfg_.dim == 3) ? kFusedMaxNodes3D : kFusedMaxNodes2D;
+    while (lc > 0 && lv_[lc - 1].g.n <= maxn) --lc;
     const int nlev = levels() - lc;
     if (nlev < 2 || nlev > kMaxFusedLevels) return Status::Ok();
     CoarseParams& P = fparams_;

@@ -11,6 +11,7 @@
 // coarse inverse read from global memory.  The arithmetic is the same as the
 // level-by-level path (same operator, same Chebyshev recurrence and interval).
 #include "coarse_cycle.h"
+#include "pdl.cuh"
 
 namespace irk {
 namespace {
@@ -279,6 +280,7 @@ __device__ void tpass(const T* src, T* dst, const int (&ds)[3], const int (&dd)[
 
 template <typename T, int K, int DIM>
 __global__ void __launch_bounds__(kCT) coarse_cycle_kernel(const CoarseParams P) {
+  dev::pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   constexpr int KD = (DIM == 3) ? K * K * K : K * K;
@@ -373,7 +375,7 @@ cudaError_t launch_kd(const CoarseParams& P, size_t smem, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     granted = smem;
   }
-  coarse_cycle_kernel<T, K, DIM><<<P.nb, kCT, smem, st>>>(P);
+  launch_pdl(coarse_cycle_kernel<T, K, DIM>, P.nb, kCT, smem, st, P);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,7 @@
 
 #include "ffmath.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 
 namespace irk {
 namespace dev {
@@ -271,6 +272,7 @@ template <typename T, int K, int EPI, int CXS>
 __global__ void __launch_bounds__(32 * Warps3D<T, K>::value, MinBlocks<T>::value)
 op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
             const EpiParams<typename Storage<T>::type> E) {
+  dev::pdl_enter();
   using S = typename Storage<T>::type;
   constexpr int RPW = 32 / CXS;  // node rows per warp
   constexpr int CY = Tile3D<T, K, CXS>::CY;
@@ -489,6 +491,7 @@ template <typename T, int K, int EPI>
 __global__ void __launch_bounds__(64)
 op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
             const EpiParams<typename Storage<T>::type> E) {
+  dev::pdl_enter();
   using S = typename Storage<T>::type;
   constexpr int NW = 2, NT = 32 * NW;
   constexpr int CX = 32 * NW, CW = CX + 2, SL = K * CW;
@@ -747,7 +750,7 @@ cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const O
   Q.cluster = sh.cluster;
   dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
   if (!Q.cluster) {
-    kern<<<grid, threads, I::smem, st>>>(u, Q, E);
+    kern<<<grid, threads, I::smem, st>>>(u, Q, E);  // a plain launch (pdl.cuh)
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -827,7 +830,7 @@ cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u,
   if (Q.zc <= 0) Q.zc = pick_zc(P.N, (long long)ntx * nstage, (long long)occ * device_sm_count(), K);
   const int nch = (P.N + Q.zc - 1) / Q.zc;
   dim3 grid(ntx, nch, nstage);
-  op2d_kernel<T, K, EPI><<<grid, 64, 0, st>>>(u, Q, E);
+  launch_pdl(op2d_kernel<T, K, EPI>, grid, 64, 0, st, u, Q, E);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@
 
 #include "ffmath.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 
 namespace irk {
 
@@ -148,6 +149,7 @@ template <typename Ta, typename Tb, typename Tout, int NMAX>
 __global__ void __launch_bounds__(kThreads) combine_kernel(const Ta* __restrict__ a, const Tb* __restrict__ b,
                                                            Tout* __restrict__ out, int n, long long ld,
                                                            const CombineParams C) {
+  dev::pdl_enter();
   using A = typename ArithOf<Ta, Tb, Tout>::type;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     A av[NMAX], bv[NMAX];
@@ -181,6 +183,7 @@ template <typename Ta, typename Tb, typename Tout, int Q, int CS>
 __global__ void __launch_bounds__(kThreads) combine_struct_kernel(const Ta* __restrict__ a, const Tb* __restrict__ b,
                                                                   Tout* __restrict__ out, int n, long long ld,
                                                                   const CombineParams C) {
+  dev::pdl_enter();
   using A = typename ArithOf<Ta, Tb, Tout>::type;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     A av[Q];
@@ -209,6 +212,7 @@ template <typename S>
 __global__ void stage_rhs_kernel(GridInfo g, const RhsParams R, const S* __restrict__ Ky,
                                  const double* __restrict__ G1, const double* __restrict__ loads,
                                  S* __restrict__ rhs) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   const int n = (int)g.n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -259,6 +263,7 @@ struct UpdateParams {
 // y += tau sum_i b_i k_i: the stage sum in the vectors' arithmetic, the add to y in FP64
 template <typename S>
 __global__ void update_kernel(GridInfo g, const UpdateParams U, const S* __restrict__ kst, double* __restrict__ y) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n; e += (long long)gridDim.x * blockDim.x) {
     C acc = dev::zero<C>();
@@ -271,10 +276,12 @@ __global__ void update_kernel(GridInfo g, const UpdateParams U, const S* __restr
 }
 
 __global__ void to_ff_kernel(const double* __restrict__ in, ff* __restrict__ out, long long n) {
+  dev::pdl_enter();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = dev::from_double<ff>(in[e]);
 }
 __global__ void from_ff_kernel(const ff* __restrict__ in, double* __restrict__ out, long long n) {
+  dev::pdl_enter();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = dev::to_double(dev::ldg<ff>(in + e));
 }
@@ -286,6 +293,7 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
                                                       const typename Coef<S>::type* __restrict__ h,
                                                       const S* __restrict__ w_in, S* __restrict__ w_out, int n,
                                                       double* __restrict__ partial, int nb, const RowSink R) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   constexpr int G = 8;
   const int i0 = blockIdx.y * G;
@@ -339,6 +347,7 @@ __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict_
                                                             const typename Coef<S>::type* __restrict__ h,
                                                             const S* __restrict__ w_in, S* __restrict__ w_out, int n,
                                                             double* __restrict__ partial, int nb, const RowSink R) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   C hr[NV];
   if (MODE == 1) {
@@ -374,6 +383,7 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
                                                              const double* __restrict__ redo_flag,
                                                              const S* __restrict__ w_in, S* __restrict__ w_out, int n,
                                                              double* __restrict__ partial, const RowSink R) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   // the flag is 1.0 or 0.0: its bit pattern decides (no FP64 compare)
   const bool redo = __double_as_longlong(redo_flag[0]) != 0;
@@ -409,6 +419,7 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
 
 template <typename S>
 __global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __restrict__ partial, const RowSink R) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   C acc[1] = {dev::zero<C>()};
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -421,6 +432,7 @@ __global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __res
 
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nb, double* __restrict__ out,
                                        int take_sqrt, const ReduceExtra X) {
+  dev::pdl_enter();
   const int i = blockIdx.x;
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[(long long)i * nb + b];
@@ -441,6 +453,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 template <typename S>
 __global__ void multi_axpy_kernel(const S* __restrict__ V, long long vstride, int nv,
                                   const typename Coef<S>::type* __restrict__ h, int negate, S* w, long long n) {
+  dev::pdl_enter();
   using C = typename Coef<S>::type;
   __shared__ C hs[64];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = negate ? dev::neg(h[i]) : h[i];
@@ -455,6 +468,7 @@ __global__ void multi_axpy_kernel(const S* __restrict__ V, long long vstride, in
 // out = inv[0] w (inv on the device, written by the norm's reduction); out may alias w
 template <typename S>
 __global__ void scale_dev_kernel(const S* w, const typename Coef<S>::type* __restrict__ inv, S* out, long long n) {
+  dev::pdl_enter();
   const typename Coef<S>::type f = inv[0];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = dev::mul(f, w[e]);
@@ -462,6 +476,7 @@ __global__ void scale_dev_kernel(const S* w, const typename Coef<S>::type* __res
 
 template <typename S>
 __global__ void scale_kernel(const S* x, typename Coef<S>::type a, S* out, long long n) {
+  dev::pdl_enter();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = dev::mul(a, x[e]);
 }
@@ -509,7 +524,7 @@ cudaError_t launch_combine(const Ta* a, const Tb* b, Tout* out, long long n, lon
     }
   const int q = C.nout;
 #define IRK_CS(QQ, CSV) \
-  combine_struct_kernel<Ta, Tb, Tout, QQ, CSV><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz)
+  launch_pdl(combine_struct_kernel<Ta, Tb, Tout, QQ, CSV>, grid, kThreads, 0, st, a, b, out, (int)n, ld, Cz)
 #define IRK_CS_Q(CSV)                         \
   switch (q) {                                \
     case 1: IRK_CS(1, CSV); break;            \
@@ -529,9 +544,9 @@ cudaError_t launch_combine(const Ta* a, const Tb* b, Tout* out, long long n, lon
   }
 #undef IRK_CS_Q
 #undef IRK_CS
-  if (nmax <= 2) combine_kernel<Ta, Tb, Tout, 2><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
-  else if (nmax <= 4) combine_kernel<Ta, Tb, Tout, 4><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
-  else combine_kernel<Ta, Tb, Tout, kMaxQ><<<grid, kThreads, 0, st>>>(a, b, out, (int)n, ld, Cz);
+  if (nmax <= 2) launch_pdl(combine_kernel<Ta, Tb, Tout, 2>, grid, kThreads, 0, st, a, b, out, (int)n, ld, Cz);
+  else if (nmax <= 4) launch_pdl(combine_kernel<Ta, Tb, Tout, 4>, grid, kThreads, 0, st, a, b, out, (int)n, ld, Cz);
+  else launch_pdl(combine_kernel<Ta, Tb, Tout, kMaxQ>, grid, kThreads, 0, st, a, b, out, (int)n, ld, Cz);
   return cudaGetLastError();
 }
 #define IRK_COMBINE_INST(TA, TB, TO)                                                                        \
@@ -553,7 +568,7 @@ cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky,
   RhsParams Rs = R;
   for (int i = 0; i < kMaxQ * kMaxQ; ++i) split_double(R.Ainv[i], &Rs.Ainvh[i], &Rs.Ainvl[i]);
   for (int j = 0; j < kMaxQ; ++j) split_double(R.phi[j], &Rs.phih[j], &Rs.phil[j]);
-  stage_rhs_kernel<S><<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, Rs, Ky, G1, loads, rhs);
+  launch_pdl(stage_rhs_kernel<S>, blocks_for(g.n, 2), kThreads, 0, st, g, Rs, Ky, G1, loads, rhs);
   return cudaGetLastError();
 }
 template cudaError_t launch_stage_rhs<double>(const GridInfo&, const RhsParams&, const double*, const double*,
@@ -570,7 +585,7 @@ cudaError_t launch_update(const GridInfo& g, int Q, const S* kst, const double* 
     U.tb[i] = (i < Q) ? tau * bw[i] : 0.0;
     split_double(U.tb[i], &U.tbh[i], &U.tbl[i]);
   }
-  update_kernel<S><<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, U, kst, y);
+  launch_pdl(update_kernel<S>, blocks_for(g.n, 2), kThreads, 0, st, g, U, kst, y);
   return cudaGetLastError();
 }
 template cudaError_t launch_update<double>(const GridInfo&, int, const double*, const double*, double, double*,
@@ -578,11 +593,11 @@ template cudaError_t launch_update<double>(const GridInfo&, int, const double*, 
 template cudaError_t launch_update<ff>(const GridInfo&, int, const ff*, const double*, double, double*, cudaStream_t);
 
 cudaError_t launch_to_ff(const double* in, ff* out, long long n, cudaStream_t st) {
-  to_ff_kernel<<<blocks_for(n, 2), kThreads, 0, st>>>(in, out, n);
+  launch_pdl(to_ff_kernel, blocks_for(n, 2), kThreads, 0, st, in, out, n);
   return cudaGetLastError();
 }
 cudaError_t launch_from_ff(const ff* in, double* out, long long n, cudaStream_t st) {
-  from_ff_kernel<<<blocks_for(n, 2), kThreads, 0, st>>>(in, out, n);
+  launch_pdl(from_ff_kernel, blocks_for(n, 2), kThreads, 0, st, in, out, n);
   return cudaGetLastError();
 }
 
@@ -592,14 +607,14 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
                                    const ReduceExtra* extra) {
   ReduceExtra X;
   if (extra) X = *extra;
-  reduce_partials_kernel<<<nv, kThreads, 0, st>>>(partial, nb, out, take_sqrt, X);
+  launch_pdl(reduce_partials_kernel, nv, kThreads, 0, st, partial, nb, out, take_sqrt, X);
   return cudaGetLastError();
 }
 
 #define IRK_GSC(MODE, NVV, ...)                                                         \
   case NVV:                                                                             \
     nb = wave_blocks((const void*)gs_small_kernel<S, MODE, NVV>, nb);                   \
-    gs_small_kernel<S, MODE, NVV><<<nb, kThreads, 0, st>>>(__VA_ARGS__);                \
+    launch_pdl(gs_small_kernel<S, MODE, NVV>, nb, kThreads, 0, st, __VA_ARGS__);                \
     break;
 #define IRK_GS_SMALL(MODE, ...)                                                                            \
   switch (nv) {                                                                                           \
@@ -610,7 +625,7 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
     IRK_GSC(MODE, 13, __VA_ARGS__) IRK_GSC(MODE, 14, __VA_ARGS__) IRK_GSC(MODE, 15, __VA_ARGS__)         \
     default:                                                                                              \
       nb = wave_blocks((const void*)gs_small_kernel<S, MODE, 16>, nb);                                    \
-      gs_small_kernel<S, MODE, 16><<<nb, kThreads, 0, st>>>(__VA_ARGS__);                                 \
+      launch_pdl(gs_small_kernel<S, MODE, 16>, nb, kThreads, 0, st, __VA_ARGS__);                                 \
       break;                                                                                              \
   }
 
@@ -625,7 +640,7 @@ cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, lon
   }
   nb = wave_blocks((const void*)gs_kernel<S, 0>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  gs_kernel<S, 0><<<grid, kThreads, 0, st>>>(V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb, R);
+  launch_pdl(gs_kernel<S, 0>, grid, kThreads, 0, st, V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb, R);
   return cudaGetLastError();
 }
 
@@ -640,7 +655,7 @@ cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const type
   // group 0 writes w_out; the other groups recompute it for their dots
   nb = wave_blocks((const void*)gs_kernel<S, 1>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  gs_kernel<S, 1><<<grid, kThreads, 0, st>>>(V, vstride, nv, h, w_in, w_out, (int)n, partial, nb, R);
+  launch_pdl(gs_kernel<S, 1>, grid, kThreads, 0, st, V, vstride, nv, h, w_in, w_out, (int)n, partial, nb, R);
   return cudaGetLastError();
 }
 #undef IRK_GS_SMALL
@@ -655,7 +670,7 @@ cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typena
 #define IRK_GSR(NVV)                                                                                            \
   case NVV:                                                                                                     \
     nb = wave_blocks((const void*)gs_reorth_kernel<S, NVV>, nb);                                                 \
-    gs_reorth_kernel<S, NVV><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R); \
+    launch_pdl(gs_reorth_kernel<S, NVV>, nb, kThreads, 0, st, V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R); \
     return cudaGetLastError();
     IRK_GSR(1) IRK_GSR(2) IRK_GSR(3) IRK_GSR(4) IRK_GSR(5) IRK_GSR(6) IRK_GSR(7) IRK_GSR(8)
     IRK_GSR(9) IRK_GSR(10) IRK_GSR(11) IRK_GSR(12) IRK_GSR(13) IRK_GSR(14) IRK_GSR(15) IRK_GSR(16)
@@ -663,7 +678,7 @@ cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typena
     default: break;
   }
   nb = wave_blocks((const void*)gs_reorth_kernel<S, 0>, nb);
-  gs_reorth_kernel<S, 0><<<nb, kThreads, 0, st>>>(V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R);
+  launch_pdl(gs_reorth_kernel<S, 0>, nb, kThreads, 0, st, V, vstride, nv, h, redo_flag, w_in, w_out, (int)n, partial, R);
   return cudaGetLastError();
 }
 
@@ -672,7 +687,7 @@ cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int& 
                                  cudaStream_t st) {
   if (!R.out || !R.count) return cudaErrorInvalidValue;
   nb = wave_blocks((const void*)norm2_kernel<S>, nb);
-  norm2_kernel<S><<<nb, kThreads, 0, st>>>(w, n, partial, R);
+  launch_pdl(norm2_kernel<S>, nb, kThreads, 0, st, w, n, partial, R);
   return cudaGetLastError();
 }
 
@@ -681,19 +696,19 @@ cudaError_t launch_multi_axpy(const S* V, long long vstride, int nv, const typen
                               S* w, long long n, cudaStream_t st) {
   if (nv < 0 || nv > 64) return cudaErrorInvalidValue;
   if (nv == 0) return cudaSuccess;
-  multi_axpy_kernel<S><<<blocks_for(n, 2), kThreads, 0, st>>>(V, vstride, nv, h, sign < 0 ? 1 : 0, w, n);
+  launch_pdl(multi_axpy_kernel<S>, blocks_for(n, 2), kThreads, 0, st, V, vstride, nv, h, sign < 0 ? 1 : 0, w, n);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_scale_dev(const S* w, const typename Coef<S>::type* inv, S* out, long long n, cudaStream_t st) {
-  scale_dev_kernel<S><<<blocks_for(n, 2), kThreads, 0, st>>>(w, inv, out, n);
+  launch_pdl(scale_dev_kernel<S>, blocks_for(n, 2), kThreads, 0, st, w, inv, out, n);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_scale(const S* x, double a, S* out, long long n, cudaStream_t st) {
-  scale_kernel<S><<<blocks_for(n, 2), kThreads, 0, st>>>(x, host_coef<S>(a), out, n);
+  launch_pdl(scale_kernel<S>, blocks_for(n, 2), kThreads, 0, st, x, host_coef<S>(a), out, n);
   return cudaGetLastError();
 }
 

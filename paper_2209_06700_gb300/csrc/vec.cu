@@ -12,6 +12,7 @@
 
 #include "ffmath.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 
 namespace irk {
 
@@ -57,6 +58,7 @@ __device__ __forceinline__ T diag_at(const DiagParams<T>& D, int s, int dim, int
 // in-cell x position are formed once per warp, then x = (c / D) b along the row (interior nodes).
 template <typename T>
 __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __restrict__ x, const DiagParams<T> D) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const int n1 = g.n1, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nrows = (g.dim == 3) ? n1 * n1 : n1;
@@ -88,6 +90,7 @@ __global__ void cheb_first_kernel(GridInfo g, const T* __restrict__ b, T* __rest
 template <typename Tin, typename Tout>
 __global__ void diag_scale_kernel(GridInfo g, const Tin* __restrict__ x, Tout* __restrict__ out,
                                   const DiagParams<double> D, int inv_sqrt) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const int n = (int)g.n;
   // the diagonal factor in FP32 (this scaling only feeds the Chebyshev-interval estimate): the
@@ -120,6 +123,7 @@ __global__ void diag_scale_kernel(GridInfo g, const Tin* __restrict__ x, Tout* _
 }
 
 __global__ void hash_fill_kernel(GridInfo g, double* __restrict__ x) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const int n = (int)g.n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -139,6 +143,7 @@ __global__ void hash_fill_kernel(GridInfo g, double* __restrict__ x) {
 
 // ------------------------------------------------------------ RHS, update, interpolation
 __global__ void interpolate_kernel(GridInfo g, const double* __restrict__ x1d, double ct, double* __restrict__ y) {
+  dev::pdl_enter();
   const double pi = 3.14159265358979323846;
   const int n = (int)g.n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -155,6 +160,7 @@ __global__ void interpolate_kernel(GridInfo g, const double* __restrict__ x1d, d
 template <int G>
 __global__ void multidot_kernel(const double* __restrict__ V, long long vstride, int nv, const double* __restrict__ w,
                                 long long n, double* __restrict__ partial, int nb) {
+  dev::pdl_enter();
   const int i0 = blockIdx.y * G;
   double acc[G];
 #pragma unroll
@@ -184,6 +190,7 @@ __global__ void multidot_kernel(const double* __restrict__ V, long long vstride,
 
 __global__ void __launch_bounds__(kThreads) block_dot_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                                              int n, long long ld, double* __restrict__ partial) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const double* as = a + s * ld;
   const double* bs = b + s * ld;
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(kThreads) block_dot_kernel(const double* __res
 __global__ void block_axpy2_kernel(double* __restrict__ w, const double* __restrict__ v1, const double* __restrict__ v0,
                                    const double* __restrict__ alpha, const double* __restrict__ beta, int n,
                                    long long ld) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const double a = alpha[s], bt = beta[s];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -215,6 +223,7 @@ __global__ void block_axpy2_kernel(double* __restrict__ w, const double* __restr
 
 __global__ void block_shift_kernel(double* __restrict__ v0, double* __restrict__ v1, const double* __restrict__ w,
                                    const double* __restrict__ nrm, int n, long long ld) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const double f = (nrm[s] > 0.0) ? 1.0 / nrm[s] : 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -264,6 +273,7 @@ __global__ void __launch_bounds__(kThreads) transfer_cell_kernel(const T* __rest
                                                                  long long ld_in, long long ld_out, int din0, int din1,
                                                                  int dout0, int dout1, int nthreads, int accumulate,
                                                                  const TransferParams P) {
+  dev::pdl_enter();
   constexpr int KP = K + 1;
   const int s = blockIdx.y;
   const int Nc = P.Nc;
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(kThreads) transfer_x_rows_kernel(const T* __re
                                                                    long long ld_in, long long ld_out, int nin,
                                                                    int nout, int rows, int accumulate,
                                                                    const TransferParams P) {
+  dev::pdl_enter();
   constexpr int KP = K + 1, NW = kThreads / 32;
   __shared__ T srow[NW][RowMax<T>::value];
   __shared__ T spc[(2 * K + 1) * KP];
@@ -384,6 +395,7 @@ __global__ void __launch_bounds__(kThreads) transfer_x_rows_kernel(const T* __re
 template <typename T>
 __global__ void coarse_solve_kernel(const T* __restrict__ b, T* __restrict__ x, long long ld,
                                     const double* __restrict__ Ainv, const int* __restrict__ map, int nci) {
+  dev::pdl_enter();
   extern __shared__ double sb[];
   const int s = blockIdx.x;
   for (int i = threadIdx.x; i < nci; i += blockDim.x) sb[i] = (double)b[s * ld + map[i]];
@@ -400,6 +412,7 @@ __global__ void coarse_solve_kernel(const T* __restrict__ b, T* __restrict__ x, 
 template <typename Tin, typename Tout>
 __global__ void fd_axis_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, long long ld, int n1, int dim,
                                int axis, const double* __restrict__ Mt, int ni) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const int total = (dim == 3) ? ni * ni * ni : ni * ni;
   const int stride[3] = {1, n1, n1 * n1};
@@ -421,6 +434,7 @@ __global__ void fd_axis_kernel(const Tin* __restrict__ in, Tout* __restrict__ ou
 
 __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, int dim, const double* __restrict__ mu,
                                 const FdParams P) {
+  dev::pdl_enter();
   const int s = blockIdx.y;
   const int ni = P.ni;
   const int total = (dim == 3) ? ni * ni * ni : ni * ni;
@@ -435,6 +449,7 @@ __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, in
 
 __global__ void fd_scale_coupled_kernel(double* __restrict__ t, long long ld, int n1, int dim,
                                         const double* __restrict__ mu, const FdParams P) {
+  dev::pdl_enter();
   const int ni = P.ni;
   const int total = (dim == 3) ? ni * ni * ni : ni * ni;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -454,6 +469,7 @@ template <typename T>
 __global__ void coupled_update_kernel(GridInfo g, const T* __restrict__ mx, const T* __restrict__ kx,
                                       const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ out,
                                       const CoupledParams C) {
+  dev::pdl_enter();
   const int n = (int)g.n;
   const T cm = (T)C.cm, ck = (T)C.ck, beta = (T)C.beta, c1 = (T)C.c1, c2 = (T)C.c2;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -509,7 +525,7 @@ template <typename T>
 cudaError_t launch_cheb_first(const GridInfo& g, int nstage, const T* b, T* x, const DiagParams<T>& D, cudaStream_t st) {
   const int rows = (g.dim == 3) ? g.n1 * g.n1 : g.n1;
   dim3 grid((rows + 7) / 8, nstage);
-  cheb_first_kernel<T><<<grid, 256, 0, st>>>(g, b, x, D);
+  launch_pdl(cheb_first_kernel<T>, grid, 256, 0, st, g, b, x, D);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb_first<float>(const GridInfo&, int, const float*, float*, const DiagParams<float>&,
@@ -521,7 +537,7 @@ template <typename Tin, typename Tout>
 cudaError_t launch_diag_scale(const GridInfo& g, int nstage, const Tin* x, Tout* out, const DiagParams<double>& D,
                               int inv_sqrt, cudaStream_t st) {
   dim3 grid(blocks_for(g.n, 2), nstage);
-  diag_scale_kernel<Tin, Tout><<<grid, kThreads, 0, st>>>(g, x, out, D, inv_sqrt);
+  launch_pdl(diag_scale_kernel<Tin, Tout>, grid, kThreads, 0, st, g, x, out, D, inv_sqrt);
   return cudaGetLastError();
 }
 template cudaError_t launch_diag_scale<double, double>(const GridInfo&, int, const double*, double*,
@@ -533,40 +549,40 @@ template cudaError_t launch_diag_scale<ff, double>(const GridInfo&, int, const f
 
 cudaError_t launch_hash_fill(const GridInfo& g, int nstage, double* x, cudaStream_t st) {
   dim3 grid(blocks_for(g.n, 2), nstage);
-  hash_fill_kernel<<<grid, kThreads, 0, st>>>(g, x);
+  launch_pdl(hash_fill_kernel, grid, kThreads, 0, st, g, x);
   return cudaGetLastError();
 }
 
 cudaError_t launch_interpolate(const GridInfo& g, const double* x1d, double ct, double* y, cudaStream_t st) {
-  interpolate_kernel<<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, x1d, ct, y);
+  launch_pdl(interpolate_kernel, blocks_for(g.n, 2), kThreads, 0, st, g, x1d, ct, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_multidot(const double* V, long long vstride, int nv, const double* w, long long n, double* partial,
                             int nb, cudaStream_t st) {
   dim3 grid(nb, (nv + 7) / 8);
-  multidot_kernel<8><<<grid, kThreads, 0, st>>>(V, vstride, nv, w, n, partial, nb);
+  launch_pdl(multidot_kernel<8>, grid, kThreads, 0, st, V, vstride, nv, w, n, partial, nb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_block_dot(const double* a, const double* b, int ns, long long n, long long ld, double* partial,
                              int nb, cudaStream_t st) {
   dim3 grid(nb, ns);
-  block_dot_kernel<<<grid, kThreads, 0, st>>>(a, b, (int)n, ld, partial);
+  launch_pdl(block_dot_kernel, grid, kThreads, 0, st, a, b, (int)n, ld, partial);
   return cudaGetLastError();
 }
 
 cudaError_t launch_block_axpy2(double* w, const double* v1, const double* v0, const double* alpha, const double* beta,
                                int ns, long long n, long long ld, cudaStream_t st) {
   dim3 grid(blocks_for(n, 2), ns);
-  block_axpy2_kernel<<<grid, kThreads, 0, st>>>(w, v1, v0, alpha, beta, (int)n, ld);
+  launch_pdl(block_axpy2_kernel, grid, kThreads, 0, st, w, v1, v0, alpha, beta, (int)n, ld);
   return cudaGetLastError();
 }
 
 cudaError_t launch_block_shift(double* v0, double* v1, const double* w, const double* nrm, int ns, long long n,
                                long long ld, cudaStream_t st) {
   dim3 grid(blocks_for(n, 2), ns);
-  block_shift_kernel<<<grid, kThreads, 0, st>>>(v0, v1, w, nrm, (int)n, ld);
+  launch_pdl(block_shift_kernel, grid, kThreads, 0, st, v0, v1, w, nrm, (int)n, ld);
   return cudaGetLastError();
 }
 
@@ -584,7 +600,7 @@ cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_i
     const int rows = dout[1] * dout[2];
     dim3 rgrid((rows + kThreads / 32 - 1) / (kThreads / 32), nstage);
 #define IRK_TX(KK, R)                                                                                          \
-  transfer_x_rows_kernel<T, KK, R><<<rgrid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], dout[0], rows, \
+  launch_pdl(transfer_x_rows_kernel<T, KK, R>, rgrid, kThreads, 0, st, in, out, ld_in, ld_out, din[0], dout[0], rows, \
                                                                 accumulate, P)
 #define IRK_TX_K(KK) \
   if (restrict_mode) IRK_TX(KK, true); else IRK_TX(KK, false);
@@ -600,7 +616,7 @@ cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_i
   }
   dim3 grid(blocks_for(nthreads), nstage);
 #define IRK_TR(KK, AX, R)                                                                                  \
-  transfer_cell_kernel<T, KK, AX, R><<<grid, kThreads, 0, st>>>(in, out, ld_in, ld_out, din[0], din[1], dout[0], \
+  launch_pdl(transfer_cell_kernel<T, KK, AX, R>, grid, kThreads, 0, st, in, out, ld_in, ld_out, din[0], din[1], dout[0], \
                                                                 dout[1], (int)nthreads, accumulate, P)
 #define IRK_TR_AX(KK)                                                          \
   if (restrict_mode) {                                                         \
@@ -632,7 +648,7 @@ cudaError_t launch_fd_axis(const Tin* in, Tout* out, int nstage, long long ld, i
                            const double* Mt, int ni, cudaStream_t st) {
   const long long total = (dim == 3) ? (long long)ni * ni * ni : (long long)ni * ni;
   dim3 grid(blocks_for(total), nstage);
-  fd_axis_kernel<Tin, Tout><<<grid, kThreads, 0, st>>>(in, out, ld, n1, dim, axis, Mt, ni);
+  launch_pdl(fd_axis_kernel<Tin, Tout>, grid, kThreads, 0, st, in, out, ld, n1, dim, axis, Mt, ni);
   return cudaGetLastError();
 }
 template cudaError_t launch_fd_axis<float, double>(const float*, double*, int, long long, int, int, int,
@@ -646,7 +662,7 @@ cudaError_t launch_fd_scale(double* t, int nstage, long long ld, int n1, int dim
                             cudaStream_t st) {
   const long long total = (dim == 3) ? (long long)P.ni * P.ni * P.ni : (long long)P.ni * P.ni;
   dim3 grid(blocks_for(total), nstage);
-  fd_scale_kernel<<<grid, kThreads, 0, st>>>(t, ld, n1, dim, mu, P);
+  launch_pdl(fd_scale_kernel, grid, kThreads, 0, st, t, ld, n1, dim, mu, P);
   return cudaGetLastError();
 }
 
@@ -661,7 +677,7 @@ cudaError_t launch_coarse_solve(const T* b, T* x, int nstage, long long ld, cons
     if (e != cudaSuccess) return e;
     granted = smem;
   }
-  coarse_solve_kernel<T><<<nstage, kThreads, smem, st>>>(b, x, ld, Ainv, map, nci);
+  launch_pdl(coarse_solve_kernel<T>, nstage, kThreads, smem, st, b, x, ld, Ainv, map, nci);
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<float>(const float*, float*, int, long long, const double*, const int*, int,
@@ -672,14 +688,14 @@ template cudaError_t launch_coarse_solve<double>(const double*, double*, int, lo
 cudaError_t launch_fd_scale_coupled(double* t, long long ld, int n1, int dim, const double* mu, const FdParams& P,
                                     cudaStream_t st) {
   const long long total = (dim == 3) ? (long long)P.ni * P.ni * P.ni : (long long)P.ni * P.ni;
-  fd_scale_coupled_kernel<<<blocks_for(total), kThreads, 0, st>>>(t, ld, n1, dim, mu, P);
+  launch_pdl(fd_scale_coupled_kernel, blocks_for(total), kThreads, 0, st, t, ld, n1, dim, mu, P);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coupled_update(const GridInfo& g, const T* mx, const T* kx, const T* x, const T* b, T* out,
                                   const CoupledParams& C, cudaStream_t st) {
-  coupled_update_kernel<T><<<blocks_for(g.n, 2), kThreads, 0, st>>>(g, mx, kx, x, b, out, C);
+  launch_pdl(coupled_update_kernel<T>, blocks_for(g.n, 2), kThreads, 0, st, g, mx, kx, x, b, out, C);
   return cudaGetLastError();
 }
 template cudaError_t launch_coupled_update<float>(const GridInfo&, const float*, const float*, const float*,

@@ -31,6 +31,30 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Accumulation for the Krylov reductions and updates.  mad_acc is a + c v without the final
+// renormalisation of the ff result: the product c.hi v.hi is split exactly by an FMA, the cross
+// terms are plain FP32, hi is the rounded sum of the leading parts and lo gathers the error terms
+// (the compensated dot product of Ogita, Rump and Oishi, 2005, on ff operands).  Cancellation can
+// leave |lo| >= |hi|, so such a value is only added to; fin() normalises it (two-sum, exact for
+// any magnitudes) before it multiplies anything, is stored or enters a block reduction.
+__device__ __forceinline__ double mad_acc(double a, double c, double v) { return fma(c, v, a); }
+__device__ __forceinline__ ff mad_acc(ff a, ff c, ff v) {
+  const float p = __fmul_rn(c.hi, v.hi);
+  float pe = __fmaf_rn(c.hi, v.hi, -p);
+  pe = __fmaf_rn(c.hi, v.lo, pe);
+  pe = __fmaf_rn(c.lo, v.hi, pe);
+  const float s = __fadd_rn(a.hi, p);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return ff{s, __fadd_rn(e, __fadd_rn(a.lo, pe))};
+}
+__device__ __forceinline__ double fin(double a) { return a; }
+__device__ __forceinline__ ff fin(ff a) {
+  const float hi = __fadd_rn(a.hi, a.lo);
+  const float bb = __fsub_rn(hi, a.hi);
+  return ff{hi, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(hi, bb)), __fsub_rn(a.lo, bb))};
+}
+
 inline int blocks_for(long long n, int per_thread = 1) {
   long long b = (n + (long long)kThreads * per_thread - 1) / ((long long)kThreads * per_thread);
   if (b < 1) b = 1;
@@ -92,7 +116,7 @@ __device__ __forceinline__ void block_partials(C (&acc)[NR], double* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < NR; ++g) {
-    C x = acc[g];
+    C x = fin(acc[g]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x = dev::add(x, dev::shfl_down(x, off));
     if (lane == 0) sred[g][warp] = x;
@@ -309,13 +333,14 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     C we = dev::ldg<S>(w_in + e);
     if (MODE == 1) {
-      for (int i = 0; i < nv; ++i) we = dev::mad(we, hs[i], dev::ldg<S>(V + i * vstride + e));
+      for (int i = 0; i < nv; ++i) we = mad_acc(we, hs[i], dev::ldg<S>(V + i * vstride + e));
+      we = fin(we);
       if (blockIdx.y == 0) w_out[e] = we;
     }
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      if (i0 + g < nv) acc[g] = dev::mad(acc[g], dev::ldg<S>(V + (i0 + g) * vstride + e), we);
-    acc[G] = dev::mad(acc[G], we, we);
+      if (i0 + g < nv) acc[g] = mad_acc(acc[g], dev::ldg<S>(V + (i0 + g) * vstride + e), we);
+    acc[G] = mad_acc(acc[G], we, we);
   }
   const int cnt = min(G, nv - i0);
   // rows i0 .. i0 + cnt - 1, and row nv from the last group
@@ -324,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g <= G; ++g) {
-    C x = acc[g];
+    C x = fin(acc[g]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x = dev::add(x, dev::shfl_down(x, off));
     if (lane == 0) sred[g][warp] = x;
@@ -364,12 +389,13 @@ __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict_
     C we = dev::ldg<S>(w_in + e);
     if (MODE == 1) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) we = dev::mad(we, hr[i], vv[i]);
+      for (int i = 0; i < NV; ++i) we = mad_acc(we, hr[i], vv[i]);
+      we = fin(we);
       w_out[e] = we;
     }
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = dev::mad(acc[i], vv[i], we);
-    acc[NV] = dev::mad(acc[NV], we, we);
+    for (int i = 0; i < NV; ++i) acc[i] = mad_acc(acc[i], vv[i], we);
+    acc[NV] = mad_acc(acc[NV], we, we);
   }
   block_partials<C, NV + 1>(acc, partial, nb, NV + 1);
   finish_rows(partial, NV + 1, nb, gridDim.x, R);
@@ -396,10 +422,11 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
       C we = dev::ldg<S>(w_in + e);
       if (redo) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) we = dev::mad(we, hr[i], dev::ldg<S>(V + i * vstride + e));
+        for (int i = 0; i < NV; ++i) we = mad_acc(we, hr[i], dev::ldg<S>(V + i * vstride + e));
+        we = fin(we);
       }
       w_out[e] = we;
-      acc[0] = dev::mad(acc[0], we, we);
+      acc[0] = mad_acc(acc[0], we, we);
     }
   } else {
     __shared__ C hs[64];
@@ -408,9 +435,10 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
       C we = dev::ldg<S>(w_in + e);
       if (redo)
-        for (int i = 0; i < nv; ++i) we = dev::mad(we, hs[i], dev::ldg<S>(V + i * vstride + e));
+        for (int i = 0; i < nv; ++i) we = mad_acc(we, hs[i], dev::ldg<S>(V + i * vstride + e));
+      we = fin(we);
       w_out[e] = we;
-      acc[0] = dev::mad(acc[0], we, we);
+      acc[0] = mad_acc(acc[0], we, we);
     }
   }
   block_partials<C, 1>(acc, partial, gridDim.x, 1);
@@ -424,7 +452,7 @@ __global__ void norm2_kernel(const S* __restrict__ w, long long n, double* __res
   C acc[1] = {dev::zero<C>()};
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const C v = dev::ldg<S>(w + e);
-    acc[0] = dev::mad(acc[0], v, v);
+    acc[0] = mad_acc(acc[0], v, v);
   }
   block_partials<C, 1>(acc, partial, gridDim.x, 1);
   finish_rows(partial, 1, gridDim.x, gridDim.x, R);
@@ -460,8 +488,8 @@ __global__ void multi_axpy_kernel(const S* __restrict__ V, long long vstride, in
   __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     C acc = w[e];
-    for (int i = 0; i < nv; ++i) acc = dev::mad(acc, hs[i], dev::ldg<S>(V + i * vstride + e));
-    w[e] = acc;
+    for (int i = 0; i < nv; ++i) acc = mad_acc(acc, hs[i], dev::ldg<S>(V + i * vstride + e));
+    w[e] = fin(acc);
   }
 }
 

@@ -22,6 +22,11 @@ the 2x2 real form and PRESB).  Modules:
 * ``irk``     - stage right-hand side, the full Kronecker stage system
   solved directly, the exact per-mode IRK step by fast diagonalisation, the
   exact semi-discrete solution, and the operator (irk:A) apply.
+* ``deformed`` - the same heat problem on a curved mesh of the cube (the
+  uniform mesh under a boundary-fixing non-affine map, Sec. 4's case of
+  mapping data per quadrature point): per-cell matrices by direct
+  quadrature with the exact Jacobian, load, initial value, L2 error.
+* ``paper_workload`` - the paper's own manufactured solution (Sec. 6).
 * ``mg``      - multigrid ingredients written from their definitions:
   Q_k embedding (prolongation), restriction, Jacobi diagonal, Chebyshev
   iteration, dense coarse solve, one V-cycle, PRESB.

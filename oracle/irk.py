@@ -96,7 +96,7 @@ def step_direct(prob, y_n, t_n, return_stages=False, stage_loads=None):
 
     stage_loads: optional (Q, n) array g(t_n + c_i tau) replacing the built-in source."""
     mesh = prob.mesh
-    M, K = assemble(mesh)
+    M, K = prob.assemble() if hasattr(prob, "assemble") else assemble(mesh)
     MI, keep = interior_restrict(mesh, M)
     KI, _ = interior_restrict(mesh, K)
     Q, tau = prob.Q, prob.tau

@@ -82,6 +82,14 @@ typedef struct {
   int pair_precond;   /* DIAG variant, 2x2 pair blocks: 0 PRESB (Eq. presb:p, two V-cycles on
                          (alpha+beta) M + tau K, default); 1 one V-cycle on the coupled 2x2 system
                          itself (Sec. 6, GMG applied directly to Eq. complex:twobytwo) */
+  double deform;      /* 0 (default): the uniform Cartesian mesh.  eps > 0: the curved mesh
+                         Phi(xi) = xi + eps prod_a sin(pi xi_a) (1, .., 1) of the same cube
+                         (boundary fixed, non-affine cells; needs eps < 1 / (dim pi)).  The
+                         stage operator, K y_n, the load and the initial interpolant then use
+                         the mapping data w det J and w det J J^-1 J^-T at every Gauss point
+                         (Sec. 4: read once per cell for all stages of a launch), in native FP64
+                         with FP64 stage vectors (op_ff is ignored); the preconditioner keeps the
+                         Cartesian blocks of Eq. (irk:P) (flexible GMRES absorbs the difference) */
 } irk_options;
 
 typedef struct {

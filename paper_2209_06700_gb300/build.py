@@ -10,7 +10,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libirk.so")
 SOURCES = ["op_f64.cu", "op_ff.cu", "op_f32.cu", "vec.cu", "stagevec.cu", "mg.cpp", "fgmres.cpp", "capi.cpp", "host_math.cpp",
-           "profiler.cpp", "tune.cpp", "coarse_cycle.cu", "noalloc.cu", "serve.cpp"]
+           "profiler.cpp", "tune.cpp", "coarse_cycle.cu", "noalloc.cu", "serve.cpp", "deform.cu",
+           "deform_geom.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,6 +23,8 @@
 #include <type_traits>
 #include <vector>
 
+#include "deform.h"
+#include "deform_kernels.h"
 #include "profiler.h"
 #include "solver.h"
 
@@ -45,6 +47,11 @@ struct irk_problem {
   double *Ky = nullptr, *rhs = nullptr, *kst = nullptr, *Mu = nullptr, *Ku = nullptr, *G1 = nullptr,
          *x1d = nullptr, *tq = nullptr;
   int nslots = 0;                                   // stage slots of Mu/Ku
+  // curved mesh (opt.deform > 0): mapping data, cell-wise buffers, full load vector
+  bool deformed = false;
+  DeformGeom dgeom;
+  DeformDevice<double> dd;
+  double* Gv = nullptr;
   Profiler prof;
   std::string last_err;
   ~irk_problem() {
@@ -84,6 +91,14 @@ template <typename S> S* as(double* p) { return reinterpret_cast<S*>(p); }
 template <typename S>
 Status launch_apply64(irk_problem* h, const S* u, int ns, const double* cm, const double* ck, int epi, S* out,
                       S* out2, int cat = PROF_APPLY64) {
+  if constexpr (std::is_same<S, double>::value) {
+    if (h->deformed) {  // curved mesh: mapping data per Gauss point, all ns stages in one cell loop
+      IRK_LAUNCH(cat, launch_deformed<double>(h->dd, ns, u, h->fine.ld, epi, cm, ck, out, out2, h->st));
+      return Status::Ok();
+    }
+  } else {
+    if (h->deformed) return Status::Err(IRK_EINVAL, "curved meshes use FP64 stage vectors");
+  }
   using T = typename std::conditional<std::is_same<S, ff>::value, ff, double>::type;
   OpParams<T> P = make_op_params<T>(h->fine, ns, cm, ck);
   EpiParams<S> E;
@@ -191,7 +206,7 @@ Status stage_rhs(irk_problem* h, const double* y, double t_n, const double* load
     const double t = t_n + h->tab.c[j] * h->tau;
     R.phi[j] = h->dim * pi * pi * std::cos(t) - std::sin(t);
   }
-  IRK_LAUNCH(PROF_RHS, launch_stage_rhs<S>(g.grid(), R, as<S>(h->Ky), h->G1, loads, rhs, h->st));
+  IRK_LAUNCH(PROF_RHS, launch_stage_rhs<S>(g.grid(), R, as<S>(h->Ky), h->G1, h->Gv, loads, rhs, h->st));
   return Status::Ok();
 }
 
@@ -369,9 +384,11 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   if (!(o.rtol > 0) || o.max_it < 1 || o.restart < 1 || o.restart > 60 || o.cheb_degree < 1 || o.cheb_degree > 16 ||
       (o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
       o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1) ||
-      (o.pair_precond != 0 && o.pair_precond != 1))
+      (o.pair_precond != 0 && o.pair_precond != 1) || !(o.deform >= 0) ||
+      (o.deform > 0 && !deform_valid(mesh->dim, o.deform)))
     return Status::Err(IRK_EINVAL, "invalid options");
   if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
+  if (o.deform > 0) h->opt.op_ff = 0;  // the curved-mesh operator runs in FP64 on FP64 stage vectors
   h->dim = mesh->dim;
   h->N = mesh->cells_per_axis;
   h->k = degree;
@@ -439,6 +456,34 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
     IRK_CUDA(cudaMemcpyAsync(h->x1d, xd.data(), n1 * sizeof(double), cudaMemcpyHostToDevice, h->st));
     IRK_CUDA(cudaStreamSynchronize(h->st));
   }
+  if (o.deform > 0) {  // curved mesh: mapping data per cell and Gauss point, load vector
+    h->deformed = true;
+    if (!build_deform_geometry(h->dim, h->N, h->el, o.deform, h->dgeom, err)) return Status::Err(IRK_EINVAL, err);
+    const DeformGeom& dg = h->dgeom;
+    double *geo = nullptr, *eM = nullptr, *eK = nullptr;
+    const size_t ecell = (size_t)dg.ncell * h->nslots * dg.nq * sizeof(double);
+    IRK_TRY(h->arena.alloc((void**)&geo, dg.geo.size() * sizeof(double)));
+    IRK_TRY(h->arena.alloc((void**)&eM, ecell));
+    IRK_TRY(h->arena.alloc((void**)&eK, ecell));
+    IRK_TRY(h->arena.alloc((void**)&h->Gv, g.ld * sizeof(double)));
+    std::vector<double> Gload;
+    deform_load_vector(dg, h->el, Gload);
+    IRK_CUDA(cudaMemcpyAsync(geo, dg.geo.data(), dg.geo.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    IRK_CUDA(cudaMemcpyAsync(h->Gv, Gload.data(), Gload.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    h->dgeom.geo.clear();
+    h->dgeom.geo.shrink_to_fit();
+    h->dd.dim = h->dim;
+    h->dd.N = h->N;
+    h->dd.k = degree;
+    h->dd.max_ns = h->nslots;
+    h->dd.ncell = dg.ncell;
+    h->dd.geo = geo;
+    h->dd.eM = eM;
+    h->dd.eK = eK;
+    h->dd.B = h->el.B.data();
+    h->dd.D = h->el.D.data();
+  }
   MGConfig mc;
   mc.dim = h->dim; mc.k = degree; mc.N = h->N; mc.tau = tau;
   mc.cheb_degree = o.cheb_degree; mc.eig_steps = o.eig_steps;
@@ -468,7 +513,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
     }
     IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena, h->st));
   }
-  if (o.autotune) IRK_TRY(autotune_stage_operator(h));
+  if (o.autotune && !h->deformed) IRK_TRY(autotune_stage_operator(h));
   IRK_CUDA(cudaStreamSynchronize(h->st));
   return Status::Ok();
 }
@@ -520,6 +565,7 @@ void irk_default_options(irk_options* o) {
   o->op_ff = 1;
   o->autotune = 1;
   o->pair_precond = 0;
+  o->deform = 0.0;
 }
 
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,
@@ -650,6 +696,13 @@ int irk_autotune_report(char* buf, int len) { return tune_report(buf, len); }
 irk_status irk_interpolate_initial(irk_handle h, double* y, double t) {
   return guarded(h, [&]() -> Status {
     if (!y) return Status::Err(IRK_EINVAL, "y is NULL");
+    if (h->deformed) {  // interpolant at the mapped nodes, built on the host
+      std::vector<double> y0;
+      deform_initial_value(h->dgeom, h->el, t, y0);
+      IRK_CUDA(cudaMemcpyAsync(y, y0.data(), y0.size() * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      IRK_CUDA(cudaStreamSynchronize(h->st));
+      return Status::Ok();
+    }
     IRK_LAUNCH(PROF_RHS, launch_interpolate(h->fine.grid(), h->x1d, std::cos(t), y, h->st));
     return Status::Ok();
   });

@@ -343,6 +343,19 @@ bool build_element1d(int k, Element1D& e, std::string& err) {
       e.Me[i * p + j] = (double)sm;
       e.Ke[i * p + j] = (double)sk;
     }
+  e.gq.resize(p);
+  e.gw.resize(p);
+  e.B.resize(p * p);
+  e.D.resize(p * p);
+  for (int q = 0; q < p; ++q) {
+    e.gq[q] = (double)gq[q];
+    e.gw[q] = (double)gw[q];
+    for (int i = 0; i < p; ++i) {
+      ld di;
+      e.B[q * p + i] = (double)lag(i, gq[q], &di);
+      e.D[q * p + i] = (double)di;
+    }
+  }
   // prolongation: fine node m (0..2k) of a coarse cell split in two
   e.Pc.assign((2 * k + 1) * p, 0);
   for (int m = 0; m <= 2 * k; ++m) {

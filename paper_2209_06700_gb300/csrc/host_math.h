@@ -33,6 +33,8 @@ struct Element1D {
   std::vector<double> nodes;        // k+1 GLL points
   std::vector<double> Me, Ke;       // (k+1)^2 reference element mass / stiffness (row-major)
   std::vector<double> Pc;           // (2k+1) x (k+1): coarse basis i at fine node m of a split cell
+  std::vector<double> gq, gw;       // k+1 Gauss-Legendre points and weights on [0, 1]
+  std::vector<double> B, D;         // (k+1) x (k+1): basis i and its derivative at Gauss point q, [q][i]
 };
 
 bool build_element1d(int k, Element1D& e, std::string& err);

@@ -133,10 +133,11 @@ struct RhsParams {
   double phi[kMaxQ];
   float Ainvh[kMaxQ * kMaxQ], Ainvl[kMaxQ * kMaxQ], phih[kMaxQ], phil[kMaxQ];  // ff split (launcher)
 };
-// rhs_i = sum_j Ainv[i][j] (load_j - Ky); load_j = phi_j (G1 (x) G1 (x) G1) (built-in source)
-// or the user stage loads (device [Q][ld], FP64) when loads != nullptr.  Ky, rhs of type S.
+// rhs_i = sum_j Ainv[i][j] (load_j - Ky); load_j = phi_j (G1 (x) G1 (x) G1) (built-in source; phi_j Gv
+// with the full load vector Gv when Gv != nullptr) or the user stage loads (device [Q][ld], FP64)
+// when loads != nullptr.  Ky, rhs of type S.
 template <typename S>
-cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky, const double* G1,
+cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky, const double* G1, const double* Gv,
                              const double* loads, S* rhs, cudaStream_t st);
 // y += tau sum_i b_i k_i  (k of type S, y FP64)
 template <typename S>

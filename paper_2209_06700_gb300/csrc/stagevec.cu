@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kThreads) combine_struct_kernel(const Ta* __re
 // rhs_i = sum_j Ainv_ij (g_j - K y_n), g_j = phi_j G (built-in source) or the user stage loads
 template <typename S>
 __global__ void stage_rhs_kernel(GridInfo g, const RhsParams R, const S* __restrict__ Ky,
-                                 const double* __restrict__ G1, const double* __restrict__ loads,
-                                 S* __restrict__ rhs) {
+                                 const double* __restrict__ G1, const double* __restrict__ Gv,
+                                 const double* __restrict__ loads, S* __restrict__ rhs) {
   dev::pdl_enter();
   using C = typename Coef<S>::type;
   const int n = (int)g.n;
@@ -250,9 +250,15 @@ __global__ void stage_rhs_kernel(GridInfo g, const RhsParams R, const S* __restr
       for (int j = 0; j < kMaxQ; ++j)
         if (j < R.Q) f[j] = dev::add(dev::from_double<C>(loads[j * g.ld + e]), mky);
     } else {
-      // G = G1[x] G1[y] (G1[z]) in FP64 once per node, then phi_j G - K y_n per stage
-      double G = G1[ix] * G1[iy];
-      if (g.dim == 3) G *= G1[iz];
+      // G = G1[x] G1[y] (G1[z]) in FP64 once per node (or the full load vector Gv of a curved
+      // mesh), then phi_j G - K y_n per stage
+      double G;
+      if (Gv) {
+        G = Gv[e];
+      } else {
+        G = G1[ix] * G1[iy];
+        if (g.dim == 3) G *= G1[iz];
+      }
       const C Gc = dev::from_double<C>(G);
 #pragma unroll
       for (int j = 0; j < kMaxQ; ++j)
@@ -591,18 +597,18 @@ IRK_COMBINE_INST(double, ff, ff)
 #undef IRK_COMBINE_INST
 
 template <typename S>
-cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky, const double* G1, const double* loads,
-                             S* rhs, cudaStream_t st) {
+cudaError_t launch_stage_rhs(const GridInfo& g, const RhsParams& R, const S* Ky, const double* G1, const double* Gv,
+                             const double* loads, S* rhs, cudaStream_t st) {
   RhsParams Rs = R;
   for (int i = 0; i < kMaxQ * kMaxQ; ++i) split_double(R.Ainv[i], &Rs.Ainvh[i], &Rs.Ainvl[i]);
   for (int j = 0; j < kMaxQ; ++j) split_double(R.phi[j], &Rs.phih[j], &Rs.phil[j]);
-  launch_pdl(stage_rhs_kernel<S>, blocks_for(g.n, 2), kThreads, 0, st, g, Rs, Ky, G1, loads, rhs);
+  launch_pdl(stage_rhs_kernel<S>, blocks_for(g.n, 2), kThreads, 0, st, g, Rs, Ky, G1, Gv, loads, rhs);
   return cudaGetLastError();
 }
 template cudaError_t launch_stage_rhs<double>(const GridInfo&, const RhsParams&, const double*, const double*,
-                                              const double*, double*, cudaStream_t);
+                                              const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_stage_rhs<ff>(const GridInfo&, const RhsParams&, const ff*, const double*, const double*,
-                                          ff*, cudaStream_t);
+                                          const double*, ff*, cudaStream_t);
 
 template <typename S>
 cudaError_t launch_update(const GridInfo& g, int Q, const S* kst, const double* bw, double tau, double* y,

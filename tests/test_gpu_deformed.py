@@ -1,0 +1,112 @@
+"""Parity of the curved-mesh path (the stage operator with mapping data at every Gauss point,
+Sec. 4) with the oracle's dense per-cell quadrature on the same curved mesh.
+
+Bars: operator applies 1e-12 relative; the initial interpolant and the stage right-hand side 1e-12;
+the whole step 1e-9 relative in y_{n+1} against the oracle's sparse direct Kronecker solve; one
+launch over all stages equals the per-stage launches bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_06700_gb300 as pkg
+from oracle.deformed import DeformedProblem
+from oracle.irk import apply_calA, step_direct
+from synthetic import uniform_vectors, zero_boundary
+from tests.gpu_util import from_dev, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+YTOL = 1e-9
+
+# (dim, cells, degree, stages, eps): several cells per axis, every degree, odd counts
+CASES = [(2, 7, 1, 2, 0.1), (2, 6, 2, 3, 0.1), (2, 5, 4, 2, 0.1), (3, 5, 1, 2, 0.05), (3, 4, 2, 3, 0.05),
+         (3, 3, 3, 2, 0.05), (3, 3, 4, 3, 0.05)]
+
+
+def _inputs(Q, dim, n1, seed=0):
+    return zero_boundary(uniform_vectors((Q, n1 ** dim), seed=seed), dim, n1)
+
+
+@pytest.mark.parametrize("dim,N,k,Q,eps", CASES)
+def test_general_operator(dim, N, k, Q, eps):
+    rng = np.random.default_rng(7)
+    Cm = rng.standard_normal((Q, Q))
+    Ck = rng.standard_normal((Q, Q))
+    prob = DeformedProblem(dim, N, k, Q, 1e-2, eps)
+    with pkg.Solver(dim, N, k, Q, 1e-2, deform=eps) as s:
+        u = _inputs(Q, dim, k * N + 1, seed=2)
+        ud = to_dev(s, u)
+        vd = torch.zeros_like(ud)
+        s.apply_op(ud, vd, Cm, Ck)
+        got = from_dev(vd, s.n)
+    assert rel_err(got, Cm @ prob.apply_M(u) + Ck @ prob.apply_K(u)) <= TOL
+
+
+@pytest.mark.parametrize("dim,N,k,Q,eps", CASES[1::2])
+def test_calA_apply(dim, N, k, Q, eps):
+    tau = 3e-3
+    prob = DeformedProblem(dim, N, k, Q, tau, eps)
+    with pkg.Solver(dim, N, k, Q, tau, deform=eps) as s:
+        u = _inputs(Q, dim, k * N + 1, seed=4)
+        ud = to_dev(s, u)
+        vd = torch.zeros_like(ud)
+        s.apply(ud, vd)
+        got = from_dev(vd, s.n)
+    assert rel_err(got, apply_calA(prob, u)) <= TOL
+
+
+def test_batched_launch_equals_per_stage_launches():
+    dim, N, k, Q, eps = 3, 5, 3, 3, 0.05
+    Cm = np.diag([1.0, 2.0, 3.0])
+    Ck = np.diag([0.5, 0.25, 0.125])
+    with pkg.Solver(dim, N, k, Q, 1e-2, deform=eps) as s:
+        ud = to_dev(s, _inputs(Q, dim, k * N + 1, seed=9))
+        vb = torch.zeros_like(ud)
+        s.apply_op(ud, vb, Cm, Ck)
+        vs = torch.zeros_like(ud)
+        for i in range(Q):
+            s.apply_op(ud[i:i + 1], vs[i:i + 1], Cm[i:i + 1, i:i + 1], Ck[i:i + 1, i:i + 1])
+        torch.cuda.synchronize()
+        assert torch.equal(vb, vs)
+
+
+@pytest.mark.parametrize("dim,N,k,Q", [(2, 8, 2, 3), (3, 4, 3, 2)])
+def test_initial_value_and_stage_rhs(dim, N, k, Q):
+    eps, tau = (0.1 if dim == 2 else 0.05), 1e-2
+    prob = DeformedProblem(dim, N, k, Q, tau, eps)
+    with pkg.Solver(dim, N, k, Q, tau, deform=eps) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        y0 = y.cpu().numpy()
+        rhs = s.stage_vector()
+        s.stage_rhs(y, 0.3, rhs)
+        got = from_dev(rhs, s.n)
+    assert rel_err(y0, prob.y0()) <= TOL
+    assert rel_err(got, prob.stage_rhs_calA(prob.y0(), 0.3)) <= TOL
+
+
+@pytest.mark.parametrize("dim,N,k,Q,tau,variant", [(2, 8, 2, 3, 1e-2, 0), (2, 6, 4, 2, 1e-2, 0),
+                                                   (3, 4, 2, 3, 1e-3, 0), (3, 4, 3, 3, 1e-3, 0),
+                                                   (3, 4, 2, 3, 1e-3, 1)])
+def test_step(dim, N, k, Q, tau, variant):
+    eps = 0.1 if dim == 2 else 0.05
+    prob = DeformedProblem(dim, N, k, Q, tau, eps)
+    yref = prob.y0()
+    with pkg.Solver(dim, N, k, Q, tau, deform=eps, variant=variant) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        its = []
+        for n in range(2):
+            its.append(s.step(y, n * tau).iterations)
+            yref = step_direct(prob, yref, n * tau)
+        s.synchronize()
+        got = y.cpu().numpy()
+    assert rel_err(got, yref) <= YTOL, its
+    assert max(its) < 60, its
+
+
+def test_invalid_amplitude_is_refused():
+    with pytest.raises(pkg.IrkError):
+        pkg.Solver(3, 4, 2, 2, 1e-2, deform=0.2)   # eps d pi >= 1: the map folds

@@ -243,6 +243,65 @@ def other_workloads(steps=3):
     return out
 
 
+def curved_mesh_workload(w, eps=0.05, steps=3, reps=10):
+    """The headline problem on the curved mesh (irk_options.deform = eps): the step (FP64 stage
+    operator with the mapping data of every Gauss point, Cartesian preconditioner), and the stage
+    operator alone as one launch over all Q stages (mapping data read once per cell) against Q
+    per-stage launches (read Q times), each timed with CUDA events on the solver's stream."""
+    import numpy as np
+    import torch
+    import paper_2209_06700_gb300 as pkg
+    stream = torch.cuda.Stream()
+    s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=w.cheb_degree, deform=eps)
+    try:
+        Cm, Ck = np.eye(w.Q), w.tau * np.eye(w.Q)
+        with torch.cuda.stream(stream):
+            u = s.stage_vector()
+            u.uniform_(-1.0, 1.0, generator=torch.Generator(device="cuda").manual_seed(0))
+            v = torch.zeros_like(u)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        batched = timed(lambda: s.apply_op(u, v, Cm, Ck))
+        per_stage = timed(lambda: [s.apply_op(u[i:i + 1], v[i:i + 1], Cm[i:i + 1, i:i + 1], Ck[i:i + 1, i:i + 1])
+                                   for i in range(w.Q)])
+        y = s.vector()
+        with torch.cuda.stream(stream):
+            s.interpolate_initial(y, 0.0)
+        s.step(y, 0.0)
+        its = []
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(steps):
+            its.append(s.step(y, (i + 1) * w.tau).iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    finally:
+        s.close()
+    ncell, nq, nf = w.cells ** w.dim, (w.degree + 1) ** w.dim, 1 + w.dim * (w.dim + 1) // 2
+    geo = ncell * nq * nf * 8
+    vec = w.n1 ** w.dim * 8
+    units = w.Q * w.n_interior
+    return {"workload": f"{w.name}_curved", "eps": eps, "value": units / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "fgmres_iterations": sum(its) / len(its),
+            "apply": {"ms_batched": batched, "ms_per_stage": per_stage, "stages": w.Q,
+                      "mapping_bytes_per_read": geo,
+                      "bytes_batched": geo + 2 * w.Q * vec, "bytes_per_stage": w.Q * (geo + 2 * vec),
+                      "arithmetic": "FP64 (FP64-ALU bound on this part: the batched launch saves the "
+                                    "mapping-data traffic, not time)"}}
+
+
 def fp64_per_stage_baseline(w, cheb, units, steps=3):
     """The same step on the plain GPU path: native FP64 operator, FP64 V-cycle, one launch per
     stage, no graph replay.  Timed with CUDA events on its stream after one warm-up step."""
@@ -485,6 +544,7 @@ def main():
             line["gpu_fp64_per_stage_baseline"] = fp64_per_stage_baseline(w, cheb, units)
         if world == 1 and not args.no_other_workloads:
             line["other_workloads"] = other_workloads()
+            line["curved_mesh"] = curved_mesh_workload(w)
         if world == 1 and not args.no_serve:
             line["serving"] = serving_measure(args.serve_requests)
             # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)

@@ -23,7 +23,7 @@ the 2x2 real form and PRESB).  Modules:
   solved directly, the exact per-mode IRK step by fast diagonalisation, the
   exact semi-discrete solution, and the operator (irk:A) apply.
 * ``deformed`` - the same heat problem on a curved mesh of the cube (the
-  uniform mesh under a boundary-fixing non-affine map, Sec. 4's case of
+  uniform mesh under a boundary-fixing non-affine map, Sec. 3.4's case of
   mapping data per quadrature point): per-cell matrices by direct
   quadrature with the exact Jacobian, load, initial value, L2 error.
 * ``paper_workload`` - the paper's own manufactured solution (Sec. 6).

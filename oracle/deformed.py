@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Source in arXiv 2209.06700, Sec. 4 (batching of operations): on deformed cells a
+Source in arXiv 2209.06700, Sec. 3.4 (batching of operations): on deformed cells a
 matrix-free loop loads the mapping data, the Jacobian of the cell map at every
 quadrature point, and batching all Q stages into one cell loop loads it once
 instead of Q times.  The paper itself runs affine meshes only and prints no

@@ -1,7 +1,7 @@
 // Stage operator on the curved mesh (sm_103a): v_s = cm[s] M u_s + ck[s] K u_s, or M u_s and
 // K u_s separately, with the mapping data of every Gauss point read from memory.
 //
-// arXiv 2209.06700, Sec. 4 (batching of operations): on deformed cells the matrix-free cell loop
+// arXiv 2209.06700, Sec. 3.4 (batching of operations): on deformed cells the matrix-free cell loop
 // loads the Jacobian data at each quadrature point; one cell loop over all Q stages loads it once
 // instead of once per stage.  deform_cell_kernel does exactly that: one CTA per cell loads the
 // cell's mapping data (w det J and the metric w det J J^-1 J^-T per Gauss point) into registers

@@ -1,6 +1,6 @@
 // Curved-mesh geometry of libirk: the uniform mesh of [0,1]^d mapped by
 // Phi(xi) = xi + eps S(xi) (1, .., 1), S = prod_a sin(pi xi_a), which fixes the boundary of the
-// cube and is non-affine in every cell (one-to-one for eps d pi < 1).  arXiv 2209.06700, Sec. 4
+// cube and is non-affine in every cell (one-to-one for eps d pi < 1).  arXiv 2209.06700, Sec. 3.4
 // (batching of operations): on deformed cells the matrix-free cell loop loads the mapping data at
 // every quadrature point, and one batched loop over all Q stages loads it once instead of Q times.
 #pragma once

@@ -1,5 +1,5 @@
 """Parity of the curved-mesh path (the stage operator with mapping data at every Gauss point,
-Sec. 4) with the oracle's dense per-cell quadrature on the same curved mesh.
+Sec. 3.4) with the oracle's dense per-cell quadrature on the same curved mesh.
 
 Bars: operator applies 1e-12 relative; the initial interpolant and the stage right-hand side 1e-12;
 the whole step 1e-9 relative in y_{n+1} against the oracle's sparse direct Kronecker solve; one

@@ -244,8 +244,8 @@ def other_workloads(steps=3):
 
 
 def curved_mesh_workload(w, eps=0.05, steps=3, reps=10):
-    """The headline problem on the curved mesh (irk_options.deform = eps): the step (FP64 stage
-    operator with the mapping data of every Gauss point, Cartesian preconditioner), and the stage
+    """The headline problem on the curved mesh (irk_options.deform = eps): the step (FP64-accurate
+    stage operator with the mapping data of every Gauss point, Cartesian preconditioner), and the stage
     operator alone as one launch over all Q stages (mapping data read once per cell) against Q
     per-stage launches (read Q times), each timed with CUDA events on the solver's stream."""
     import numpy as np
@@ -298,8 +298,8 @@ def curved_mesh_workload(w, eps=0.05, steps=3, reps=10):
             "apply": {"ms_batched": batched, "ms_per_stage": per_stage, "stages": w.Q,
                       "mapping_bytes_per_read": geo,
                       "bytes_batched": geo + 2 * w.Q * vec, "bytes_per_stage": w.Q * (geo + 2 * vec),
-                      "arithmetic": "FP64 (FP64-ALU bound on this part: the batched launch saves the "
-                                    "mapping-data traffic, not time)"}}
+                      "arithmetic": "float-float on the FP32 pipe, FP64 vectors and mapping data (ALU "
+                                    "bound: the batched launch saves mapping-data traffic, little time)"}}
 
 
 def fp64_per_stage_baseline(w, cheb, units, steps=3):

@@ -87,9 +87,10 @@ typedef struct {
                          (boundary fixed, non-affine cells; needs eps < 1 / (dim pi)).  The
                          stage operator, K y_n, the load and the initial interpolant then use
                          the mapping data w det J and w det J J^-1 J^-T at every Gauss point
-                         (Sec. 3.4: read once per cell for all stages of a launch), in native FP64
-                         with FP64 stage vectors (op_ff is ignored); the preconditioner keeps the
-                         Cartesian blocks of Eq. (irk:P) (flexible GMRES absorbs the difference) */
+                         (Sec. 3.4: read once per cell for all stages of a launch), with FP64
+                         stage vectors; op_ff then picks the operator's arithmetic (1 float-float,
+                         0 native FP64).  The preconditioner keeps the Cartesian blocks of
+                         Eq. (irk:P) (flexible GMRES absorbs the difference) */
 } irk_options;
 
 typedef struct {

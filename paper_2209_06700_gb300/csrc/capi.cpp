@@ -388,7 +388,9 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
       (o.deform > 0 && !deform_valid(mesh->dim, o.deform)))
     return Status::Err(IRK_EINVAL, "invalid options");
   if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
-  if (o.deform > 0) h->opt.op_ff = 0;  // the curved-mesh operator runs in FP64 on FP64 stage vectors
+  // curved mesh: FP64 stage vectors; op_ff picks the operator's arithmetic (float-float or FP64)
+  const int deform_ff = o.op_ff;
+  if (o.deform > 0) h->opt.op_ff = 0;
   h->dim = mesh->dim;
   h->N = mesh->cells_per_axis;
   h->k = degree;
@@ -477,6 +479,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
     h->dd.N = h->N;
     h->dd.k = degree;
     h->dd.max_ns = h->nslots;
+    h->dd.ff = deform_ff;
     h->dd.ncell = dg.ncell;
     h->dd.geo = geo;
     h->dd.eM = eM;

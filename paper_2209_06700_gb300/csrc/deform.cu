@@ -12,7 +12,10 @@
 // every node, the contributions of its (up to 2^d) cells in a fixed order (deterministic, no
 // atomics) and applies the output combination.  Launched with ns = 1 per stage, the same kernels
 // give the per-stage loop that reloads the mapping data Q times.
+#include <type_traits>
+
 #include "deform_kernels.h"
+#include "ffmath.cuh"
 #include "pdl.cuh"
 
 namespace irk {
@@ -20,15 +23,36 @@ namespace {
 
 constexpr int kCellThreads = 128;
 
-template <typename T, int K, int DIM>
+// 1D tables in the arithmetic type A: basis i (B) and its derivative (D) at Gauss point q
+template <typename A> struct Tab;
+template <> struct Tab<double> {
+  __device__ __forceinline__ static double b(const DeformParams& P, int q, int i) { return P.B[q][i]; }
+  __device__ __forceinline__ static double d(const DeformParams& P, int q, int i) { return P.D[q][i]; }
+  __device__ __forceinline__ static double c(double v, float, float) { return v; }
+};
+template <> struct Tab<float> {
+  __device__ __forceinline__ static float b(const DeformParams& P, int q, int i) { return P.Bh[q][i]; }
+  __device__ __forceinline__ static float d(const DeformParams& P, int q, int i) { return P.Dh[q][i]; }
+  __device__ __forceinline__ static float c(double, float h, float) { return h; }
+};
+template <> struct Tab<ff> {
+  __device__ __forceinline__ static ff b(const DeformParams& P, int q, int i) { return ff{P.Bh[q][i], P.Bl[q][i]}; }
+  __device__ __forceinline__ static ff d(const DeformParams& P, int q, int i) { return ff{P.Dh[q][i], P.Dl[q][i]}; }
+  __device__ __forceinline__ static ff c(double, float h, float l) { return ff{h, l}; }
+};
+
+// T: element type of the vectors and of the mapping data in memory; A: arithmetic (double, ff,
+// or float), also the element type of the cell-wise buffers.
+template <typename T, typename A, int K, int DIM>
 __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __restrict__ u, long long ld, int ns,
-                                                                   const T* __restrict__ geo, T* __restrict__ eM,
-                                                                   T* __restrict__ eK, const DeformParams P) {
+                                                                   const T* __restrict__ geo, A* __restrict__ eM,
+                                                                   A* __restrict__ eK, const DeformParams P) {
   dev::pdl_enter();
+  using dev::mad;
   constexpr int p = K + 1;
   constexpr int NP = (DIM == 3) ? p * p * p : p * p;
   constexpr int NF = 1 + DIM * (DIM + 1) / 2;
-  __shared__ T s[9][NP];
+  __shared__ A s[9][NP];
   const long long cell = blockIdx.x;
   const int N = P.N, n1 = P.n1;
   const int cx = (int)(cell % N), cy = (int)((cell / N) % N), cz = (DIM == 3) ? (int)(cell / ((long long)N * N)) : 0;
@@ -37,40 +61,41 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
   const int tx = t % p, ty = (t / p) % p, tz = (DIM == 3) ? t / (p * p) : 0;
   // this thread's node of the cell and its mapping data (read once for all stages)
   long long node = 0;
-  T g[NF];
+  A g[NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) g[f] = T(0);
+  for (int f = 0; f < NF; ++f) g[f] = dev::zero<A>();
   if (act) {
     node = (long long)(K * cx + tx) + (long long)n1 * ((K * cy + ty) + (long long)n1 * (K * cz + tz));
 #pragma unroll
-    for (int f = 0; f < NF; ++f) g[f] = geo[(cell * NF + f) * NP + t];
+    for (int f = 0; f < NF; ++f) g[f] = dev::convert<A>(geo[(cell * NF + f) * NP + t]);
   }
-  auto B = [&](int q, int i) { return (T)P.B[q][i]; };
-  auto D = [&](int q, int i) { return (T)P.D[q][i]; };
+  auto B = [&](int q, int i) { return Tab<A>::b(P, q, i); };
+  auto D = [&](int q, int i) { return Tab<A>::d(P, q, i); };
+  const A z = dev::zero<A>();
   for (int st = 0; st < ns; ++st) {
-    if (act) s[0][t] = u[st * ld + node];
+    if (act) s[0][t] = dev::convert<A>(u[st * ld + node]);
     __syncthreads();
     if constexpr (DIM == 3) {
       if (act) {  // x: (qx, j, l)
-        T a = 0, b = 0;
+        A a = z, b = z;
 #pragma unroll
         for (int i = 0; i < p; ++i) {
-          const T v = s[0][i + p * ty + p * p * tz];
-          a += B(tx, i) * v;
-          b += D(tx, i) * v;
+          const A v = s[0][i + p * ty + p * p * tz];
+          a = mad(a, B(tx, i), v);
+          b = mad(b, D(tx, i), v);
         }
         s[1][t] = a;
         s[2][t] = b;
       }
       __syncthreads();
       if (act) {  // y: (qx, qy, l)
-        T a = 0, b = 0, c = 0;
+        A a = z, b = z, c = z;
 #pragma unroll
         for (int j = 0; j < p; ++j) {
-          const T v1 = s[1][tx + p * j + p * p * tz], v2 = s[2][tx + p * j + p * p * tz];
-          a += B(ty, j) * v1;
-          b += D(ty, j) * v1;
-          c += B(ty, j) * v2;
+          const A v1 = s[1][tx + p * j + p * p * tz], v2 = s[2][tx + p * j + p * p * tz];
+          a = mad(a, B(ty, j), v1);
+          b = mad(b, D(ty, j), v1);
+          c = mad(c, B(ty, j), v2);
         }
         s[3][t] = a;  // B B u
         s[4][t] = b;  // B D_y u
@@ -78,31 +103,31 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
       }
       __syncthreads();
       if (act) {  // z: values and reference gradients at Gauss point t, then mass weight and metric
-        T U = 0, Ux = 0, Uy = 0, Uz = 0;
+        A U = z, Ux = z, Uy = z, Uz = z;
 #pragma unroll
         for (int l = 0; l < p; ++l) {
           const int o = tx + p * ty + p * p * l;
-          U += B(tz, l) * s[3][o];
-          Uz += D(tz, l) * s[3][o];
-          Uy += B(tz, l) * s[4][o];
-          Ux += B(tz, l) * s[5][o];
+          U = mad(U, B(tz, l), s[3][o]);
+          Uz = mad(Uz, D(tz, l), s[3][o]);
+          Uy = mad(Uy, B(tz, l), s[4][o]);
+          Ux = mad(Ux, B(tz, l), s[5][o]);
         }
         // g: w det J, then (xx, yy, zz, xy, xz, yz) of w det J J^-1 J^-T
-        s[6][t] = g[0] * U;
-        s[7][t] = g[1] * Ux + g[4] * Uy + g[5] * Uz;
-        s[8][t] = g[4] * Ux + g[2] * Uy + g[6] * Uz;
-        s[0][t] = g[5] * Ux + g[6] * Uy + g[3] * Uz;
+        s[6][t] = dev::mul(g[0], U);
+        s[7][t] = mad(mad(dev::mul(g[1], Ux), g[4], Uy), g[5], Uz);
+        s[8][t] = mad(mad(dev::mul(g[4], Ux), g[2], Uy), g[6], Uz);
+        s[0][t] = mad(mad(dev::mul(g[5], Ux), g[6], Uy), g[3], Uz);
       }
       __syncthreads();
       if (act) {  // z^T: (qx, qy, l)
-        T a = 0, b = 0, c = 0, e = 0;
+        A a = z, b = z, c = z, e = z;
 #pragma unroll
         for (int q = 0; q < p; ++q) {
           const int o = tx + p * ty + p * p * q;
-          a += B(q, tz) * s[6][o];
-          b += B(q, tz) * s[7][o];
-          c += B(q, tz) * s[8][o];
-          e += D(q, tz) * s[0][o];
+          a = mad(a, B(q, tz), s[6][o]);
+          b = mad(b, B(q, tz), s[7][o]);
+          c = mad(c, B(q, tz), s[8][o]);
+          e = mad(e, D(q, tz), s[0][o]);
         }
         s[1][t] = a;
         s[2][t] = b;
@@ -111,13 +136,13 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
       }
       __syncthreads();
       if (act) {  // y^T: (qx, j, l)
-        T a = 0, b = 0, c = 0;
+        A a = z, b = z, c = z;
 #pragma unroll
         for (int q = 0; q < p; ++q) {
           const int o = tx + p * q + p * p * tz;
-          a += B(q, ty) * s[1][o];
-          b += B(q, ty) * s[2][o];
-          c += D(q, ty) * s[3][o] + B(q, ty) * s[4][o];
+          a = mad(a, B(q, ty), s[1][o]);
+          b = mad(b, B(q, ty), s[2][o]);
+          c = mad(mad(c, D(q, ty), s[3][o]), B(q, ty), s[4][o]);
         }
         s[5][t] = a;
         s[6][t] = b;
@@ -125,12 +150,12 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
       }
       __syncthreads();
       if (act) {  // x^T: node (i, j, l)
-        T m = 0, k = 0;
+        A m = z, k = z;
 #pragma unroll
         for (int q = 0; q < p; ++q) {
           const int o = q + p * ty + p * p * tz;
-          m += B(q, tx) * s[5][o];
-          k += D(q, tx) * s[6][o] + B(q, tx) * s[7][o];
+          m = mad(m, B(q, tx), s[5][o]);
+          k = mad(mad(k, D(q, tx), s[6][o]), B(q, tx), s[7][o]);
         }
         const long long e = (cell * ns + st) * NP + t;
         eM[e] = m;
@@ -138,39 +163,39 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
       }
     } else {
       if (act) {  // x: (qx, j)
-        T a = 0, b = 0;
+        A a = z, b = z;
 #pragma unroll
         for (int i = 0; i < p; ++i) {
-          const T v = s[0][i + p * ty];
-          a += B(tx, i) * v;
-          b += D(tx, i) * v;
+          const A v = s[0][i + p * ty];
+          a = mad(a, B(tx, i), v);
+          b = mad(b, D(tx, i), v);
         }
         s[1][t] = a;
         s[2][t] = b;
       }
       __syncthreads();
       if (act) {  // y: Gauss point (qx, qy); g: w det J, then (xx, yy, xy)
-        T U = 0, Ux = 0, Uy = 0;
+        A U = z, Ux = z, Uy = z;
 #pragma unroll
         for (int j = 0; j < p; ++j) {
           const int o = tx + p * j;
-          U += B(ty, j) * s[1][o];
-          Uy += D(ty, j) * s[1][o];
-          Ux += B(ty, j) * s[2][o];
+          U = mad(U, B(ty, j), s[1][o]);
+          Uy = mad(Uy, D(ty, j), s[1][o]);
+          Ux = mad(Ux, B(ty, j), s[2][o]);
         }
-        s[3][t] = g[0] * U;
-        s[4][t] = g[1] * Ux + g[3] * Uy;
-        s[5][t] = g[3] * Ux + g[2] * Uy;
+        s[3][t] = dev::mul(g[0], U);
+        s[4][t] = mad(dev::mul(g[1], Ux), g[3], Uy);
+        s[5][t] = mad(dev::mul(g[3], Ux), g[2], Uy);
       }
       __syncthreads();
       if (act) {  // y^T: (qx, j)
-        T a = 0, b = 0, c = 0;
+        A a = z, b = z, c = z;
 #pragma unroll
         for (int q = 0; q < p; ++q) {
           const int o = tx + p * q;
-          a += B(q, ty) * s[3][o];
-          b += B(q, ty) * s[4][o];
-          c += D(q, ty) * s[5][o];
+          a = mad(a, B(q, ty), s[3][o]);
+          b = mad(b, B(q, ty), s[4][o]);
+          c = mad(c, D(q, ty), s[5][o]);
         }
         s[6][t] = a;
         s[7][t] = b;
@@ -178,12 +203,12 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
       }
       __syncthreads();
       if (act) {  // x^T: node (i, j)
-        T m = 0, k = 0;
+        A m = z, k = z;
 #pragma unroll
         for (int q = 0; q < p; ++q) {
           const int o = q + p * ty;
-          m += B(q, tx) * s[6][o];
-          k += D(q, tx) * s[7][o] + B(q, tx) * s[8][o];
+          m = mad(m, B(q, tx), s[6][o]);
+          k = mad(mad(k, D(q, tx), s[7][o]), B(q, tx), s[8][o]);
         }
         const long long e = (cell * ns + st) * NP + t;
         eM[e] = m;
@@ -195,8 +220,8 @@ __global__ void __launch_bounds__(kCellThreads) deform_cell_kernel(const T* __re
 }
 
 // Node-wise sum of the cell contributions (fixed order: z, y, x candidates), then out.
-template <typename T, int K, int DIM, int EPI>
-__global__ void deform_gather_kernel(const T* __restrict__ eM, const T* __restrict__ eK, int ns, long long ld,
+template <typename T, typename A, int K, int DIM, int EPI>
+__global__ void deform_gather_kernel(const A* __restrict__ eM, const A* __restrict__ eK, int ns, long long ld,
                                      T* __restrict__ out, T* __restrict__ out2, const DeformParams P) {
   dev::pdl_enter();
   constexpr int p = K + 1;
@@ -207,7 +232,7 @@ __global__ void deform_gather_kernel(const T* __restrict__ eM, const T* __restri
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(e % n1), iy = (int)((e / n1) % n1), iz = (DIM == 3) ? (int)(e / ((long long)n1 * n1)) : 1;
     const bool inner = ix > 0 && ix < n1 - 1 && iy > 0 && iy < n1 - 1 && (DIM == 2 || (iz > 0 && iz < n1 - 1));
-    T sm = 0, sk = 0;
+    A sm = dev::zero<A>(), sk = dev::zero<A>();
     if (inner) {
       int c[3][2], r[3][2], nc[3];
       const int idx[3] = {ix, iy, iz};
@@ -234,32 +259,54 @@ __global__ void deform_gather_kernel(const T* __restrict__ eM, const T* __restri
               loc += p * p * r[2][bz];
             }
             const long long o = (cell * ns + st) * NP + loc;
-            sm += eM[o];
-            sk += eK[o];
+            sm = dev::add(sm, eM[o]);
+            sk = dev::add(sk, eK[o]);
           }
     }
     if (EPI == EPI_DUAL) {
-      out[st * ld + e] = sm;
-      out2[st * ld + e] = sk;
+      out[st * ld + e] = dev::convert<T>(sm);
+      out2[st * ld + e] = dev::convert<T>(sk);
     } else {
-      out[st * ld + e] = (T)P.cm[st] * sm + (T)P.ck[st] * sk;
+      const A cm = Tab<A>::c(P.cm[st], P.cmh[st], P.cml[st]), ck = Tab<A>::c(P.ck[st], P.ckh[st], P.ckl[st]);
+      out[st * ld + e] = dev::convert<T>(dev::mad(dev::mul(cm, sm), ck, sk));
     }
   }
 }
 
-template <typename T, int K, int DIM>
+template <typename T, typename A, int K, int DIM>
 cudaError_t launch_kd(const DeformDevice<T>& G, int ns, const T* u, long long ld, int epi, const DeformParams& P,
                       T* out, T* out2, cudaStream_t st) {
-  launch_pdl(deform_cell_kernel<T, K, DIM>, (unsigned)G.ncell, kCellThreads, 0, st, u, ld, ns, G.geo, G.eM, G.eK, P);
+  A* eM = reinterpret_cast<A*>(G.eM);
+  A* eK = reinterpret_cast<A*>(G.eK);
+  launch_pdl(deform_cell_kernel<T, A, K, DIM>, (unsigned)G.ncell, kCellThreads, 0, st, u, ld, ns, G.geo, eM, eK, P);
   const long long n = (DIM == 3) ? (long long)P.n1 * P.n1 * P.n1 : (long long)P.n1 * P.n1;
   long long nb = (n + 255) / 256;
   if (nb > 152 * 16) nb = 152 * 16;
   dim3 grid((unsigned)nb, ns);
   if (epi == EPI_DUAL)
-    launch_pdl(deform_gather_kernel<T, K, DIM, EPI_DUAL>, grid, 256, 0, st, G.eM, G.eK, ns, ld, out, out2, P);
+    launch_pdl(deform_gather_kernel<T, A, K, DIM, EPI_DUAL>, grid, 256, 0, st, eM, eK, ns, ld, out, out2, P);
   else
-    launch_pdl(deform_gather_kernel<T, K, DIM, EPI_STORE>, grid, 256, 0, st, G.eM, G.eK, ns, ld, out, out2, P);
+    launch_pdl(deform_gather_kernel<T, A, K, DIM, EPI_STORE>, grid, 256, 0, st, eM, eK, ns, ld, out, out2, P);
   return cudaGetLastError();
+}
+
+template <typename T, typename A>
+cudaError_t launch_a(const DeformDevice<T>& G, int ns, const T* u, long long ld, int epi, const DeformParams& P,
+                     T* out, T* out2, cudaStream_t st) {
+#define IRK_DK(KK)                                                                                  \
+  case KK:                                                                                          \
+    return (G.dim == 3) ? launch_kd<T, A, KK, 3>(G, ns, u, ld, epi, P, out, out2, st)               \
+                        : launch_kd<T, A, KK, 2>(G, ns, u, ld, epi, P, out, out2, st);
+  switch (G.k) {
+    IRK_DK(1) IRK_DK(2) IRK_DK(3) IRK_DK(4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef IRK_DK
+}
+
+void split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
 }
 
 }  // namespace
@@ -278,20 +325,21 @@ cudaError_t launch_deformed(const DeformDevice<T>& G, int ns, const T* u, long l
     for (int i = 0; i < p; ++i) {
       P.B[q][i] = G.B[q * p + i];
       P.D[q][i] = G.D[q * p + i];
+      split(P.B[q][i], P.Bh[q][i], P.Bl[q][i]);
+      split(P.D[q][i], P.Dh[q][i], P.Dl[q][i]);
     }
   for (int s = 0; s < kMaxStages; ++s) {
     P.cm[s] = (epi == EPI_STORE && s < ns) ? cm[s] : 0.0;
     P.ck[s] = (epi == EPI_STORE && s < ns) ? ck[s] : 0.0;
+    split(P.cm[s], P.cmh[s], P.cml[s]);
+    split(P.ck[s], P.ckh[s], P.ckl[s]);
   }
-#define IRK_DK(KK)                                                                                  \
-  case KK:                                                                                          \
-    return (G.dim == 3) ? launch_kd<T, KK, 3>(G, ns, u, ld, epi, P, out, out2, st)                  \
-                        : launch_kd<T, KK, 2>(G, ns, u, ld, epi, P, out, out2, st);
-  switch (G.k) {
-    IRK_DK(1) IRK_DK(2) IRK_DK(3) IRK_DK(4)
-    default: return cudaErrorInvalidValue;
+  if constexpr (std::is_same<T, float>::value) {
+    return launch_a<float, float>(G, ns, u, ld, epi, P, out, out2, st);
+  } else {
+    return G.ff ? launch_a<double, ff>(G, ns, u, ld, epi, P, out, out2, st)
+                : launch_a<double, double>(G, ns, u, ld, epi, P, out, out2, st);
   }
-#undef IRK_DK
 }
 
 template cudaError_t launch_deformed<double>(const DeformDevice<double>&, int, const double*, long long, int,

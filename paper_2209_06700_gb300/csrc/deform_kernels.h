@@ -11,13 +11,18 @@ struct DeformParams {
   double B[kMaxDeg + 1][kMaxDeg + 1];  // basis i at Gauss point q, [q][i] (unit cell)
   double D[kMaxDeg + 1][kMaxDeg + 1];  // its derivative
   double cm[kMaxStages], ck[kMaxStages];
+  float Bh[kMaxDeg + 1][kMaxDeg + 1], Bl[kMaxDeg + 1][kMaxDeg + 1];  // hi + lo splits (ff, FP32)
+  float Dh[kMaxDeg + 1][kMaxDeg + 1], Dl[kMaxDeg + 1][kMaxDeg + 1];
+  float cmh[kMaxStages], cml[kMaxStages], ckh[kMaxStages], ckl[kMaxStages];
 };
 
-// Device data of one curved mesh: mapping data [cell][1 + d(d+1)/2][(k+1)^d] and the cell-wise
-// result buffers eM, eK [cell][max_ns][(k+1)^d] (element type T).  B, D: host tables [q][i].
+// Device data of one curved mesh: mapping data [cell][1 + d(d+1)/2][(k+1)^d] (element type T)
+// and the cell-wise result buffers eM, eK [cell][max_ns][(k+1)^d] (8-byte elements for T = double:
+// FP64 or ff, 4-byte for T = float).  B, D: host tables [q][i].
 template <typename T>
 struct DeformDevice {
   int dim = 0, N = 0, k = 0, max_ns = 0;
+  int ff = 0;                     // T = double: 1 float-float arithmetic (FP32 pipe), 0 native FP64
   long long ncell = 0;
   const T* geo = nullptr;
   T* eM = nullptr;

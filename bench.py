@@ -358,11 +358,16 @@ def main():
     ap.add_argument("--cheb-degree", type=int, default=None)
     ap.add_argument("--smoothing-range", type=float, default=None)
     ap.add_argument("--eig-safety", type=float, default=None)
+    ap.add_argument("--curved-only", action="store_true",
+                    help="run only the curved-mesh measurement (profiler captures of its operator)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.cells is not None and args.cells != w.cells:
         import dataclasses
         w = dataclasses.replace(w, name=f"heat{w.dim}d_k{w.degree}_n{args.cells}_q{w.Q}", cells=args.cells)
+    if args.curved_only:
+        print(json.dumps({"curved_mesh": curved_mesh_workload(w)}))
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return

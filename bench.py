@@ -42,6 +42,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def slowest_rank_ms(ms_total, dist, device):
+    """Replicas: the job's timed region is the slowest rank's (max over ranks; one rank: itself)."""
+    if dist is None:
+        return ms_total
+    import torch
+    tt = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, ms_step):
+    """Whole-job stage-DoF/s: every rank advances its own replica by units_per_rank per step."""
+    return world * units_per_rank / (ms_step / 1e3)
+
+
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, profiling recipe's table)
 FF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 15 * 2 / 1e12   # float-float multiply-adds on the FP32 pipe
 
@@ -457,13 +472,10 @@ def main():
         if i == dom:
             dom_ms, dom_n = ms.value, nt.value
     lib.irk_profile(s.h, 0)
-    if dist:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = slowest_rank_ms(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
     units = w.Q * w.n_interior
-    value = world * units / (ms_step / 1e3)
+    value = job_throughput(units, world, ms_step)
 
     # end to end through the C ABI with host buffers: H2D of y_n, the step, D2H of y_{n+1}
     y_host = torch.empty(s.n, dtype=torch.float64, pin_memory=True)

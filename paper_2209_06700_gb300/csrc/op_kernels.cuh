@@ -120,25 +120,6 @@ __device__ __forceinline__ void ytaps_dispatch(int r, const T* col, int stride, 
   }
 }
 
-// One staged row of y taps (slots lane, lane + 32, ... < SL) with the tap row R fixed for the loop.
-template <typename T, int K, int SL, int R>
-__device__ __forceinline__ void yrow(const T* colbase, const OpParams<T>& P, T* gout, T* hout, int lane) {
-  for (int sl = lane; sl < SL; sl += 32) {
-    T g = zero<T>(), h = zero<T>();
-    ytaps<T, K, R>(colbase + sl, SL, P, g, h);
-    gout[sl] = g;
-    hout[sl] = h;
-  }
-}
-template <typename T, int K, int SL, int R = 0>
-__device__ __forceinline__ void yrow_dispatch(int r, const T* colbase, const OpParams<T>& P, T* gout, T* hout,
-                                              int lane) {
-  if constexpr (R < K) {
-    if (r == R) yrow<T, K, SL, R>(colbase, P, gout, hout, lane);
-    else yrow_dispatch<T, K, SL, R + 1>(r, colbase, P, gout, hout, lane);
-  }
-}
-
 // Cell-wise x contraction for one lane's cell (staged columns cl, cl+1 of slots [m][cell]).
 // MODE3: g = My u, h = Ky u given -> R = Mx g, Pp = Kx g + Mx h.  MODE2: u given -> R = Mx u, Pp = Kx u.
 template <typename T, int K, bool MODE3, int CW>

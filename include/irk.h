@@ -269,6 +269,13 @@ irk_status irk_mg_prolongate(irk_handle h, int level, const void* e_coarse, void
 irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x);
 irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x);
 
+/* Hierarchy the irk_mg_* calls and irk_get_cheb_interval act on: 0 the LU blocks (default);
+ * 1 + i the DIAG variant's block i in irk_get_tableau(J) order: a real block gamma M + tau K
+ * (one vector); a 2x2 pair with pair_precond = 0 the PRESB block (alpha + beta) M + tau K (one
+ * vector); a 2x2 pair with pair_precond = 1 the coupled system of Sec. 6 (two vectors
+ * [2][stride]).  IRK_EINVAL for a block the handle does not have. */
+irk_status irk_mg_select(irk_handle h, int which);
+
 /* The generalized mat-vec of Sec. 2, v = (D (x) I) u, D host row-major
  * nout x nin, u [nin][stride], v [nout][stride], FP64. */
 irk_status irk_stage_combine(irk_handle h, const double* u, int nin, double* v, int nout,

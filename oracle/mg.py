@@ -26,6 +26,10 @@ global-coarsening GMG):
 * one V(m, m)-cycle: pre-smooth from zero, residual, restrict, recurse,
   prolongate and add, post-smooth.
 
+The coupled 2x2 V-cycle (``CoupledVCycle``, Sec. 6) is pinned by: with beta = 0 it is the
+scalar V-cycle on each component; its nodal 2x2 Jacobi inverse inverts the nodal blocks; as a
+stationary iteration it contracts the error of the coupled system.
+
 Pinned by tests/test_oracle_mg.py: the Chebyshev error-propagation
 polynomial equals T_m((theta - mu)/delta) / T_m(theta/delta) on every
 eigenpair of D^{-1}A; the prolongation reproduces degree-k polynomials
@@ -160,6 +164,102 @@ class VCycle:
         x = x + self.P[level] @ ec
         x = chebyshev(L["A"], L["D"], b, x, self.m, L["lo"], L["hi"], L["bm"])
         return x
+
+
+def coupled_level(d, N, k, alpha, beta, tau):
+    """The 2x2 block of Sec. 6 (Eq. complex:twobytwo) on one level, for x = (x0, x1):
+    [[alpha M + tau K, -beta M], [beta M, alpha M + tau K]], rediscretised, boundary rows and
+    columns zeroed (dense, small N); with its nodal 2x2 Jacobi inverse (reading: the paper's
+    point-Jacobi, applied to the coupled system, takes a node with its two components as the
+    point)."""
+    mesh = Mesh(d, N, k)
+    M, K = assemble(mesh)
+    M, K = M.toarray(), K.toarray()
+    bm = mesh.boundary_mask()
+    for X in (M, K):
+        X[bm, :] = 0.0
+        X[:, bm] = 0.0
+    A = alpha * M + tau * K
+    C = np.block([[A, -beta * M], [beta * M, A]])
+    da = np.diag(A).copy()
+    dm = beta * np.diag(M)
+    da[bm] = 1.0
+    dm[bm] = 0.0
+    n = mesh.n
+
+    def dinv(r):
+        """z = blockdiag([[da_i, -dm_i], [dm_i, da_i]])^{-1} r, node by node."""
+        r0, r1 = r[:n], r[n:]
+        den = da * da + dm * dm
+        z = np.concatenate([(da * r0 + dm * r1) / den, (da * r1 - dm * r0) / den])
+        z[np.concatenate([bm, bm])] = 0.0
+        return z
+
+    return C, dinv, np.concatenate([bm, bm])
+
+
+def chebyshev_op(A, dinv, b, x0, m, lo, hi, bmask):
+    """The Chebyshev recurrence of ``chebyshev`` with a general inverse-diagonal map dinv."""
+    theta = 0.5 * (hi + lo)
+    delta = 0.5 * (hi - lo)
+    x = x0.copy()
+    r = dinv(b - A @ x)
+    r[bmask] = 0.0
+    dd = r / theta
+    rho = delta / theta
+    x = x + dd
+    for _ in range(1, m):
+        rho_new = 1.0 / (2.0 * theta / delta - rho)
+        r = dinv(b - A @ x)
+        r[bmask] = 0.0
+        dd = rho_new * rho * dd + (2.0 * rho_new / delta) * r
+        x = x + dd
+        rho = rho_new
+    return x
+
+
+class CoupledVCycle:
+    """One V(m, m)-cycle on the coupled 2x2 system itself (Sec. 6: GMG applied directly to
+    Eq. complex:twobytwo, the paper's IRK-GMG): per level the rediscretised coupled operator,
+    Chebyshev around nodal 2x2 block Jacobi over the interval ``bounds[level]``, the Q_k
+    prolongation per component, the coarsest coupled system solved exactly (FP64, dense)."""
+
+    def __init__(self, d, N, k, alpha, beta, tau, m, bounds):
+        self.sizes = level_sizes(N, k)
+        self.levels = []
+        for li, Nl in enumerate(self.sizes):
+            C, dinv, bm = coupled_level(d, Nl, k, alpha, beta, tau)
+            lo, hi = bounds[li] if li < len(bounds) else (1.0, 2.0)
+            self.levels.append(dict(N=Nl, A=C, dinv=dinv, bm=bm, lo=lo, hi=hi))
+        self.P = [prolongation(d, self.sizes[i + 1], k) for i in range(len(self.sizes) - 1)]
+        c = self.levels[-1]
+        keep = ~c["bm"]
+        self.coarse_keep = keep
+        self.coarse_inv = np.linalg.inv(c["A"][np.ix_(keep, keep)])
+        self.m = m
+
+    def _P2(self, level, e):
+        P = self.P[level]
+        nc = P.shape[1]
+        return np.concatenate([P @ e[:nc], P @ e[nc:]])
+
+    def _R2(self, level, r):
+        P = self.P[level]
+        nf = P.shape[0]
+        return np.concatenate([P.T @ r[:nf], P.T @ r[nf:]])
+
+    def apply(self, b, level=0):
+        if level == len(self.levels) - 1:
+            x = np.zeros_like(b)
+            x[self.coarse_keep] = self.coarse_inv @ b[self.coarse_keep]
+            return x
+        L = self.levels[level]
+        x = chebyshev_op(L["A"], L["dinv"], b, np.zeros_like(b), self.m, L["lo"], L["hi"], L["bm"])
+        r = b - L["A"] @ x
+        r[L["bm"]] = 0.0
+        ec = self.apply(self._R2(level, r), level + 1)
+        x = x + self._P2(level, ec)
+        return chebyshev_op(L["A"], L["dinv"], b, x, self.m, L["lo"], L["hi"], L["bm"])
 
 
 def presb_factors(Kp, Mp):

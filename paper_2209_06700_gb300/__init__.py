@@ -186,6 +186,9 @@ class Solver:
     def mg_coarse_solve(self, b, x):
         check(lib().irk_mg_coarse_solve(self.h, _ptr(b), _ptr(x)), self.h)
 
+    def mg_select(self, which):
+        check(lib().irk_mg_select(self.h, int(which)), self.h)
+
     def mg_vcycle(self, level, b, x):
         check(lib().irk_mg_vcycle(self.h, level, _ptr(b), _ptr(x)), self.h)
 

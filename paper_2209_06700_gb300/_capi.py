@@ -91,6 +91,7 @@ SIGNATURES = {
     "irk_mg_prolongate": (_I, [_H, _I, _P, _P]),
     "irk_mg_coarse_solve": (_I, [_H, _P, _P]),
     "irk_mg_vcycle": (_I, [_H, _I, _P, _P]),
+    "irk_mg_select": (_I, [_H, _I]),
     "irk_stage_combine": (_I, [_H, _P, _I, _P, _I, ctypes.POINTER(_D)]),
     "irk_synchronize": (_I, [_H]),
     "irk_profile": (_I, [_H, ctypes.c_uint]),

@@ -47,6 +47,7 @@ struct irk_problem {
   double *Ky = nullptr, *rhs = nullptr, *kst = nullptr, *Mu = nullptr, *Ku = nullptr, *G1 = nullptr,
          *x1d = nullptr, *tq = nullptr;
   int nslots = 0;                                   // stage slots of Mu/Ku
+  int mg_sel = 0;                                   // hierarchy of the irk_mg_* entry points (irk_mg_select)
   // curved mesh (opt.deform > 0): mapping data, cell-wise buffers, full load vector
   bool deformed = false;
   DeformGeom dgeom;
@@ -536,14 +537,15 @@ irk_status guarded(irk_problem* h, F&& f) {
   }
 }
 
-MGBase* lu_mg(irk_problem* h) { return h->mg.get(); }
+// the hierarchy the irk_mg_* entry points act on: the LU blocks, or one DIAG block (irk_mg_select)
+MGBase* lu_mg(irk_problem* h) { return h->mg_sel == 0 ? h->mg.get() : h->mg_diag[h->mg_sel - 1].get(); }
 
 }  // namespace
 
 // Restriction with caller-provided scratch, for the allocation-free entry point (noalloc.cu).
 irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, void* scratch, size_t bytes) {
   return guarded(h, [&]() -> Status {
-    if (!r || !bc || !scratch || level < 0 || level + 1 >= h->mg->levels())
+    if (!r || !bc || !scratch || level < 0 || level + 1 >= lu_mg(h)->levels())
       return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->restrict_in_scratch(level, r, bc, scratch, bytes, h->st);
   });
@@ -738,9 +740,10 @@ irk_status irk_get_tableau(irk_handle h, int which, double* out) {
 
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out) {
   return guarded(h, [&]() -> Status {
-    if (!out || level < 0 || level + 1 >= h->mg->levels() || block < 0 || block >= h->Q)
+    const int nb = h->mg_sel == 0 ? h->Q : (h->tab.blocks[h->mg_sel - 1].pair && h->opt.pair_precond == 1 ? 2 : 1);
+    if (!out || level < 0 || level + 1 >= lu_mg(h)->levels() || block < 0 || block >= nb)
       return Status::Err(IRK_EINVAL, "bad level/block");
-    h->mg->interval(level, block, &out[0], &out[1]);
+    lu_mg(h)->interval(level, block, &out[0], &out[1]);
     return Status::Ok();
   });
 }
@@ -794,25 +797,25 @@ long long irk_level_stride(irk_handle h, int level) {
 
 irk_status irk_mg_smooth(irk_handle h, int level, const void* b, void* x, int x_is_zero) {
   return guarded(h, [&]() -> Status {
-    if (!b || !x || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (!b || !x || level < 0 || level + 1 >= lu_mg(h)->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->smooth(level, b, x, x_is_zero, h->st);
   });
 }
 irk_status irk_mg_residual(irk_handle h, int level, const void* b, const void* x, void* r) {
   return guarded(h, [&]() -> Status {
-    if (!b || !x || !r || level < 0 || level >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (!b || !x || !r || level < 0 || level >= lu_mg(h)->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->residual(level, b, x, r, h->st);
   });
 }
 irk_status irk_mg_restrict(irk_handle h, int level, const void* r, void* bc) {
   return guarded(h, [&]() -> Status {
-    if (!r || !bc || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (!r || !bc || level < 0 || level + 1 >= lu_mg(h)->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->restrict_to(level, r, bc, h->st);
   });
 }
 irk_status irk_mg_prolongate(irk_handle h, int level, const void* ec, void* x) {
   return guarded(h, [&]() -> Status {
-    if (!ec || !x || level < 0 || level + 1 >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (!ec || !x || level < 0 || level + 1 >= lu_mg(h)->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->prolongate_add(level, ec, x, h->st);
   });
 }
@@ -822,9 +825,17 @@ irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x) {
     return lu_mg(h)->coarse_solve(b, x, h->st);
   });
 }
+irk_status irk_mg_select(irk_handle h, int which) {
+  return guarded(h, [&]() -> Status {
+    if (which < 0 || which > (int)h->mg_diag.size()) return Status::Err(IRK_EINVAL, "no such multigrid hierarchy");
+    h->mg_sel = which;
+    return Status::Ok();
+  });
+}
+
 irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x) {
   return guarded(h, [&]() -> Status {
-    if (!b || !x || level < 0 || level >= h->mg->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (!b || !x || level < 0 || level >= lu_mg(h)->levels()) return Status::Err(IRK_EINVAL, "bad arguments");
     return lu_mg(h)->vcycle_io(level, b, x, h->st);
   });
 }

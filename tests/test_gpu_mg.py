@@ -154,3 +154,27 @@ def test_coarse_solve_fast_diagonalisation(dim, N, k, Q, prec, dt):
             x[keep] = np.linalg.solve(A[np.ix_(keep, keep)], b[i][keep])
             ref.append(x)
         assert rel_err(got, np.stack(ref)) <= (1e-11 if prec == 64 else 2e-6)
+
+
+@pytest.mark.parametrize("dim,N,k", [(2, 8, 2), (3, 4, 2), (3, 4, 3)])
+@pytest.mark.parametrize("prec,dt,tol", PREC)
+def test_coupled_vcycle_matches_oracle(dim, N, k, prec, dt, tol):
+    """One V-cycle on the coupled 2x2 block itself (pair_precond=1, Sec. 6: GMG applied directly to
+    Eq. complex:twobytwo) against the oracle's CoupledVCycle on the library's Chebyshev intervals."""
+    from oracle.mg import CoupledVCycle
+    from oracle.tableau import real_jordan
+    Q, tau, m = 2, 1e-2, 3
+    _, _, blocks = real_jordan(lu_preconditioner_factors(Q)["Ainv"])
+    _, alpha, beta = blocks[0]
+    n1 = k * N + 1
+    n = n1 ** dim
+    b = zero_boundary(uniform_vectors((2, n), seed=8), dim, n1)
+    with pkg.Solver(dim, N, k, Q, tau, variant=pkg.IRK_VARIANT_DIAG, pair_precond=1, mg_precision=prec,
+                    cheb_degree=m) as s:
+        s.mg_select(1)
+        bounds = [s.cheb_interval(lv, 0) for lv in range(len(level_sizes(N, k)) - 1)]
+        xd = s.stage_vector(ns=2, dtype=dt)
+        s.mg_vcycle(0, to_dev(s, b, dt), xd)
+        got = from_dev(xd, n)
+    ref = CoupledVCycle(dim, N, k, alpha, beta, tau, m, bounds).apply(b.reshape(-1)).reshape(2, n)
+    assert rel_err(got, ref) <= tol

@@ -108,3 +108,61 @@ def test_presb_factorisation_and_bound():
     f, g = rng.standard_normal(n), rng.standard_normal(n)
     u, v = presb_apply(lambda r: np.linalg.solve(H, r), lambda w: Mp @ w, f, g)
     np.testing.assert_allclose(P @ np.concatenate([u, v]), np.concatenate([f, g]), atol=1e-11)
+
+
+# ---- the coupled 2x2 V-cycle (Sec. 6, GMG applied directly to Eq. complex:twobytwo)
+
+def _bounds(d, N, k, lam, tau):
+    from oracle.mg import max_eig_DinvA
+    out = []
+    for Nl in level_sizes(N, k):
+        A, bm = level_operator(d, Nl, k, lam, tau)
+        hi = 1.2 * max_eig_DinvA(A, jacobi_diag(A, bm), bm)
+        out.append((hi / 20.0, hi))
+    return out
+
+
+def test_coupled_vcycle_without_coupling_is_two_scalar_vcycles():
+    from oracle.mg import CoupledVCycle, VCycle
+    d, N, k, alpha, tau = 2, 8, 2, 2.7, 1e-2
+    bounds = _bounds(d, N, k, alpha, tau)
+    cv = CoupledVCycle(d, N, k, alpha, 0.0, tau, 3, bounds)
+    sv = VCycle(d, N, k, alpha, tau, 3, bounds=bounds)
+    rng = np.random.default_rng(3)
+    n = (k * N + 1) ** d
+    b = rng.uniform(-1, 1, 2 * n)
+    b[np.concatenate([cv.levels[0]["bm"][:n]] * 2)] = 0.0
+    got = cv.apply(b)
+    ref = np.concatenate([sv.apply(b[:n]), sv.apply(b[n:])])
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_coupled_nodal_jacobi_inverts_the_nodal_blocks():
+    from oracle.mg import coupled_level
+    d, N, k = 2, 4, 3
+    C, dinv, bm = coupled_level(d, N, k, 2.0, 3.0, 1e-2)
+    n = C.shape[0] // 2
+    rng = np.random.default_rng(4)
+    z = rng.uniform(-1, 1, 2 * n)
+    z[bm] = 0.0
+    # nodal blocks of C: [[C[i,i], C[i,n+i]], [C[n+i,i], C[n+i,n+i]]]
+    i = np.arange(n)
+    r0 = C[i, i] * z[:n] + C[i, n + i] * z[n:]
+    r1 = C[n + i, i] * z[:n] + C[n + i, n + i] * z[n:]
+    r = np.concatenate([r0, r1])
+    r[bm] = 0.0
+    assert np.abs(dinv(r) - z).max() <= 1e-12 * np.abs(z).max()
+
+
+def test_coupled_vcycle_contracts_the_error():
+    from oracle.mg import CoupledVCycle
+    d, N, k, alpha, beta, tau = 2, 8, 2, 2.68, 3.05, 1e-3
+    cv = CoupledVCycle(d, N, k, alpha, beta, tau, 3, _bounds(d, N, k, alpha, tau))
+    A, bm = cv.levels[0]["A"], cv.levels[0]["bm"]
+    rng = np.random.default_rng(5)
+    e = rng.uniform(-1, 1, A.shape[0])
+    e[bm] = 0.0
+    e0 = np.linalg.norm(e)
+    for _ in range(5):  # e <- (I - B A) e
+        e = e - cv.apply(A @ e)
+    assert np.linalg.norm(e) <= 0.5 ** 5 * e0

@@ -71,9 +71,10 @@ class DeformedMesh(Mesh):
         """Physical node coordinates Phi(xi_node), (n, d)."""
         return phi_map(super().node_coords(), self.eps)
 
-    def quadrature(self, npts=None):
+    def quadrature(self, npts=None, cells=None):
         """Reference points xi (ncell, nq, d), weights w_q h^d (nq,), basis values (nq, nb) and
-        reference gradients (nq, nb, d) in the cell coordinate xi (not the unit-cell one)."""
+        reference gradients (nq, nb, d) in the cell coordinate xi (not the unit-cell one); for the
+        listed cell indices only (x fastest) when ``cells`` is given."""
         d, N, k, p, h = self.d, self.N, self.k, self.p, self.h
         npts = p if npts is None else npts
         xq, wq = gauss_rule(npts)
@@ -90,14 +91,16 @@ class DeformedMesh(Mesh):
             phi *= Va
             for g in range(d):
                 grad[:, :, g] *= Da if g == a else Va
-        cells = np.array(np.unravel_index(np.arange(N ** d), (N,) * d, order="F")).T
-        xi = (cells[:, None, :] + xq[qidx][None, :, :]) * h
+        ids = np.arange(N ** d) if cells is None else np.asarray(cells)
+        cidx = np.array(np.unravel_index(ids, (N,) * d, order="F")).T
+        xi = (cidx[:, None, :] + xq[qidx][None, :, :]) * h
         return xi, w * h ** d, phi, grad
 
 
-def element_matrices_deformed(mesh):
-    """Per-cell dense mass and stiffness matrices (ncell, nb, nb) by direct quadrature."""
-    xi, w, phi, grad = mesh.quadrature()
+def element_matrices_deformed(mesh, cells=None):
+    """Per-cell dense mass and stiffness matrices (ncell, nb, nb) by direct quadrature (all cells,
+    or the listed cell indices)."""
+    xi, w, phi, grad = mesh.quadrature(cells=cells)
     J = jacobian(xi, mesh.eps)                      # (ncell, nq, d, d)
     det = np.linalg.det(J)
     Jinv = np.linalg.inv(J)

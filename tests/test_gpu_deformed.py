@@ -117,3 +117,43 @@ def test_step(dim, N, k, Q, tau, variant, op_ff):
 def test_invalid_amplitude_is_refused():
     with pytest.raises(pkg.IrkError):
         pkg.Solver(3, 4, 2, 2, 1e-2, deform=0.2)   # eps d pi >= 1: the map folds
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op_ff", [1, 0])
+def test_full_size_sampled_nodes(op_ff):
+    """The bench's curved workload (3D, degree 4, 32^3 cells, Q = 3, eps = 0.05): M u and K u of
+    every stage at 150 random interior nodes against the oracle's dense matrices of the cells
+    around them (the full operator is out of reach of the dense oracle at this size)."""
+    from oracle.deformed import DeformedMesh, element_matrices_deformed
+    from synthetic import HEAT3D_K4_N32_Q3 as w
+    eps = 0.05
+    mesh = DeformedMesh(w.dim, w.cells, w.degree, eps)
+    n1, n, Q, k, N = w.n1, w.n1 ** 3, w.Q, w.degree, w.cells
+    u = _inputs(Q, 3, n1, seed=13)
+    with pkg.Solver(3, N, k, Q, w.tau, deform=eps, op_ff=op_ff) as s:
+        ud = to_dev(s, u)
+        vm, vk = torch.zeros_like(ud), torch.zeros_like(ud)
+        s.apply_op(ud, vm, np.eye(Q), np.zeros((Q, Q)))
+        s.apply_op(ud, vk, np.zeros((Q, Q)), np.eye(Q))
+        gm, gk = from_dev(vm, n), from_dev(vk, n)
+    rng = np.random.default_rng(17)
+    pts = rng.integers(1, n1 - 1, size=(150, 3))
+    around = []
+    for p in pts:   # the cells whose closure holds the node, and the node's local index in each
+        cand = [[c for c in (i // k - 1, i // k) if 0 <= c < N and k * c <= i <= k * (c + 1)] for i in p]
+        around.append([(cx + N * (cy + N * cz), (p[0] - k * cx) + (k + 1) * ((p[1] - k * cy) + (k + 1) * (p[2] - k * cz)))
+                       for cz in cand[2] for cy in cand[1] for cx in cand[0]])
+    cells = np.unique([c for a in around for c, _ in a])
+    Me, Ke = element_matrices_deformed(mesh, cells=cells)
+    slot = {c: i for i, c in enumerate(cells)}
+    dofs = mesh.cell_dofs()
+    node = pts[:, 0] + n1 * (pts[:, 1] + n1 * pts[:, 2])
+    refm, refk = np.zeros((Q, len(pts))), np.zeros((Q, len(pts)))
+    for j, a in enumerate(around):
+        for c, loc in a:
+            ue = u[:, dofs[c]]
+            refm[:, j] += ue @ Me[slot[c], loc]
+            refk[:, j] += ue @ Ke[slot[c], loc]
+    assert rel_err(gm[:, node], refm) <= TOL
+    assert rel_err(gk[:, node], refk) <= TOL

@@ -95,3 +95,11 @@ def test_direct_step_solves_stage_system():
     # Eq. (irk:A) form: calA k = (A^{-1} (x) I) rhs
     assert np.abs(apply_calA(prob, kk) - prob.Ainv @ rhs).max() <= 1e-11 * np.abs(rhs).max()
     assert np.abs(y1 - y).max() > 0
+
+
+def test_cell_subset_matches_all_cells():
+    m = DeformedMesh(3, 3, 2, 0.05)
+    Me, Ke = element_matrices_deformed(m)
+    sel = np.array([0, 5, 13, 26])
+    Ms, Ks = element_matrices_deformed(m, cells=sel)
+    assert np.array_equal(Ms, Me[sel]) and np.array_equal(Ks, Ke[sel])

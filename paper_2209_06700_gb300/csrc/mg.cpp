@@ -805,13 +805,18 @@ class MG final : public MGBase {
     const size_t len = (size_t)nb * g0.ld;
     const int steps = std::max(2, cfg_.eig_steps);
     DeviceArena tmp(st);  // Lanczos work vectors, released when the setup returns
+    // the operator of the estimate in the smoother's own arithmetic for an FP32 hierarchy (it needs
+    // a few digits of lambda_max, and the FP32 level kernels are several times faster than the
+    // float-float ones on the large fine levels), float-float for an FP64 hierarchy (FP32 pipe);
+    // Lanczos vectors and reductions in FP64, the diagonal scalings convert between the two
+    using LT = typename std::conditional<sizeof(T) == 4, float, ff>::type;
     double *v0, *v1, *w, *partial, *ab;
-    ff *t, *wf;  // the operator's input and output in float-float form
+    LT *t, *wf;
     IRK_TRY(tmp.alloc((void**)&v0, len * sizeof(double)));
     IRK_TRY(tmp.alloc((void**)&v1, len * sizeof(double)));
     IRK_TRY(tmp.alloc((void**)&w, len * sizeof(double)));
-    IRK_TRY(tmp.alloc((void**)&t, len * sizeof(ff)));
-    IRK_TRY(tmp.alloc((void**)&wf, len * sizeof(ff)));
+    IRK_TRY(tmp.alloc((void**)&t, len * sizeof(LT)));
+    IRK_TRY(tmp.alloc((void**)&wf, len * sizeof(LT)));
     const int nbred = std::min(reduction_blocks((long long)g0.ld), 1024);
     IRK_TRY(tmp.alloc((void**)&partial, (size_t)nbred * nb * sizeof(double)));
     // alpha[step][block], beta[step][block], norm[block]
@@ -834,17 +839,15 @@ class MG final : public MGBase {
       IRK_CUDA(launch_block_shift(nullptr, v1, w, nrm0, nb, n, ldl, st));
       std::vector<double> one(nb, 1.0);
       DiagParams<double> D = make_diag_params<double>(g, nb, cfg_.cm.data(), ck_.data(), one.data());
-      // the estimate's operator in float-float arithmetic (FP32 pipe), Lanczos vectors and reductions in
-      // FP64; the diagonal scalings convert between the two
-      OpParams<ff> P = make_op_params<ff>(g, nb, cfg_.cm.data(), ck_.data());
-      EpiParams<ff> E;
+      OpParams<LT> P = make_op_params<LT>(g, nb, cfg_.cm.data(), ck_.data());
+      EpiParams<LT> E;
       std::memset(&E, 0, sizeof(E));
       E.out = wf;
       // symmetric form D^{-1/2} A D^{-1/2}; every block advances together, no host round trip
       for (int it = 0; it < steps; ++it) {
-        IRK_CUDA(launch_diag_scale<double, ff>(g.grid(), nb, v1, t, D, 1, st));
-        IRK_CUDA(launch_op<ff>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
-        IRK_CUDA(launch_diag_scale<ff, double>(g.grid(), nb, wf, w, D, 1, st));
+        IRK_CUDA(launch_diag_scale<double, LT>(g.grid(), nb, v1, t, D, 1, st));
+        IRK_CUDA(launch_op<LT>(g.dim, g.k, nb, t, P, EPI_STORE, E, st));
+        IRK_CUDA(launch_diag_scale<LT, double>(g.grid(), nb, wf, w, D, 1, st));
         double* a_it = alpha + (size_t)it * nb;
         double* b_it = beta + (size_t)it * nb;
         const double* b_prev = (it == 0) ? zeros : beta + (size_t)(it - 1) * nb;

@@ -546,6 +546,10 @@ template cudaError_t launch_diag_scale<double, ff>(const GridInfo&, int, const d
                                                    int, cudaStream_t);
 template cudaError_t launch_diag_scale<ff, double>(const GridInfo&, int, const ff*, double*, const DiagParams<double>&,
                                                    int, cudaStream_t);
+template cudaError_t launch_diag_scale<double, float>(const GridInfo&, int, const double*, float*,
+                                                      const DiagParams<double>&, int, cudaStream_t);
+template cudaError_t launch_diag_scale<float, double>(const GridInfo&, int, const float*, double*,
+                                                      const DiagParams<double>&, int, cudaStream_t);
 
 cudaError_t launch_hash_fill(const GridInfo& g, int nstage, double* x, cudaStream_t st) {
   dim3 grid(blocks_for(g.n, 2), nstage);

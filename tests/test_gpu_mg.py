@@ -76,7 +76,8 @@ def test_smoother(dim, N, k, Q, prec, dt, tol):
 
 @pytest.mark.parametrize("dim,N,k,Q", CASES)
 def test_chebyshev_interval_from_lanczos(dim, N, k, Q):
-    """hi = 1.2 * lambda_max estimate; Lanczos never overestimates and is within 5 %."""
+    """hi = 1.2 * lambda_max estimate; Lanczos never overestimates (beyond the FP32 rounding of the
+    FP32 level operator it applies, about 1e-7 relative) and is within 5 %."""
     tau = 1e-2
     with pkg.Solver(dim, N, k, Q, tau) as s:
         lam = _blocks(Q)
@@ -85,7 +86,7 @@ def test_chebyshev_interval_from_lanczos(dim, N, k, Q):
             true = max_eig_DinvA(A, jacobi_diag(A, bm), bm)
             lo, hi = s.cheb_interval(0, i)
             est = hi / 1.2
-            assert 0.95 * true <= est <= true * (1 + 1e-9)
+            assert 0.95 * true <= est <= true * (1 + 1e-6)
             assert abs(lo - hi / 20.0) <= 1e-12 * hi
 
 

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Sources in arXiv 2209.06700, Sec. 5: the heat equation is solved with a
 manufactured solution on the unit cube, the source chosen to match, the
 load integrated with the same (k+1)^d Gauss rule as the operators.  The
-workloads of this build replace the paper's solution by
+default workloads replace the paper's solution by
 u = prod_a sin(pi x_a) cos t, so f = u_t - Lap u = S(x) (d pi^2 cos t - sin t)
 with S = prod_a sin(pi x_a); S vanishes on the boundary (homogeneous
 Dirichlet).  The weak form gives M y' + K y = g(t) with

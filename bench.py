@@ -230,7 +230,7 @@ def run_reference(args, w):
 
 def other_workloads(steps=3):
     """The remaining configurations, each timed like the headline one (CUDA events on the solver's
-    stream after one warm-up step, inputs resident): the 64^3 degree-3 problem for Q = 2..5, and the
+    stream after two warm-up steps, inputs resident): the 64^3 degree-3 problem for Q = 2..5, and the
     48^3 degree-2 Q=3 problem in the LU and directly diagonalised variants."""
     import torch
     import paper_2209_06700_gb300 as pkg
@@ -249,13 +249,14 @@ def other_workloads(steps=3):
             y = s.vector()
             with torch.cuda.stream(stream):
                 s.interpolate_initial(y, 0.0)
-            s.step(y, 0.0)
+            for i in range(2):
+                s.step(y, i * w.tau)
             its = []
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for i in range(steps):
-                its.append(s.step(y, (i + 1) * w.tau).iterations)
+                its.append(s.step(y, (i + 2) * w.tau).iterations)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps

@@ -31,16 +31,14 @@ __device__ __forceinline__ void cell_row(const T* src, int stride, int r, const 
 #pragma unroll
     for (int o = 0; o <= 2 * K; ++o) {
       const T v = src[(r + o) * stride];
-      a = mad(a, P.yvm[o], v);
-      b = mad(b, P.yvk[o], v);
+      mad2(a, b, P.yvm[o], P.yvk[o], v, v);
     }
   } else {  // inner row rr of its cell: the K+1 nodes of the cell
     const T* c = src + (K + r - rr) * stride;
 #pragma unroll
     for (int q = 0; q <= K; ++q) {
       const T v = c[q * stride];
-      a = mad(a, P.me[rr][q], v);
-      b = mad(b, P.ke[rr][q], v);
+      mad2(a, b, P.me[rr][q], P.ke[rr][q], v, v);
     }
   }
   m = a;
@@ -108,16 +106,14 @@ __global__ void __launch_bounds__(128 * B) op3d_cell_kernel(const typename Stora
       for (int o = 0; o <= 2 * K; ++o) {
         const int j = (rz + o) * NO * NO + col;
         const T f = dev::mad(dev::mul(cm, g1[j]), ck, dev::add(g2[j], g3[j]));
-        az = dev::mad(az, P.yvm[o], f);
-        kz = dev::mad(kz, P.yvk[o], g1[j]);
+        dev::mad2(az, kz, P.yvm[o], P.yvk[o], f, g1[j]);
       }
     } else {
 #pragma unroll
       for (int q = 0; q <= K; ++q) {
         const int j = (K + rz - rr + q) * NO * NO + col;
         const T f = dev::mad(dev::mul(cm, g1[j]), ck, dev::add(g2[j], g3[j]));
-        az = dev::mad(az, P.me[rr][q], f);
-        kz = dev::mad(kz, P.ke[rr][q], g1[j]);
+        dev::mad2(az, kz, P.me[rr][q], P.ke[rr][q], f, g1[j]);
       }
     }
     const T va = dev::mad(az, ck, kz);

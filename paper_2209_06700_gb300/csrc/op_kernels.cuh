@@ -92,37 +92,46 @@ __device__ __forceinline__ S inv_diag(const EpiParams<S>& E, S cm, S ck, int rx,
 // ---------------------------------------------------------------- 1D contractions
 // y-direction banded taps for output row position R (compile time); col points at the
 // output row in the staged input column, stride = row stride.
-template <typename T, int K, int R>
+// (a, b) += (ca va, cb vb): a packed pair when PK, else two scalar multiply-adds (same result)
+template <bool PK, typename T>
+__device__ __forceinline__ void mad2p(T& a, T& b, T ca, T cb, T va, T vb) {
+  if constexpr (PK) {
+    mad2(a, b, ca, cb, va, vb);
+  } else {
+    a = mad(a, ca, va);
+    b = mad(b, cb, vb);
+  }
+}
+
+template <typename T, int K, int R, bool PK>
 __device__ __forceinline__ void ytaps(const T* col, int stride, const OpParams<T>& P, T& g, T& h) {
   if constexpr (R == 0) {
 #pragma unroll
     for (int o = -K; o <= K; ++o) {
       const T v = col[o * stride];
-      g = mad(g, P.yvm[o + K], v);
-      h = mad(h, P.yvk[o + K], v);
+      mad2p<PK>(g, h, P.yvm[o + K], P.yvk[o + K], v, v);
     }
   } else {
 #pragma unroll
     for (int m = 0; m <= K; ++m) {
       const T v = col[(m - R) * stride];
-      g = mad(g, P.me[R][m], v);
-      h = mad(h, P.ke[R][m], v);
+      mad2p<PK>(g, h, P.me[R][m], P.ke[R][m], v, v);
     }
   }
 }
 
-template <typename T, int K, int R = 0>
+template <typename T, int K, bool PK, int R = 0>
 __device__ __forceinline__ void ytaps_dispatch(int r, const T* col, int stride, const OpParams<T>& P,
                                                T& g, T& h) {
   if constexpr (R < K) {
-    if (r == R) ytaps<T, K, R>(col, stride, P, g, h);
-    else ytaps_dispatch<T, K, R + 1>(r, col, stride, P, g, h);
+    if (r == R) ytaps<T, K, R, PK>(col, stride, P, g, h);
+    else ytaps_dispatch<T, K, PK, R + 1>(r, col, stride, P, g, h);
   }
 }
 
 // Cell-wise x contraction for one lane's cell (staged columns cl, cl+1 of slots [m][cell]).
 // MODE3: g = My u, h = Ky u given -> R = Mx g, Pp = Kx g + Mx h.  MODE2: u given -> R = Mx u, Pp = Kx u.
-template <typename T, int K, bool MODE3, int CW>
+template <typename T, int K, bool MODE3, int CW, bool PK>
 __device__ __forceinline__ void xcell(const T* g, const T* h, int cl, const OpParams<T>& P,
                                       T (&r)[K + 1], T (&p)[K + 1]) {
   T gv[K + 1], hv[K + 1];
@@ -138,8 +147,7 @@ __device__ __forceinline__ void xcell(const T* g, const T* h, int cl, const OpPa
     T a = zero<T>(), b = zero<T>();
 #pragma unroll
     for (int m = 0; m <= K; ++m) {
-      a = mad(a, P.me[mo][m], gv[m]);
-      b = mad(b, P.ke[mo][m], gv[m]);
+      mad2p<PK>(a, b, P.me[mo][m], P.ke[mo][m], gv[m], gv[m]);
       if constexpr (MODE3) b = mad(b, P.me[mo][m], hv[m]);
     }
     r[mo] = a;
@@ -148,15 +156,14 @@ __device__ __forceinline__ void xcell(const T* g, const T* h, int cl, const OpPa
 }
 
 // Top-vertex outputs (local node K) of the cell at staged column cl.
-template <typename T, int K, bool MODE3, int CW>
+template <typename T, int K, bool MODE3, int CW, bool PK>
 __device__ __forceinline__ void xcell_top(const T* g, const T* h, int cl, const OpParams<T>& P, T& r, T& p) {
   T a = zero<T>(), b = zero<T>();
 #pragma unroll
   for (int m = 0; m <= K; ++m) {
     const int slot = (m < K) ? (m * CW + cl) : (cl + 1);
     const T gv = g[slot];
-    a = mad(a, P.me[K][m], gv);
-    b = mad(b, P.ke[K][m], gv);
+    mad2p<PK>(a, b, P.me[K][m], P.ke[K][m], gv, gv);
     if constexpr (MODE3) b = mad(b, P.me[K][m], h[slot]);
   }
   r = a;
@@ -164,22 +171,50 @@ __device__ __forceinline__ void xcell_top(const T* g, const T* h, int cl, const 
 }
 
 // z push of column RZ (compile time) into the accumulators of the owned nodes.
-template <typename T, int K, int RZ, bool DUAL>
+template <typename T, int K, int RZ, bool DUAL, bool PK>
 __device__ __forceinline__ void zpush(const OpParams<T>& P, T cm, T ck, const T (&R)[K], const T (&Pp)[K],
                                       T (&accA)[K][K + 1], T (&accB)[K][K + 1]) {
+  if constexpr (PK && !DUAL) {
+    T F[K], Ez[K];
 #pragma unroll
-  for (int m = 0; m < K; ++m) {
-    if constexpr (DUAL) {
+    for (int m = 0; m < K; ++m) {
+      F[m] = mad(mul(cm, R[m]), ck, Pp[m]);
+      Ez[m] = mul(ck, R[m]);
+    }
+    // nodes m and m + 1 share the coefficients: one pair of multiply-adds per tap
+#pragma unroll
+    for (int m = 0; m + 1 < K; m += 2) {
 #pragma unroll
       for (int mo = 0; mo <= K; ++mo) {
-        accA[m][mo] = mad(accA[m][mo], P.me[mo][RZ], R[m]);
-        accB[m][mo] = mad(mad(accB[m][mo], P.me[mo][RZ], Pp[m]), P.ke[mo][RZ], R[m]);
+        mad2(accA[m][mo], accA[m + 1][mo], P.me[mo][RZ], P.me[mo][RZ], F[m], F[m + 1]);
+        mad2(accA[m][mo], accA[m + 1][mo], P.ke[mo][RZ], P.ke[mo][RZ], Ez[m], Ez[m + 1]);
       }
-    } else {
-      const T F = mad(mul(cm, R[m]), ck, Pp[m]);
-      const T Ez = mul(ck, R[m]);
+    }
+    if constexpr (K % 2 == 1) {
 #pragma unroll
-      for (int mo = 0; mo <= K; ++mo) accA[m][mo] = mad(mad(accA[m][mo], P.me[mo][RZ], F), P.ke[mo][RZ], Ez);
+      for (int mo = 0; mo <= K; ++mo)
+        accA[K - 1][mo] = mad(mad(accA[K - 1][mo], P.me[mo][RZ], F[K - 1]), P.ke[mo][RZ], Ez[K - 1]);
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      if constexpr (DUAL) {
+#pragma unroll
+        for (int mo = 0; mo <= K; ++mo) {
+          if constexpr (PK) {
+            mad2(accA[m][mo], accB[m][mo], P.me[mo][RZ], P.me[mo][RZ], R[m], Pp[m]);
+            accB[m][mo] = mad(accB[m][mo], P.ke[mo][RZ], R[m]);
+          } else {
+            accA[m][mo] = mad(accA[m][mo], P.me[mo][RZ], R[m]);
+            accB[m][mo] = mad(mad(accB[m][mo], P.me[mo][RZ], Pp[m]), P.ke[mo][RZ], R[m]);
+          }
+        }
+      } else {
+        const T F = mad(mul(cm, R[m]), ck, Pp[m]);
+        const T Ez = mul(ck, R[m]);
+#pragma unroll
+        for (int mo = 0; mo <= K; ++mo) accA[m][mo] = mad(mad(accA[m][mo], P.me[mo][RZ], F), P.ke[mo][RZ], Ez);
+      }
     }
   }
 }
@@ -200,23 +235,23 @@ __device__ __forceinline__ void carry(T (&accA)[K][K + 1], T (&accB)[K][K + 1]) 
 
 // push of the plane with in-cell position r (0..K-1) into the accumulators; at a vertex plane
 // (r = 0) the cell below is completed first (column K), emitted, and its top vertex carried.
-template <typename T, int K, bool DUAL, class Emit>
+template <typename T, int K, bool DUAL, bool PK, class Emit>
 __device__ __forceinline__ void zstep(int r, int c, int cstart, int c0, const OpParams<T>& P, T cm, T ck,
                                       const T (&R)[K], const T (&Pp)[K], T (&accA)[K][K + 1], T (&accB)[K][K + 1],
                                       Emit&& emit) {
   if (r == 0) {
     if (c > cstart) {
-      zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
+      zpush<T, K, K, DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
       if (c - 1 >= c0) emit(c - 1);
       carry<T, K, DUAL>(accA, accB);
     }
-    zpush<T, K, 0, DUAL>(P, cm, ck, R, Pp, accA, accB);
+    zpush<T, K, 0, DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
   } else if (r == 1) {
-    zpush<T, K, (1 < K ? 1 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
+    zpush<T, K, (1 < K ? 1 : 0), DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
   } else if (r == 2) {
-    zpush<T, K, (2 < K ? 2 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
+    zpush<T, K, (2 < K ? 2 : 0), DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
   } else {
-    zpush<T, K, (3 < K ? 3 : 0), DUAL>(P, cm, ck, R, Pp, accA, accB);
+    zpush<T, K, (3 < K ? 3 : 0), DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
   }
 }
 
@@ -263,6 +298,9 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   constexpr int NLD = HY * HX;
   constexpr int PF = (NLD + NT - 1) / NT;
   constexpr bool DUAL = (EPI == EPI_DUAL);
+  // packed pairs of multiply-adds, except FP32 DUAL (only on the coupled-block path), where the
+  // pairing constraints on the allocator raise the spills at this kernel's register cap
+  constexpr bool PK = !(DUAL && sizeof(T) == 4);
   using L = Op3dSmem<T, K, EPI, CXS>;
   extern __shared__ __align__(16) unsigned char op_smem[];
   T* const su2 = reinterpret_cast<T*>(op_smem);  // two staged planes (double buffer)
@@ -335,7 +373,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       const T* colbase = su + (yr + K) * SL;
       for (int sl = lane; sl < SL; sl += 32) {
         T g = dev::zero<T>(), h = dev::zero<T>();
-        dev::ytaps_dispatch<T, K>(ro, colbase + sl, SL, P, g, h);
+        dev::ytaps_dispatch<T, K, PK>(ro, colbase + sl, SL, P, g, h);
         sgb[yr * SL + sl] = g;
         shb[yr * SL + sl] = h;
       }
@@ -347,12 +385,12 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     const T* g = sg2 + buf * L::SG + trow * SL;
     const T* h = sh2 + buf * L::SG + trow * SL;
     T r[K + 1], p[K + 1];
-    dev::xcell<T, K, true, CW>(g, h, lx + 1, P, r, p);
+    dev::xcell<T, K, true, CW, PK>(g, h, lx + 1, P, r, p);
     T rl = dev::shfl_up(r[K]);
     T pl = dev::shfl_up(p[K]);
     if (lx == 0) {  // the cell left of the tile: none at the domain's left boundary
       if (cx0 > 0) {
-        dev::xcell_top<T, K, true, CW>(g, h, 0, P, rl, pl);
+        dev::xcell_top<T, K, true, CW, PK>(g, h, 0, P, rl, pl);
       } else {
         rl = dev::zero<T>();
         pl = dev::zero<T>();
@@ -423,7 +461,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       ypass(buf);
       T R[K], Pp[K];
       xpass(buf ^ 1, R, Pp);
-      dev::zstep<T, K, DUAL>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
+      dev::zstep<T, K, DUAL, PK>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
       if (zp + 1 <= zlast) {
         store_plane(buf ^ 1);
         if (zp + 2 <= zlast) load_plane(zp + 2);
@@ -434,7 +472,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   {  // upper vertex plane of the last cell
     T R[K], Pp[K];
     xpass((zlast - z0) & 1, R, Pp);
-    dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
+    dev::zpush<T, K, K, DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
     if (c1 - 1 >= c0) emit(c1 - 1);
   }
   if (clustered) {
@@ -479,6 +517,7 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   constexpr int HX = K * CX + K + 1;
   constexpr int PF = (HX + NT - 1) / NT;
   constexpr bool DUAL = (EPI == EPI_DUAL);
+  constexpr bool PK = false;  // scalar multiply-adds: the packed pairs spill the degree-4 kernels here
   __shared__ T su[SL];
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -520,10 +559,10 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   const int cl = w * 32 + lane + 1;
   auto xpass = [&](T (&R)[K], T (&Pp)[K]) {
     T r[K + 1], p[K + 1];
-    dev::xcell<T, K, false, CW>(su, su, cl, P, r, p);
+    dev::xcell<T, K, false, CW, PK>(su, su, cl, P, r, p);
     T rl = dev::shfl_up(r[K]);
     T pl = dev::shfl_up(p[K]);
-    if (lane == 0) dev::xcell_top<T, K, false, CW>(su, su, cl - 1, P, rl, pl);
+    if (lane == 0) dev::xcell_top<T, K, false, CW, PK>(su, su, cl - 1, P, rl, pl);
     r[0] = dev::add(r[0], rl);
     p[0] = dev::add(p[0], pl);
 #pragma unroll
@@ -565,7 +604,7 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       load_row(yp + 1);
       T R[K], Pp[K];
       xpass(R, Pp);
-      dev::zstep<T, K, DUAL>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
+      dev::zstep<T, K, DUAL, PK>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
     }
   }
   __syncthreads();
@@ -574,7 +613,7 @@ op2d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   {
     T R[K], Pp[K];
     xpass(R, Pp);
-    dev::zpush<T, K, K, DUAL>(P, cm, ck, R, Pp, accA, accB);
+    dev::zpush<T, K, K, DUAL, PK>(P, cm, ck, R, Pp, accA, accB);
     if (c1 - 1 >= c0) emit(c1 - 1);
   }
 }

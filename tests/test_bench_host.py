@@ -49,3 +49,10 @@ def test_recorded_traffic_is_dropped_when_a_kernel_source_changes(tmp_path, monk
     src = tmp_path / rec["source_files"][0]
     src.write_bytes(src.read_bytes() + b"\n")
     assert bench.recorded_traffic() is None
+
+
+def test_one_thread_oracle_leg_runs_in_a_child_process():
+    from synthetic import HEAT2D_K2_N16_Q2 as w
+    got = bench.cpu_baseline_one_thread(w, timeout_s=120)
+    assert "error" not in got, got
+    assert got["cores"] == 1 and got["value"] > 0 and got["unit"] == bench.UNIT

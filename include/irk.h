@@ -210,6 +210,14 @@ irk_status irk_interpolate_initial(irk_handle h, double* y, double t);
  * 9 T (real Jordan basis of A^{-1}), 10 T^{-1}, 11 J (real block form). */
 irk_status irk_get_tableau(irk_handle h, int which, double* out_host);
 
+/* The same factors without a handle or a device: Radau IIA with Q stages (1..9; Sec. 2, the
+ * collocation tableau), the Crout factors of A^{-1} with its eigen-decomposition (Eq. irk:P) and
+ * the real block form (Eq. irk:Ainv), built by the host routine irk_create uses.  which as in
+ * irk_get_tableau; out_host holds Q x Q (row-major) or Q doubles, owned by the caller.  Returns
+ * IRK_EINVAL for a NULL out_host, Q outside 1..9 or an unknown which, IRK_ENUMERIC if the
+ * construction fails.  Runs on the host only (no CUDA call). */
+irk_status irk_tableau_factors(int Q, int which, double* out_host);
+
 /* Chebyshev interval of level l (0 = finest) and block i: out_host[0] = lo, [1] = hi. */
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out_host);
 

@@ -11,7 +11,7 @@ from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOpti
                     IrkServeOptions, IrkStats, TABLEAU_FIELDS, check, lib)
 
 __all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "autotune_report", "lib", "options", "serve",
-           "solve_batch"]
+           "solve_batch", "tableau_factors"]
 
 
 def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, **solver_opts):
@@ -62,6 +62,17 @@ def solve_batch(solvers, ys, t_ns):
     per = (ctypes.c_int * n)()
     status = lib().irk_solve_batch(hs, yp, ts, n, per)
     return status, list(per)
+
+
+def tableau_factors(Q, name):
+    """Factor `name` (a key of TABLEAU_FIELDS) of the Q-stage Radau IIA tableau as built on the host
+    by the library (irk_tableau_factors; no device needed)."""
+    import numpy as np
+    size = Q if name in ("b", "c", "lam") else Q * Q
+    out = (ctypes.c_double * size)()
+    check(lib().irk_tableau_factors(int(Q), TABLEAU_FIELDS[name], out))
+    a = np.array(out[:], dtype=np.float64)
+    return a if name in ("b", "c", "lam") else a.reshape(Q, Q)
 
 
 def autotune_report():
@@ -199,7 +210,7 @@ class Solver:
         out = (ctypes.c_double * size)()
         check(lib().irk_get_tableau(self.h, TABLEAU_FIELDS[name], out), self.h)
         a = np.array(out[:], dtype=np.float64)
-        return a if size == Q else a.reshape(Q, Q)
+        return a if name in ("b", "c", "lam") else a.reshape(Q, Q)
 
     def cheb_interval(self, level, block):
         out = (ctypes.c_double * 2)()

@@ -77,6 +77,7 @@ SIGNATURES = {
     "irk_autotune_report": (_I, [ctypes.c_char_p, _I]),
     "irk_interpolate_initial": (_I, [_H, _P, _D]),
     "irk_get_tableau": (_I, [_H, _I, ctypes.POINTER(_D)]),
+    "irk_tableau_factors": (_I, [_I, _I, ctypes.POINTER(_D)]),
     "irk_get_cheb_interval": (_I, [_H, _I, _I, ctypes.POINTER(_D)]),
     "irk_apply_op": (_I, [_H, _P, _P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "irk_apply": (_I, [_H, _P, _P]),

@@ -713,29 +713,52 @@ irk_status irk_interpolate_initial(irk_handle h, double* y, double t) {
   });
 }
 
+namespace {
+// factor `which` of irk_get_tableau / irk_tableau_factors (nullptr: unknown)
+const std::vector<double>* tableau_field(const Tableau& t, int which) {
+  switch (which) {
+    case 0: return &t.A;
+    case 1: return &t.b;
+    case 2: return &t.c;
+    case 3: return &t.Ainv;
+    case 4: return &t.L;
+    case 5: return &t.U;
+    case 6: return &t.S;
+    case 7: return &t.Sinv;
+    case 8: return &t.lam;
+    case 9: return &t.T;
+    case 10: return &t.Tinv;
+    case 11: return &t.J;
+    default: return nullptr;
+  }
+}
+}  // namespace
+
 irk_status irk_get_tableau(irk_handle h, int which, double* out) {
   return guarded(h, [&]() -> Status {
     if (!out) return Status::Err(IRK_EINVAL, "out is NULL");
-    const Tableau& t = h->tab;
-    const std::vector<double>* src = nullptr;
-    switch (which) {
-      case 0: src = &t.A; break;
-      case 1: src = &t.b; break;
-      case 2: src = &t.c; break;
-      case 3: src = &t.Ainv; break;
-      case 4: src = &t.L; break;
-      case 5: src = &t.U; break;
-      case 6: src = &t.S; break;
-      case 7: src = &t.Sinv; break;
-      case 8: src = &t.lam; break;
-      case 9: src = &t.T; break;
-      case 10: src = &t.Tinv; break;
-      case 11: src = &t.J; break;
-      default: return Status::Err(IRK_EINVAL, "unknown tableau factor");
-    }
+    const std::vector<double>* src = tableau_field(h->tab, which);
+    if (!src) return Status::Err(IRK_EINVAL, "unknown tableau factor");
     std::memcpy(out, src->data(), src->size() * sizeof(double));
     return Status::Ok();
   });
+}
+
+irk_status irk_tableau_factors(int Q, int which, double* out) {
+  if (!out || Q < 1 || Q > kMaxQ) return IRK_EINVAL;
+  try {
+    Tableau t;
+    std::string err;
+    if (!build_tableau(Q, t, err)) return IRK_ENUMERIC;
+    const std::vector<double>* src = tableau_field(t, which);
+    if (!src) return IRK_EINVAL;
+    std::memcpy(out, src->data(), src->size() * sizeof(double));
+    return IRK_OK;
+  } catch (const std::bad_alloc&) {
+    return IRK_ENOMEM;
+  } catch (...) {
+    return IRK_ENUMERIC;
+  }
 }
 
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out) {

@@ -218,6 +218,17 @@ irk_status irk_get_tableau(irk_handle h, int which, double* out_host);
  * construction fails.  Runs on the host only (no CUDA call). */
 irk_status irk_tableau_factors(int Q, int which, double* out_host);
 
+/* One-dimensional Q_k element data on the reference cell [0, 1] as the operators use it, built
+ * on the host without a handle or a device (Sec. 5: tensor-product Lagrange elements with the
+ * consistent (k+1)-point Gauss rule; nodes at the Gauss-Lobatto-Legendre points; the
+ * prolongation is the Q_k embedding of a cell split in two).  k in 1..4, p = k + 1; which:
+ * 0 nodes (p), 1 mass matrix (p x p), 2 stiffness matrix (p x p), 3 prolongation block
+ * ((2k+1) x p: coarse basis i at fine node m, row-major [m][i]), 4 Gauss points (p), 5 Gauss
+ * weights (p), 6 basis values and 7 basis derivatives at the Gauss points (p x p, [q][i]).
+ * out_host is owned by the caller.  Returns IRK_EINVAL for a NULL out_host, k outside 1..4 or an
+ * unknown which, IRK_ENUMERIC if the construction fails.  Host only (no CUDA call). */
+irk_status irk_element_factors(int k, int which, double* out_host);
+
 /* Chebyshev interval of level l (0 = finest) and block i: out_host[0] = lo, [1] = hi. */
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out_host);
 

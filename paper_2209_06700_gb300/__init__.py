@@ -8,10 +8,10 @@ import ctypes
 
 from . import _capi
 from ._capi import (IRK_VARIANT_DIAG, IRK_VARIANT_LU, IrkError, IrkMesh, IrkOptions, IrkRequest, IrkResult,
-                    IrkServeOptions, IrkStats, TABLEAU_FIELDS, check, lib)
+                    IrkServeOptions, IrkStats, TABLEAU_FIELDS, ELEMENT_FIELDS, check, lib)
 
 __all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "autotune_report", "lib", "options", "serve",
-           "solve_batch", "tableau_factors"]
+           "solve_batch", "tableau_factors", "element_factors"]
 
 
 def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, **solver_opts):
@@ -73,6 +73,17 @@ def tableau_factors(Q, name):
     check(lib().irk_tableau_factors(int(Q), TABLEAU_FIELDS[name], out))
     a = np.array(out[:], dtype=np.float64)
     return a if name in ("b", "c", "lam") else a.reshape(Q, Q)
+
+
+def element_factors(k, name):
+    """1D element data `name` (a key of ELEMENT_FIELDS) of degree k as the library builds it on the
+    host (irk_element_factors; no device needed)."""
+    import numpy as np
+    p = k + 1
+    shape = {"nodes": (p,), "gq": (p,), "gw": (p,), "Pc": (2 * k + 1, p)}.get(name, (p, p))
+    out = (ctypes.c_double * int(np.prod(shape)))()
+    check(lib().irk_element_factors(int(k), ELEMENT_FIELDS[name], out))
+    return np.array(out[:], dtype=np.float64).reshape(shape)
 
 
 def autotune_report():

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libirk.so")
 IRK_OK, IRK_EINVAL, IRK_ENOMEM, IRK_ENOTCONV, IRK_ENUMERIC, IRK_ETIMEOUT, IRK_ECUDA, IRK_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 IRK_VARIANT_LU, IRK_VARIANT_DIAG = 0, 1
 
+ELEMENT_FIELDS = {"nodes": 0, "Me": 1, "Ke": 2, "Pc": 3, "gq": 4, "gw": 5, "B": 6, "D": 7}
 TABLEAU_FIELDS = {"A": 0, "b": 1, "c": 2, "Ainv": 3, "L": 4, "U": 5, "S": 6, "Sinv": 7, "lam": 8,
                   "T": 9, "Tinv": 10, "J": 11}
 
@@ -78,6 +79,7 @@ SIGNATURES = {
     "irk_interpolate_initial": (_I, [_H, _P, _D]),
     "irk_get_tableau": (_I, [_H, _I, ctypes.POINTER(_D)]),
     "irk_tableau_factors": (_I, [_I, _I, ctypes.POINTER(_D)]),
+    "irk_element_factors": (_I, [_I, _I, ctypes.POINTER(_D)]),
     "irk_get_cheb_interval": (_I, [_H, _I, _I, ctypes.POINTER(_D)]),
     "irk_apply_op": (_I, [_H, _P, _P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "irk_apply": (_I, [_H, _P, _P]),

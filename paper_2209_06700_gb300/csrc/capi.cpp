@@ -761,6 +761,33 @@ irk_status irk_tableau_factors(int Q, int which, double* out) {
   }
 }
 
+irk_status irk_element_factors(int k, int which, double* out) {
+  if (!out || k < 1 || k > kMaxDeg) return IRK_EINVAL;
+  try {
+    Element1D e;
+    std::string err;
+    if (!build_element1d(k, e, err)) return IRK_ENUMERIC;
+    const std::vector<double>* src = nullptr;
+    switch (which) {
+      case 0: src = &e.nodes; break;
+      case 1: src = &e.Me; break;
+      case 2: src = &e.Ke; break;
+      case 3: src = &e.Pc; break;
+      case 4: src = &e.gq; break;
+      case 5: src = &e.gw; break;
+      case 6: src = &e.B; break;
+      case 7: src = &e.D; break;
+      default: return IRK_EINVAL;
+    }
+    std::memcpy(out, src->data(), src->size() * sizeof(double));
+    return IRK_OK;
+  } catch (const std::bad_alloc&) {
+    return IRK_ENOMEM;
+  } catch (...) {
+    return IRK_ENUMERIC;
+  }
+}
+
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out) {
   return guarded(h, [&]() -> Status {
     const int nb = h->mg_sel == 0 ? h->Q : (h->tab.blocks[h->mg_sel - 1].pair && h->opt.pair_precond == 1 ? 2 : 1);

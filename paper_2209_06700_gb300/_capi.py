@@ -2,8 +2,9 @@
 
 Every computation of the solver runs in libirk's CUDA kernels; this module
 loads the in-tree shared library and forwards pointers and sizes.  There is no
-fallback: if libirk.so is missing or cannot be loaded, importing the package
-raises.
+fallback: if libirk.so is missing or cannot be loaded, the first call into the
+package raises OSError (the import itself succeeds, so that the in-package build
+script can run before the library exists).
 """
 import ctypes
 import os

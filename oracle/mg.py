@@ -36,8 +36,8 @@ eigenpair of D^{-1}A; the prolongation reproduces degree-k polynomials
 exactly; <P^T r, v> = <r, P v>; the V-cycle is symmetric and its two-grid
 error contraction is below one; the PRESB factors multiply to P and the
 PRESB-preconditioned spectrum lies in [1/2, 1].
-The chosen Chebyshev interval and level count are heuristics (parity
-unpinned beyond the algebraic checks above); only the converged step
+The chosen Chebyshev interval and level count are heuristics:
+parity unpinned beyond the algebraic checks above; only the converged step
 result is pinned as a whole.
 """
 import numpy as np

@@ -30,6 +30,10 @@
  *    (Krylov bases, multigrid hierarchy) and frees it in irk_destroy.
  *  - Errors are returned as irk_status codes; no C++ exception crosses the
  *    ABI.  irk_last_error(h) gives a one-line message for the last failure.
+ *    Every call that takes a handle returns IRK_EINVAL for a NULL handle and
+ *    for the NULL or out-of-range arguments named at the call, IRK_ENOMEM when
+ *    an allocation fails and IRK_ECUDA when a CUDA call fails; the size queries
+ *    return -1 instead of a status.
  *  - A handle is not thread-safe; distinct handles may be used from distinct
  *    threads.
  */
@@ -114,17 +118,23 @@ void irk_default_options(irk_options* opt);
  * intervals (Lanczos on D^{-1}A per level and block) and the dense coarse
  * inverses, and allocates all work memory on the current device.
  * `cuda_stream` is a cudaStream_t (NULL: default stream).  On success *out
- * holds the handle; on failure *out is NULL and nothing is leaked. */
+ * holds the handle; on failure *out is NULL and nothing is leaked.  The setup
+ * follows Sec. 5 (solver setup) with the readings of the multigrid stated above.
+ * IRK_EINVAL: NULL mesh or out, dim not 2 or 3, cells_per_axis outside 1..4096,
+ * degree outside 1..4, Q outside 1..9 (DIAG: 2..9), tau not positive and finite,
+ * no interior node, or invalid options; IRK_ENOMEM / IRK_ECUDA as above. */
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau,
                       const irk_options* opt, void* cuda_stream, irk_handle* out);
 
-/* One Radau IIA step from t_n.  y (device, irk_ndofs(h) doubles): in y_n,
+/* One Radau IIA step from t_n (Sec. 2: the stage system of Eq. (irk:A) solved by
+ * flexible GMRES preconditioned by Eq. (irk:P), then the update of Sec. 1).
+ * y (device, irk_ndofs(h) doubles): in y_n,
  * out y_{n+1}.  stage_load: NULL = the built-in manufactured source
  * g(t) = (d pi^2 cos t - sin t) G with G_j = int prod sin(pi x_a) phi_j;
  * otherwise a device array [Q][stride] with g(t_n + c_i tau) per stage.
  * stats may be NULL.  Returns after the step is complete on the stream
  * (the FGMRES convergence test reads residual norms on the host).
- * On IRK_ENOTCONV / IRK_ENUMERIC y is unchanged. */
+ * IRK_EINVAL for a NULL y.  On IRK_ENOTCONV / IRK_ENUMERIC y is unchanged. */
 irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load,
                     irk_stats* stats);
 
@@ -184,15 +194,18 @@ void irk_default_serve_options(irk_serve_options* opt);
 irk_status irk_serve(const irk_request* reqs, int count, const irk_serve_options* opt, irk_result* results,
                      double** out_host);
 
-/* Release every resource of the handle (NULL is accepted). */
+/* Release every resource of the handle (NULL is accepted).  Returns IRK_OK. */
 irk_status irk_destroy(irk_handle h);
 
-/* ---- sizes and helpers ---- */
+/* ---- sizes and helpers (the size queries return -1 for a NULL handle) ---- */
 long long irk_ndofs(irk_handle h);            /* (kN+1)^d */
 long long irk_ninterior(irk_handle h);        /* (kN-1)^d unknowns per stage */
 long long irk_stage_stride(irk_handle h);     /* elements between stage vectors in [Q][stride] arrays */
-int irk_num_levels(irk_handle h);
+int irk_num_levels(irk_handle h);             /* multigrid levels, finest first */
+/* Static text of a status code (never NULL). */
 const char* irk_strerror(irk_status s);
+/* Message of the handle's last failure ("" before any; "NULL handle" for NULL); the string is
+ * owned by the handle and valid until its next failing call or irk_destroy. */
 const char* irk_last_error(irk_handle h);
 
 /* Text report of the launch shapes chosen by the autotuner so far in this process, one line
@@ -202,12 +215,16 @@ const char* irk_last_error(irk_handle h);
  * batched launches of Sec. 5.4). */
 int irk_autotune_report(char* buf, int len);
 
-/* y (device, irk_ndofs doubles) <- nodal interpolant of prod sin(pi x_a) cos t. */
+/* y (device, irk_ndofs doubles) <- nodal interpolant of the manufactured solution
+ * u = prod sin(pi x_a) cos t (the initial value of the step; on the curved mesh at the mapped
+ * nodes).  IRK_EINVAL for a NULL y. */
 irk_status irk_interpolate_initial(irk_handle h, double* y, double t);
 
 /* Host copies of the tableau factors (row-major Q x Q or length Q), FP64:
  * which = 0 A, 1 b, 2 c, 3 A^{-1}, 4 L, 5 U, 6 S~, 7 S~^{-1}, 8 lambda~ (diag L),
- * 9 T (real Jordan basis of A^{-1}), 10 T^{-1}, 11 J (real block form). */
+ * 9 T (real Jordan basis of A^{-1}), 10 T^{-1}, 11 J (real block form)
+ * (Sec. 2; Eq. (irk:P); Eq. (irk:Ainv)).  out_host is owned by the caller.  IRK_EINVAL for a
+ * NULL out_host or an unknown which. */
 irk_status irk_get_tableau(irk_handle h, int which, double* out_host);
 
 /* The same factors without a handle or a device: Radau IIA with Q stages (1..9; Sec. 2, the
@@ -229,7 +246,10 @@ irk_status irk_tableau_factors(int Q, int which, double* out_host);
  * unknown which, IRK_ENUMERIC if the construction fails.  Host only (no CUDA call). */
 irk_status irk_element_factors(int k, int which, double* out_host);
 
-/* Chebyshev interval of level l (0 = finest) and block i: out_host[0] = lo, [1] = hi. */
+/* Chebyshev interval of the smoother (Sec. 5) on level l (0 = finest) and block i of the
+ * hierarchy chosen by irk_mg_select: out_host[0] = lo, [1] = hi (host, caller-owned).
+ * IRK_EINVAL for a NULL out_host, a level without a smoother (the coarsest is solved exactly)
+ * or a block the hierarchy does not have. */
 irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out_host);
 
 /* ---- the steps of the hot path, exposed one by one (all device pointers) ---- */
@@ -241,15 +261,17 @@ irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out
 irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns,
                         const double* Cm_host, const double* Ck_host);
 
-/* v = calA u with calA = A^{-1} (x) M + tau I (x) K (Eq. irk:A), [Q][stride] FP64. */
+/* v = calA u with calA = A^{-1} (x) M + tau I (x) K (Eq. irk:A), [Q][stride] FP64.
+ * IRK_EINVAL for NULL u or v. */
 irk_status irk_apply(irk_handle h, const double* u, double* v);
 
 /* rhs = (A^{-1} (x) I)(gbar - 1 (x) K y_n) (Eq. irk:A right-hand side) with the
- * built-in source; rhs is [Q][stride] FP64. */
+ * built-in source; rhs is [Q][stride] FP64.  IRK_EINVAL for NULL y or rhs. */
 irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs);
 
 /* z = P^{-1} r (Eq. irk:P): basis change S~^{-1}, one V-cycle per block in the
- * configured MG precision, basis change S~.  [Q][stride] FP64 in and out. */
+ * configured MG precision, basis change S~.  [Q][stride] FP64 in and out.
+ * IRK_EINVAL for NULL r or z. */
 irk_status irk_precondition(irk_handle h, const double* r, double* z);
 
 /* Multigrid pieces on level `level` (0 = finest) for all Q LU blocks at once,
@@ -262,7 +284,10 @@ irk_status irk_precondition(irk_handle h, const double* r, double* z);
  *   coarse:    x = (lambda_i M_c + tau K_c)^{-1} b on the coarsest level (dense FP64)
  *   vcycle:    x = V-cycle(b) starting from level `level`.
  * Vectors are [Q][level stride] of the level's (k N_l + 1)^d nodes; strides from
- * irk_level_stride. */
+ * irk_level_stride.  The V-cycle of Sec. 5 (geometric multigrid, Chebyshev smoother around
+ * point-Jacobi) taken apart.  IRK_EINVAL for NULL vectors or a level out of range: smooth,
+ * restrict and prolongate need level < levels - 1, residual and vcycle level < levels;
+ * irk_level_ndofs / irk_level_stride return -1 for a NULL handle or a bad level. */
 long long irk_level_ndofs(irk_handle h, int level);
 long long irk_level_stride(irk_handle h, int level);
 irk_status irk_mg_smooth(irk_handle h, int level, const void* b, void* x, int x_is_zero);
@@ -296,11 +321,12 @@ irk_status irk_mg_vcycle(irk_handle h, int level, const void* b, void* x);
 irk_status irk_mg_select(irk_handle h, int which);
 
 /* The generalized mat-vec of Sec. 2, v = (D (x) I) u, D host row-major
- * nout x nin, u [nin][stride], v [nout][stride], FP64. */
+ * nout x nin, u [nin][stride], v [nout][stride], FP64.  IRK_EINVAL for NULL
+ * pointers or nin / nout outside 1..9. */
 irk_status irk_stage_combine(irk_handle h, const double* u, int nin, double* v, int nout,
                              const double* D_host);
 
-/* Wait for the handle's stream. */
+/* Wait for the handle's stream; IRK_ECUDA if the stream reports an error. */
 irk_status irk_synchronize(irk_handle h);
 
 /* ---- launch accounting (no counterpart in the paper: measurement support) ----
@@ -308,7 +334,8 @@ irk_status irk_synchronize(irk_handle h);
  * categories whose bit is set in `mask` are also bracketed by CUDA events on the
  * handle's stream.  irk_profile resets the counters (after synchronising the
  * stream); irk_profile_read returns, for one category, the summed device time
- * of the timed launches in ms, the number of launches, and the number timed. */
+ * of the timed launches in ms, the number of launches, and the number timed
+ * (host pointers; IRK_EINVAL for an unknown category). */
 enum {
   IRK_PROF_APPLY64 = 0,   /* FP64-accurate stage-operator kernel of Eq. (irk:A) */
   IRK_PROF_MG_OP = 1,     /* level-operator kernels (Chebyshev steps, residuals), coarser levels */

@@ -66,17 +66,17 @@ typedef struct {
 } irk_mesh;
 
 typedef struct {
-  double rtol;        /* outer FGMRES: stop when ||r|| <= rtol ||rhs|| (default 1e-10) */
-  int max_it;         /* maximum FGMRES iterations per step, all restarts (default 200) */
-  int restart;        /* Krylov basis size before restart (default 30) */
-  int cheb_degree;    /* Chebyshev smoother degree per half V-cycle (default 3) */
+  double rtol;        /* outer FGMRES: stop when ||r|| <= rtol ||rhs|| (default 1e-10; > 0) */
+  int max_it;         /* maximum FGMRES iterations per step, all restarts (default 200; >= 1) */
+  int restart;        /* Krylov basis size before restart (default 30; 1..60) */
+  int cheb_degree;    /* Chebyshev smoother degree per half V-cycle (default 3; 1..16) */
   int variant;        /* IRK_VARIANT_LU (Eq. irk:P) or IRK_VARIANT_DIAG (Eq. irk:Ainv + PRESB) */
   int mg_precision;   /* 32: FP32 V-cycle (default); 64: FP64 V-cycle */
   int batched;        /* 1: all stage blocks in one launch per kernel (default); 0: per-stage launches */
   int use_graph;      /* 1: replay the preconditioner as a CUDA graph (default 1) */
-  int eig_steps;      /* Lanczos steps for the Chebyshev interval (default 20) */
-  double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 20) */
-  double eig_safety;  /* hi = safety * Lanczos estimate (default 1.2) */
+  int eig_steps;      /* Lanczos steps for the Chebyshev interval (default 20; >= 2) */
+  double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 20; > 1) */
+  double eig_safety;  /* hi = safety * Lanczos estimate (default 1.2; >= 1) */
   int shared_cheb;    /* 1: one Chebyshev interval for all blocks (batched mode of Sec. 5.4) */
   int op_ff;          /* FP64-accurate operator apply: 1 float-float on the FP32 pipe (default,
                          about 48 significant bits; |values| within 1e-30..1e30), 0 native FP64 */

@@ -75,3 +75,36 @@ def test_status_texts(capi):
     texts = [lib.irk_strerror(c) for c in codes]
     assert all(texts) and len(set(texts)) == len(codes)
     assert lib.irk_strerror(-99) == b"unknown status"
+
+
+def test_create_refuses_every_documented_bad_argument(capi):
+    """irk_create checks its arguments and options on the host, before any device work."""
+    lib = capi.lib()
+    out = ctypes.c_void_p()
+
+    def create(dim=3, N=4, k=2, Q=3, tau=1e-2, **opt):
+        o = capi.IrkOptions()
+        lib.irk_default_options(ctypes.byref(o))
+        for key, v in opt.items():
+            setattr(o, key, v)
+        mesh = capi.IrkMesh(dim, N)
+        r = lib.irk_create(ctypes.byref(mesh), k, Q, tau, ctypes.byref(o), None, ctypes.byref(out))
+        if r == capi.IRK_OK:   # a machine with a GPU: valid arguments create a solver
+            lib.irk_destroy(out)
+            out.value = None
+        assert out.value is None
+        return r
+
+    E = capi.IRK_EINVAL
+    assert lib.irk_create(None, 2, 2, 0.1, None, None, ctypes.byref(out)) == E
+    for bad in [dict(dim=1), dict(dim=4), dict(N=0), dict(N=4097), dict(k=0), dict(k=5), dict(Q=0), dict(Q=10),
+                dict(tau=0.0), dict(tau=-1e-3), dict(tau=float("inf")), dict(tau=float("nan")), dict(N=1, k=1),
+                dict(rtol=0.0), dict(max_it=0), dict(restart=0), dict(restart=61), dict(cheb_degree=0),
+                dict(cheb_degree=17), dict(mg_precision=16), dict(variant=2), dict(eig_steps=1),
+                dict(smoothing_range=1.0), dict(eig_safety=0.9), dict(pair_precond=2), dict(deform=-0.1),
+                dict(deform=0.2), dict(dim=2, deform=0.2), dict(variant=capi.IRK_VARIANT_DIAG, Q=1)]:
+        assert create(**bad) == E, bad
+    # control: the valid neighbours pass the host checks (without a GPU they fail later, IRK_ECUDA)
+    for good in [dict(), dict(N=1, k=2), dict(dim=2, deform=0.1), dict(variant=capi.IRK_VARIANT_DIAG, Q=2),
+                 dict(restart=60, cheb_degree=16, eig_steps=2, eig_safety=1.0, smoothing_range=1.5)]:
+        assert create(**good) != E, good

@@ -66,6 +66,13 @@ def test_batch_checks_its_arrays(capi):
     per = (ctypes.c_int * 1)(12345)
     assert lib.irk_solve_batch(hs, ys, ts, 1, per) == capi.IRK_EINVAL
     assert per[0] == capi.IRK_EINVAL
+    # the serving loop checks its arrays before any device query
+    res = (capi.IrkResult * 1)()
+    req = (capi.IrkRequest * 1)()
+    assert lib.irk_serve(None, -1, None, None, None) == capi.IRK_EINVAL
+    assert lib.irk_serve(None, 0, None, None, None) == capi.IRK_OK
+    assert lib.irk_serve(None, 1, None, res, None) == capi.IRK_EINVAL
+    assert lib.irk_serve(req, 1, None, None, None) == capi.IRK_EINVAL
 
 
 def test_status_texts(capi):

@@ -60,6 +60,7 @@ def job_throughput(units_per_rank, world, ms_step):
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, profiling recipe's table)
 FF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 15 * 2 / 1e12   # float-float multiply-adds on the FP32 pipe
+FP32_PEAK_TFLOPS = 152 * 128 * 2.07e9 * 2 / 1e12       # FP32 FMA: 152 SMs x 128 lanes x 2.07 GHz x 2
 
 
 def recorded_traffic():
@@ -82,6 +83,22 @@ def algorithmic_flops_per_cell(dim, k):
     (p = k + 1), the per-unit figure the roofline divides by."""
     p = k + 1
     return 14.0 * p ** 4 + 4.0 * p ** 3 if dim == 3 else 8.0 * p ** 3
+
+
+def smoother_alu(w, cheb_degree, avg_launch_ms, fp32=True):
+    """ALU side of the finest-level smoother's roofline: per launch the level operator on all Q blocks
+    in the algorithmic flops of the DoF-space Kronecker form, plus the pointwise epilogue (about 6
+    flops per stage-DoF for a Chebyshev step, 1 for the residual), averaged over the launch mix of
+    a smoothing: 2m - 1 Chebyshev steps and one residual."""
+    m = cheb_degree
+    op = algorithmic_flops_per_cell(w.dim, w.degree) * w.cells ** w.dim * w.Q
+    epi = ((2 * m - 1) * 6.0 + 1.0) / (2 * m) * w.n_interior * w.Q
+    flops = op + epi
+    achieved = flops / (avg_launch_ms / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    src = ("derived: 152 SM x 128 FP32 lanes x 2.07 GHz x 2" if fp32 else "nominal FP64 rate of the profiling recipe")
+    return {"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_launch": flops, "peak_source": src}
 
 
 def flops_per_stage_dof(dim, k):
@@ -568,7 +585,8 @@ def main():
         roof_sm = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                    "traffic": st_traffic, "kernel": sname + " (finest level, Chebyshev steps and residual)",
                    "peak_source": hbm_src, "avg_launch_ms": sm_avg, "bytes_per_launch": bytes_,
-                   "timing": "CUDA events on the solver stream, profiled eager step"}
+                   "timing": "CUDA events on the solver stream, profiled eager step",
+                   "alu": smoother_alu(w, m, sm_avg, fp32=(eb == 4))}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -56,3 +56,13 @@ def test_one_thread_oracle_leg_runs_in_a_child_process():
     got = bench.cpu_baseline_one_thread(w, timeout_s=120)
     assert "error" not in got, got
     assert got["cores"] == 1 and got["value"] > 0 and got["unit"] == bench.UNIT
+
+
+def test_smoother_alu_side_of_the_roofline():
+    from synthetic import HEAT3D_K4_N32_Q3 as w
+    r = bench.smoother_alu(w, 3, 0.069)
+    # 32^3 cells x (14 5^4 + 4 5^3) flops x 3 blocks, + (5 x 6 + 1) / 6 flops x 3 x 2,048,383
+    flops = 32 ** 3 * 9250 * 3 + 31 / 6 * 3 * 2_048_383
+    assert abs(r["flops_per_launch"] - flops) < 1e-6 * flops
+    assert abs(r["achieved"] - flops / 0.069e-3 / 1e12) < 1e-9
+    assert abs(r["peak"] - 152 * 128 * 2.07e9 * 2 / 1e12) < 1e-9 and 0 < r["frac"] < 1

@@ -302,12 +302,18 @@ irk_status irk_mg_restrict(irk_handle h, int level, const void* r_fine, void* b_
  * irk_mg_restrict; the intermediate grids of the axis passes live in one
  * library-owned device array of 24 MiB per device (held by every GPU that loads
  * the library until the process exits) instead of the handle's buffers, and no
- * allocating routine is called.  The first call on a device resolves the
- * array's device address (with that device current) and should come before any
- * stream capture.  Levels needing more than 24 MiB of intermediate grids are
- * rejected with IRK_EINVAL (irk_last_error names the sizes).  Every call shares
- * the array and clears the part it uses; calls that overlap on the GPU race on
- * it and must be serialised by the caller. */
+ * allocating routine is called.  Like the other irk_mg_* calls it works
+ * whatever device is current: the array used is the one on the GPU the handle
+ * was created on.  The first call that uses a GPU resolves the array's device
+ * address there (making that GPU current for the lookup and restoring the
+ * caller's device) and should come before any stream capture; if the lookup
+ * fails it returns IRK_ECUDA and irk_last_error says why.  The address is
+ * cached for the process: after a cudaDeviceReset of that GPU (which also
+ * invalidates every handle created there) the entry point must not be used.
+ * Levels needing more than 24 MiB of intermediate grids are rejected with
+ * IRK_EINVAL (irk_last_error names the sizes).  Every call shares the array
+ * and clears the part it uses; calls that overlap on the GPU race on it and
+ * must be serialised by the caller. */
 irk_status irk_mg_restrict_noalloc(irk_handle h, int level, const void* r_fine, void* b_coarse);
 irk_status irk_mg_prolongate(irk_handle h, int level, const void* e_coarse, void* x_fine);
 irk_status irk_mg_coarse_solve(irk_handle h, const void* b, void* x);

@@ -26,7 +26,7 @@ the 2x2 real form and PRESB).  Modules:
   uniform mesh under a boundary-fixing non-affine map, Sec. 3.4's case of
   mapping data per quadrature point): per-cell matrices by direct
   quadrature with the exact Jacobian, load, initial value, L2 error.
-* ``paper_workload`` - the paper's own manufactured solution (Sec. 6).
+* ``paper_workload`` - the paper's own manufactured solution (Sec. 5).
 * ``mg``      - multigrid ingredients written from their definitions:
   Q_k embedding (prolongation), restriction, Jacobi diagonal, Chebyshev
   iteration, dense coarse solve, one V-cycle, PRESB.

@@ -14,9 +14,11 @@ g_j(t) = phi(t) G_j, G_j = int S phi_j, phi(t) = d pi^2 cos t - sin t.
 Readings: the initial value is the nodal interpolant of u(., 0); the load
 uses Gauss-Legendre (k+1)^d per cell (same rule as the matrices).
 
-Pinned by tests: the load vector against its 1D-product closed form at a
-cell-exact case, and the spatial order k+1 of the whole discretisation
-(tests/test_oracle_irk.py).
+Pinned by tests: the load vector's quadrature rule by exact integration of a
+degree-(2k+1) integrand against polynomial antiderivatives, its tensor-product
+structure, and its entries against adaptive quadrature of int sin(pi x) phi_j
+at the Gauss rule's rate (tests/test_oracle_heat_load.py); the spatial order
+k+1 of the whole discretisation (tests/test_oracle_irk.py).
 """
 import numpy as np
 

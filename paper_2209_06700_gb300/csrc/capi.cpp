@@ -542,11 +542,25 @@ MGBase* lu_mg(irk_problem* h) { return h->mg_sel == 0 ? h->mg.get() : h->mg_diag
 
 }  // namespace
 
-// Restriction with caller-provided scratch, for the allocation-free entry point (noalloc.cu).
-irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, void* scratch, size_t bytes) {
+// Restriction into library-owned scratch, for the allocation-free entry point (noalloc.cu).  The
+// kernels run on the handle's stream, on the GPU the handle was created on, so the scratch address
+// is looked up for that device with that device current; the caller's current device is restored
+// afterwards.  `resolve` returns the array's device address and size for a device index, or a
+// status and a one-line reason that become the handle's last error.
+using ScratchResolver = irk_status (*)(int device, void** addr, size_t* bytes, const char** why);
+irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, ScratchResolver resolve) {
   return guarded(h, [&]() -> Status {
-    if (!r || !bc || !scratch || level < 0 || level + 1 >= lu_mg(h)->levels())
+    if (!r || !bc || level < 0 || level + 1 >= lu_mg(h)->levels())
       return Status::Err(IRK_EINVAL, "bad arguments");
+    int cur = -1;
+    IRK_CUDA(cudaGetDevice(&cur));
+    if (cur != h->device) IRK_CUDA(cudaSetDevice(h->device));
+    void* scratch = nullptr;
+    size_t bytes = 0;
+    const char* why = "";
+    const irk_status rs = resolve(h->device, &scratch, &bytes, &why);
+    if (cur != h->device) IRK_CUDA(cudaSetDevice(cur));
+    if (rs != IRK_OK) return Status::Err(rs, std::string("scratch array: ") + why);
     return lu_mg(h)->restrict_in_scratch(level, r, bc, scratch, bytes, h->st);
   });
 }

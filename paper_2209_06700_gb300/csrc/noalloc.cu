@@ -11,10 +11,13 @@
 //
 // * The array is kNoAllocScratchBytes (24 MiB) per device; every GPU on which
 //   the library's kernels are loaded holds it until the process exits.
-// * Its device address is resolved once per device, with that device current,
-//   by the first call made on that device (cudaGetSymbolAddress; the host-side
-//   name of the array is not a device address).  That first call should come
-//   before any stream capture.
+// * Its device address is resolved once per device, for the GPU the handle was
+//   created on and with that GPU current (cudaGetSymbolAddress; the host-side
+//   name of the array is not a device address), by the first call that uses
+//   that GPU; the caller's current device is restored afterwards.  That first
+//   call should come before any stream capture.  The address is cached for the
+//   life of the process: a cudaDeviceReset of that GPU invalidates it, as it
+//   invalidates every handle created there.
 // * Every call shares the array and it keeps the last call's contents; each
 //   call clears the part it uses first.  Calls whose work overlaps on the GPU
 //   (different streams, different handles) race on the array: serialise them.
@@ -24,7 +27,8 @@
 
 #include "irk.h"
 
-irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, void* scratch, size_t bytes);
+using ScratchResolver = irk_status (*)(int device, void** addr, size_t* bytes, const char** why);
+irk_status irk_restrict_scratch_impl(irk_handle h, int level, const void* r, void* bc, ScratchResolver resolve);
 
 namespace {
 
@@ -35,25 +39,29 @@ constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
+// Device address of the array on `device`, which the caller has made current.
+irk_status resolve_scratch(int device, void** addr, size_t* bytes, const char** why) {
+  if (device < 0 || device >= kMaxDevices) {
+    *why = "device index beyond the 64 devices the address table holds";
+    return IRK_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      *why = "cudaGetSymbolAddress failed (make the first call on a device outside stream capture)";
+      return IRK_ECUDA;
+    }
+    g_scratch_addr[device] = p;
+  }
+  *addr = g_scratch_addr[device];
+  *bytes = kNoAllocScratchBytes;
+  return IRK_OK;
+}
+
 }  // namespace
 
 extern "C" irk_status irk_mg_restrict_noalloc(irk_handle h, int level, const void* r_fine, void* b_coarse) {
-  if (!h) return IRK_EINVAL;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return IRK_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return IRK_EINVAL;
-  void* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return IRK_ECUDA;
-      }
-      g_scratch_addr[dev] = p;
-    }
-    scratch = g_scratch_addr[dev];
-  }
-  return irk_restrict_scratch_impl(h, level, r_fine, b_coarse, scratch, kNoAllocScratchBytes);
+  return irk_restrict_scratch_impl(h, level, r_fine, b_coarse, resolve_scratch);
 }

@@ -215,6 +215,23 @@ const char* irk_last_error(irk_handle h);
  * batched launches of Sec. 5.4). */
 int irk_autotune_report(char* buf, int len);
 
+/* Launch-shape control of the 3D operator kernels (no paper counterpart: it lets tests reach every
+ * launch shape of the streaming kernel, Sec. 3's matrix-free evaluation tiled for the GPU).
+ * irk_op_shape_force makes every later 3D streaming operator launch of one element size use the
+ * given shape, process-wide, until cleared with cxs = 0: elem_bytes 4 for the FP32 multigrid
+ * kernels (level operator, Chebyshev step, residual), 8 for the FP64-accurate stage operator and
+ * K y_n; cxs the cells per warp segment (8, 16 or 32; below 32 only for elem_bytes 4), zc the
+ * cells per z chunk (>= 1), cluster 1 to run the chunks of a tile as one thread-block cluster
+ * (2..16 chunks that the device can hold).  Levels of at most 8 cells per axis keep the cell
+ * kernel.  A forced shape the kernel cannot run makes the launching call fail (IRK_ECUDA); CUDA
+ * graphs captured before the call keep their shapes.  Returns IRK_EINVAL for an unknown element
+ * size or a shape outside these ranges.
+ * irk_op_shape_last writes (cxs, zc, cluster, number of z chunks) of the last such launch of that
+ * element size into out4 (host, 4 ints; -1 each before any launch); IRK_EINVAL for a NULL out4 or
+ * an unknown element size. */
+irk_status irk_op_shape_force(int elem_bytes, int cxs, int zc, int cluster);
+irk_status irk_op_shape_last(int elem_bytes, int* out4);
+
 /* y (device, irk_ndofs doubles) <- nodal interpolant of the manufactured solution
  * u = prod sin(pi x_a) cos t (the initial value of the step; on the curved mesh at the mapped
  * nodes).  IRK_EINVAL for a NULL y. */

@@ -35,7 +35,8 @@ polynomial equals T_m((theta - mu)/delta) / T_m(theta/delta) on every
 eigenpair of D^{-1}A; the prolongation reproduces degree-k polynomials
 exactly; <P^T r, v> = <r, P v>; the V-cycle is symmetric and its two-grid
 error contraction is below one; the PRESB factors multiply to P and the
-PRESB-preconditioned spectrum lies in [1/2, 1].
+PRESB-preconditioned spectrum lies in [1/2, 1]; the sparse prolongation and level operator
+(for meshes beyond the dense forms' reach) equal the dense definitions on small meshes.
 The chosen Chebyshev interval and level count are heuristics:
 parity unpinned beyond the algebraic checks above; only the converged step
 result is pinned as a whole.
@@ -80,6 +81,47 @@ def prolongation(d, Nc, k):
     return P
 
 
+def prolongation_1d(Nc, k):
+    """Dense 1D Q_k embedding (kNf+1 x kNc+1), Nf = 2 Nc: coarse basis functions at the fine nodes
+    of one grid line (no boundary elimination)."""
+    mc, mf = Mesh(1, Nc, k), Mesh(1, 2 * Nc, k)
+    xf = mf.node_coords_1d()
+    xi = gll_nodes(k)
+    P1 = np.zeros((mf.n1, mc.n1))
+    for f in range(mf.n1):
+        s = xf[f] * Nc
+        c = min(int(np.floor(s)), Nc - 1)
+        V, _ = lagrange_values(xi, np.array([s - c]))
+        P1[f, k * c + np.arange(k + 1)] += V[0]
+    return P1
+
+
+def prolongation_sparse(d, Nc, k):
+    """The prolongation of ``prolongation`` as a sparse matrix for larger meshes: on the uniform
+    tensor-product mesh each Q_k basis function is a product of 1D ones, so P is the Kronecker
+    product of the 1D embeddings (x fastest: P1 (x) .. (x) P1 with the z factor first), with the
+    boundary rows and columns zeroed."""
+    import scipy.sparse as sp
+    P1 = sp.csr_matrix(prolongation_1d(Nc, k))
+    P = P1
+    for _ in range(d - 1):
+        P = sp.kron(P1, P, format="csr")
+    mc, mf = Mesh(d, Nc, k), Mesh(d, 2 * Nc, k)
+    keep_f = sp.diags((~mf.boundary_mask()).astype(float))
+    keep_c = sp.diags((~mc.boundary_mask()).astype(float))
+    return (keep_f @ P @ keep_c).tocsr()
+
+
+def level_operator_sparse(d, N, k, lam, tau):
+    """lambda M + tau K as ``level_operator`` but sparse (CSR), boundary rows/columns zeroed."""
+    import scipy.sparse as sp
+    mesh = Mesh(d, N, k)
+    M, K = assemble(mesh)
+    b = mesh.boundary_mask()
+    keep = sp.diags((~b).astype(float))
+    return (keep @ (lam * M + tau * K) @ keep).tocsr(), b
+
+
 def level_operator(d, N, k, lam, tau):
     """Assembled lambda M + tau K on interior DoFs embedded in full-length (dense for small N)."""
     mesh = Mesh(d, N, k)
@@ -92,7 +134,7 @@ def level_operator(d, N, k, lam, tau):
 
 
 def jacobi_diag(A, bmask):
-    D = np.diag(A).copy()
+    D = (A.diagonal() if hasattr(A, "tocsr") else np.diag(A)).copy()
     D[bmask] = 1.0
     return D
 

@@ -94,6 +94,19 @@ def autotune_report():
     return buf.value.decode()
 
 
+def op_shape_force(elem_bytes, cxs=0, zc=1, cluster=0):
+    """Force the launch shape of every later 3D streaming operator launch of one element size
+    (4: FP32 multigrid kernels, 8: FP64-accurate kernels); cxs=0 clears the override."""
+    _capi.check(lib().irk_op_shape_force(elem_bytes, cxs, zc, cluster))
+
+
+def op_shape_last(elem_bytes):
+    """(cxs, zc, cluster, z chunks) of the last 3D streaming operator launch of that element size."""
+    out = (ctypes.c_int * 4)()
+    _capi.check(lib().irk_op_shape_last(elem_bytes, out))
+    return tuple(out)
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 

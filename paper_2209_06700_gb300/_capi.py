@@ -77,6 +77,8 @@ SIGNATURES = {
     "irk_strerror": (ctypes.c_char_p, [_I]),
     "irk_last_error": (ctypes.c_char_p, [_H]),
     "irk_autotune_report": (_I, [ctypes.c_char_p, _I]),
+    "irk_op_shape_force": (_I, [_I, _I, _I, _I]),
+    "irk_op_shape_last": (_I, [_I, ctypes.POINTER(_I)]),
     "irk_interpolate_initial": (_I, [_H, _P, _D]),
     "irk_get_tableau": (_I, [_H, _I, ctypes.POINTER(_D)]),
     "irk_tableau_factors": (_I, [_I, _I, ctypes.POINTER(_D)]),

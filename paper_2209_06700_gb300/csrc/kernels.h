@@ -75,6 +75,13 @@ cudaError_t tune_op(int dim, int k, int nstage, const typename Storage<T>::type*
 void tune_record(const char* kernel, int k, int epi, int N, int nstage, int cxs, int zc, int cluster,
                  double us, double us_model, int model_cxs, int model_zc, int model_cluster);
 int tune_report(char* buf, int len);
+// Test support: a launch shape forced on every later 3D streaming operator launch of one element
+// size (elem 4: the FP32 multigrid kernels, 8: the FP64-accurate kernels; cxs = 0 clears it), and
+// the shape (cxs, zc, cluster, z chunks) of the last such launch.
+void op_shape_force(int elem, int cxs, int zc, int cluster);
+bool op_shape_forced(int elem, int* cxs, int* zc, int* cluster);
+void op_shape_record(int elem, int cxs, int zc, int cluster, int nch);
+bool op_shape_last(int elem, int* out4);
 
 // ---------------- pointwise / vector kernels (vec.cu) ----------------
 

@@ -769,6 +769,7 @@ cudaError_t launch_shape(int nstage, const typename Storage<T>::type* u, const O
   Q.nch = (P.N + Q.zc - 1) / Q.zc;
   Q.cluster = sh.cluster;
   dim3 grid(ntx, Q.ntile_y * Q.nch, nstage);
+  op_shape_record(sizeof(T) == 4 ? 4 : 8, CXS, Q.zc, Q.cluster, Q.nch);
   if (!Q.cluster) {
     kern<<<grid, threads, I::smem, st>>>(u, Q, E);  // a plain launch (pdl.cuh)
     return cudaGetLastError();
@@ -835,7 +836,27 @@ cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u,
                         const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
   if (dim == 3) {
     OpShape sh;
-    if (!OpTuned<T, K, EPI>::find(P.N, nstage, sh)) sh = default_shape<T, K, EPI>(P.N, nstage);
+    if (op_shape_forced(sizeof(T) == 4 ? 4 : 8, &sh.cxs, &sh.zc, &sh.cluster)) {
+      // a forced shape (test support) runs only where this kernel supports it
+      if (sh.cxs != 32 && !(narrow_tiles<T>() && (sh.cxs == 8 || sh.cxs == 16))) return cudaErrorInvalidValue;
+      if (sh.zc < 1) return cudaErrorInvalidValue;
+      if (sh.cluster) {
+        const int nch = (P.N + sh.zc - 1) / sh.zc;
+        const int cy = (sh.cxs == 8) ? Tile3D<T, K, 8>::CY : (sh.cxs == 16) ? Tile3D<T, K, 16>::CY : Tile3D<T, K, 32>::CY;
+        const dim3 grid((P.N + sh.cxs - 1) / sh.cxs, ((P.N + cy - 1) / cy) * nch, nstage);
+        int fit = 0;
+        if constexpr (narrow_tiles<T>()) {
+          fit = (sh.cxs == 8) ? Op3dInfo<T, K, EPI, 8>::clusters_fit(nch, grid)
+                : (sh.cxs == 16) ? Op3dInfo<T, K, EPI, 16>::clusters_fit(nch, grid)
+                                 : Op3dInfo<T, K, EPI, 32>::clusters_fit(nch, grid);
+        } else {
+          fit = Op3dInfo<T, K, EPI, 32>::clusters_fit(nch, grid);
+        }
+        if (fit <= 0) return cudaErrorInvalidConfiguration;
+      }
+    } else if (!OpTuned<T, K, EPI>::find(P.N, nstage, sh)) {
+      sh = default_shape<T, K, EPI>(P.N, nstage);
+    }
     return launch_by_shape<T, K, EPI>(nstage, u, P, E, st, sh);
   }
   int cx, cy;

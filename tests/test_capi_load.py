@@ -60,3 +60,20 @@ def test_host_only_calls():
     assert lib.irk_create(ctypes.byref(mesh), 2, 2, 0.1, None, None, ctypes.byref(out)) == capi.IRK_EINVAL
     assert out.value is None
     del h
+
+
+def test_op_shape_control_on_the_host():
+    """irk_op_shape_force checks its ranges and irk_op_shape_last reports no launch yet (no CUDA call)."""
+    capi = _built_lib()
+    lib = capi.load()
+    E = capi.IRK_EINVAL
+    assert lib.irk_op_shape_force(2, 32, 1, 0) == E           # unknown element size
+    assert lib.irk_op_shape_force(4, 12, 1, 0) == E           # segment width not 8/16/32
+    assert lib.irk_op_shape_force(4, 16, 0, 0) == E           # empty z chunk
+    assert lib.irk_op_shape_force(4, 16, 2, 2) == E           # cluster flag not 0/1
+    out = (ctypes.c_int * 4)()
+    assert lib.irk_op_shape_last(4, None) == E
+    assert lib.irk_op_shape_last(3, out) == E
+    assert lib.irk_op_shape_last(8, out) == capi.IRK_OK and list(out) == [-1, -1, -1, -1]
+    assert lib.irk_op_shape_force(4, 16, 3, 1) == capi.IRK_OK  # valid; cleared again below
+    assert lib.irk_op_shape_force(4, 0, 1, 0) == capi.IRK_OK

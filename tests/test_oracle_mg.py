@@ -166,3 +166,19 @@ def test_coupled_vcycle_contracts_the_error():
     for _ in range(5):  # e <- (I - B A) e
         e = e - cv.apply(A @ e)
     assert np.linalg.norm(e) <= 0.5 ** 5 * e0
+
+
+@pytest.mark.parametrize("d,Nc,k", [(2, 2, 1), (2, 3, 3), (3, 2, 2), (3, 1, 4), (3, 3, 1)])
+def test_sparse_forms_equal_the_dense_definitions(d, Nc, k):
+    """The sparse prolongation (Kronecker product of 1D embeddings) and the sparse level operator
+    equal the dense ones built from their definitions (coarse basis at each fine node; assembled
+    lambda M + tau K with boundary rows and columns zeroed)."""
+    from oracle.mg import level_operator_sparse, prolongation_sparse
+    Pd = prolongation(d, Nc, k)
+    Ps = prolongation_sparse(d, Nc, k).toarray()
+    assert np.abs(Pd - Ps).max() <= 1e-15
+    A, bm = level_operator(d, 2 * Nc, k, 1.7, 0.3)
+    As, bs = level_operator_sparse(d, 2 * Nc, k, 1.7, 0.3)
+    assert np.array_equal(bm, bs)
+    assert np.abs(A - As.toarray()).max() <= 1e-15 * np.abs(A).max()
+    assert np.array_equal(jacobi_diag(A, bm), jacobi_diag(As, bs))

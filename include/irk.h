@@ -75,11 +75,13 @@ typedef struct {
   int batched;        /* 1: all stage blocks in one launch per kernel (default); 0: per-stage launches */
   int use_graph;      /* 1: replay the preconditioner as a CUDA graph (default 1) */
   int eig_steps;      /* Lanczos steps for the Chebyshev interval (default 20; >= 2) */
-  double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 20; > 1) */
+  double smoothing_range; /* Chebyshev interval [hi/range, hi] (default 10; > 1) */
   double eig_safety;  /* hi = safety * Lanczos estimate (default 1.2; >= 1) */
   int shared_cheb;    /* 1: one Chebyshev interval for all blocks (batched mode of Sec. 5.4) */
-  int op_ff;          /* FP64-accurate operator apply: 1 float-float on the FP32 pipe (default,
-                         about 48 significant bits; |values| within 1e-30..1e30), 0 native FP64 */
+  int op_ff;          /* arithmetic of the outer solver (stage operator, Krylov vectors, stage
+                         combinations): 0 native FP64 (default); 1 float-float on the FP32 pipe
+                         (about 48 significant bits, |values| within 1e-30..1e30; faster on GPUs
+                         with a narrow FP64 pipe, not FP64) */
   int autotune;       /* 1: time the 3D operator kernels' launch shapes (tile width, z chunk,
                          cluster) at create on the handle's own buffers and keep the fastest,
                          process-wide per kernel and size (default 1); 0: cost model only */

@@ -170,7 +170,7 @@ def max_eig_DinvA(A, D, bmask):
 class VCycle:
     """One V(m, m)-cycle for lambda M + tau K on the uniform hierarchy (FP64, dense, small N)."""
 
-    def __init__(self, d, N, k, lam, tau, m, bounds=None, smoothing_range=20.0, safety=1.2):
+    def __init__(self, d, N, k, lam, tau, m, bounds=None, smoothing_range=10.0, safety=1.2):
         self.sizes = level_sizes(N, k)
         self.levels = []
         for li, Nl in enumerate(self.sizes):

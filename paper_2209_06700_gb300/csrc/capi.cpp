@@ -94,7 +94,11 @@ Status launch_apply64(irk_problem* h, const S* u, int ns, const double* cm, cons
                       S* out2, int cat = PROF_APPLY64) {
   if constexpr (std::is_same<S, double>::value) {
     if (h->deformed) {  // curved mesh: mapping data per Gauss point, all ns stages in one cell loop
-      IRK_LAUNCH(cat, launch_deformed<double>(h->dd, ns, u, h->fine.ld, epi, cm, ck, out, out2, h->st));
+      // K y_n of the stage right-hand side always in native FP64: on a smooth y_n the stiffness
+      // terms cancel strongly, and float-float's 48 bits would miss the 1e-12 operator bar there
+      DeformDevice<double> dd = h->dd;
+      if (cat == PROF_RHS) dd.ff = false;
+      IRK_LAUNCH(cat, launch_deformed<double>(dd, ns, u, h->fine.ld, epi, cm, ck, out, out2, h->st));
       return Status::Ok();
     }
   } else {
@@ -578,10 +582,10 @@ void irk_default_options(irk_options* o) {
   o->batched = 1;
   o->use_graph = 1;
   o->eig_steps = 20;
-  o->smoothing_range = 20.0;
+  o->smoothing_range = 10.0;
   o->eig_safety = 1.2;
   o->shared_cheb = 0;
-  o->op_ff = 1;
+  o->op_ff = 0;
   o->autotune = 1;
   o->pair_precond = 0;
   o->deform = 0.0;
@@ -711,6 +715,21 @@ const char* irk_strerror(irk_status s) {
 const char* irk_last_error(irk_handle h) { return h ? h->last_err.c_str() : "NULL handle"; }
 
 int irk_autotune_report(char* buf, int len) { return tune_report(buf, len); }
+
+irk_status irk_op_shape_force(int elem_bytes, int cxs, int zc, int cluster) {
+  if (elem_bytes != 4 && elem_bytes != 8) return IRK_EINVAL;
+  if (cxs != 0 && ((cxs != 8 && cxs != 16 && cxs != 32) || zc < 1 || zc > 4096 || (cluster != 0 && cluster != 1)))
+    return IRK_EINVAL;
+  op_shape_force(elem_bytes, cxs, zc, cluster);
+  return IRK_OK;
+}
+
+irk_status irk_op_shape_last(int elem_bytes, int* out4) {
+  if ((elem_bytes != 4 && elem_bytes != 8) || !out4) return IRK_EINVAL;
+  if (!op_shape_last(elem_bytes, out4))
+    for (int i = 0; i < 4; ++i) out4[i] = -1;
+  return IRK_OK;
+}
 
 irk_status irk_interpolate_initial(irk_handle h, double* y, double t) {
   return guarded(h, [&]() -> Status {

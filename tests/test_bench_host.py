@@ -66,3 +66,14 @@ def test_smoother_alu_side_of_the_roofline():
     assert abs(r["flops_per_launch"] - flops) < 1e-6 * flops
     assert abs(r["achieved"] - flops / 0.069e-3 / 1e12) < 1e-9
     assert abs(r["peak"] - 152 * 128 * 2.07e9 * 2 / 1e12) < 1e-9 and 0 < r["frac"] < 1
+
+
+def test_oracle_replicas_use_every_process():
+    """The CPU baseline runs one single-threaded oracle replica per process and reports whole-host
+    throughput: two replicas of a tiny problem report twice the units of one over the slowest time."""
+    import bench
+    from synthetic import Workload
+    w = Workload("tiny", 3, 2, 4, 2, 1e-2, 1)
+    value, nproc, per = bench.oracle_replicas(w, steps=2, nproc=2, timeout_s=120)
+    assert nproc in (1, 2) and per > 0
+    assert abs(value - nproc * w.Q * w.n_interior / per) <= 1e-9 * value

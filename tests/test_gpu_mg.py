@@ -87,7 +87,7 @@ def test_chebyshev_interval_from_lanczos(dim, N, k, Q):
             lo, hi = s.cheb_interval(0, i)
             est = hi / 1.2
             assert 0.95 * true <= est <= true * (1 + 1e-6)
-            assert abs(lo - hi / 20.0) <= 1e-12 * hi
+            assert abs(lo - hi / 10.0) <= 1e-12 * hi   # default smoothing range 10
 
 
 @pytest.mark.parametrize("dim,N,k,Q", CASES)

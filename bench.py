@@ -435,7 +435,8 @@ def main():
     ap.add_argument("--workload", default=HEADLINE.name, choices=sorted(WORKLOADS))
     ap.add_argument("--cells", type=int, default=None,
                     help="override the workload's cells per axis (small cases for profiler captures)")
-    ap.add_argument("--mg-precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--mg-precision", type=int, default=0, choices=[0, 32, 64],
+                    help="multigrid precision: 0 automatic (FP32 up to Q = 5), 32 or 64")
     ap.add_argument("--per-stage", action="store_true", help="per-stage launches (batched=0)")
     ap.add_argument("--variant", default="lu", choices=["lu", "diag"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -490,6 +491,7 @@ def main():
     if args.eig_safety is not None:
         extra["eig_safety"] = args.eig_safety
     cheb = w.cheb_degree if args.cheb_degree is None else args.cheb_degree
+    mg_bits = args.mg_precision or (32 if w.Q <= 5 else 64)   # the library's automatic choice
     s = pkg.Solver(w.dim, w.cells, w.degree, w.Q, w.tau, stream=stream, cheb_degree=cheb,
                    mg_precision=args.mg_precision, batched=0 if args.per_stage else 1, variant=variant,
                    op_ff=args.op_ff, autotune=args.autotune, **extra)
@@ -618,7 +620,7 @@ def main():
         """The finest-level FP32 smoother: algorithmic bytes (16 B per stage-DoF for a Chebyshev step,
         12 B for the residual) against measured HBM, with its ALU side against the FP32 peak."""
         m = cheb
-        eb = 4 if args.mg_precision == 32 else 8
+        eb = 4 if mg_bits == 32 else 8
         per_node = ((2 * m - 1) * 4 * eb + 3 * eb) / (2 * m)
         bytes_ = per_node * w.n_interior * w.Q
         ach = bytes_ / (avg_ms / 1e3) / 1e9
@@ -663,7 +665,7 @@ def main():
     if args.op_ff:
         dtype = "float-float outer (~48 bits) / f32 multigrid"
     else:
-        dtype = "f64 outer / f32 multigrid" if args.mg_precision == 32 else "f64"
+        dtype = "f64 outer / f32 multigrid" if mg_bits == 32 else "f64"
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -675,7 +677,7 @@ def main():
                            "n_interior": w.n_interior, "stage_dofs": units,
                            "launch": "per-stage" if args.per_stage else "stage-batched",
                            "outer_arithmetic": "float-float" if args.op_ff else "fp64",
-                           "variant": args.variant, "mg_precision": args.mg_precision,
+                           "variant": args.variant, "mg_precision": mg_bits,
                            "parallelism": f"replicas x{world}",
                            "smoothing_range": extra.get("smoothing_range", 10.0),
                            "l2": "inputs larger than L2: Krylov basis of several GB > 129 MB; no flush"},

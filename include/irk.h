@@ -71,7 +71,10 @@ typedef struct {
   int restart;        /* Krylov basis size before restart (default 30; 1..60) */
   int cheb_degree;    /* Chebyshev smoother degree per half V-cycle (default 3; 1..16) */
   int variant;        /* IRK_VARIANT_LU (Eq. irk:P) or IRK_VARIANT_DIAG (Eq. irk:Ainv + PRESB) */
-  int mg_precision;   /* 32: FP32 V-cycle (default); 64: FP64 V-cycle */
+  int mg_precision;   /* 0 (default): chosen at create from the preconditioner's basis change:
+                         FP32 while cond_F(S~) (DIAG: cond_F(T)) <= 2e5, i.e. Q <= 5, FP64 above,
+                         where the basis change would magnify FP32 rounding beyond the V-cycle's
+                         own error; 32: FP32 V-cycle; 64: FP64 V-cycle */
   int batched;        /* 1: all stage blocks in one launch per kernel (default); 0: per-stage launches */
   int use_graph;      /* 1: replay the preconditioner as a CUDA graph (default 1) */
   int eig_steps;      /* Lanczos steps for the Chebyshev interval (default 20; >= 2) */

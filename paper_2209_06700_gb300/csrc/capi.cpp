@@ -374,6 +374,19 @@ Status autotune_stage_operator(irk_problem* h) {
   return h->opt.op_ff ? autotune_stage_operator_t<ff>(h) : autotune_stage_operator_t<double>(h);
 }
 
+// Multigrid precision of mg_precision = 0: the preconditioner of Eq. (irk:P) maps the V-cycle's
+// result back through the basis S~ (the real Jordan basis T in the DIAG variant), which magnifies
+// the FP32 rounding of the V-cycle by up to cond(S~).  FP32 while cond_F(S~) 2^-24 stays about two
+// orders below the V-cycle's own error contraction (cond_F <= 2e5: Q <= 5), FP64 above.
+int auto_mg_precision(const Tableau& t, int variant) {
+  const std::vector<double>& B = (variant == IRK_VARIANT_DIAG) ? t.T : t.S;
+  const std::vector<double>& Bi = (variant == IRK_VARIANT_DIAG) ? t.Tinv : t.Sinv;
+  double f = 0.0, fi = 0.0;
+  for (double v : B) f += v * v;
+  for (double v : Bi) fi += v * v;
+  return std::sqrt(f * fi) <= 2e5 ? 32 : 64;
+}
+
 Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt, void* stream,
               irk_problem* h) {
   if (!mesh) return Status::Err(IRK_EINVAL, "mesh is NULL");
@@ -387,7 +400,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   if (opt) h->opt = *opt;
   const irk_options& o = h->opt;
   if (!(o.rtol > 0) || o.max_it < 1 || o.restart < 1 || o.restart > 60 || o.cheb_degree < 1 || o.cheb_degree > 16 ||
-      (o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
+      (o.mg_precision != 0 && o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
       o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1) ||
       (o.pair_precond != 0 && o.pair_precond != 1) || !(o.deform >= 0) ||
       (o.deform > 0 && !deform_valid(mesh->dim, o.deform)))
@@ -407,6 +420,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   IRK_CUDA(cudaGetDevice(&h->device));
   std::string err;
   if (!build_tableau(Q, h->tab, err)) return Status::Err(IRK_EINVAL, err);
+  if (o.mg_precision == 0) h->opt.mg_precision = auto_mg_precision(h->tab, o.variant);
   if (!build_element1d(degree, h->el, err)) return Status::Err(IRK_EINVAL, err);
   h->fine = make_level(h->dim, degree, h->N, h->el);
   const LevelGeom& g = h->fine;
@@ -578,7 +592,7 @@ void irk_default_options(irk_options* o) {
   o->restart = 30;
   o->cheb_degree = 3;
   o->variant = IRK_VARIANT_LU;
-  o->mg_precision = 32;
+  o->mg_precision = 0;
   o->batched = 1;
   o->use_graph = 1;
   o->eig_steps = 20;

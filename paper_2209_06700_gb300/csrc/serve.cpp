@@ -36,7 +36,8 @@ double estimate_bytes(const irk_request& r, const irk_options& o) {
   const double n = std::pow(n1, r.dim);
   const double ld = std::ceil(n / 64.0) * 64.0;
   const double Q = r.Q, ns = std::max(r.Q, 2);
-  const double eb = (o.mg_precision == 64) ? 8.0 : 4.0;
+  // mg_precision 0: FP64 from Q = 6 on, where the basis change of the preconditioner needs it
+  const double eb = (o.mg_precision == 64 || (o.mg_precision == 0 && r.Q >= 6)) ? 8.0 : 4.0;
   double b = (2.0 * o.restart + 2.0) * Q * ld * 8.0;              // V, Z, work vector
   b += (5.0 * ns + 1.0) * ld * 8.0;                               // rhs, stages, M u, K u, T^{-1} rhs, K y
   b += 4.75 * Q * ld * eb * 8.0 / 7.0;                            // multigrid levels and transfer grids

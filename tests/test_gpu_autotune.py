@@ -20,7 +20,7 @@ def test_autotune_records_shapes_and_step_stays_exact():
     with pkg.Solver(d, N, k, Q, tau, stream=torch.cuda.Stream(), autotune=1) as s:
         report = pkg.autotune_report()
         assert f"op3d<float> k={k} cheb N={N} stages={Q}" in report, report
-        assert f"op3d<ff> k={k} dual N={N} stages={Q}" in report, report
+        assert f"op3d<double> k={k} dual N={N} stages={Q}" in report, report   # native FP64 outer (default)
         for line in report.splitlines():
             assert " zc=" in line and " cluster=" in line
         y = s.vector()

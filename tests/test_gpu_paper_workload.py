@@ -6,8 +6,8 @@ u = prod sin(2 pi x_a) (1 + sin pi t) e^{-t/2}, tau = 0.1, loads handed to irk_s
    the LU-based preconditioner of Eq. (irk:P) with (nearly) exact block solves — FP64 multigrid,
    Chebyshev degree 16 — needs about the GMRES iterations the paper reports (5.0, 7.0, 9.9, 11.9
    for Q = 2, 4, 6, 8); the paper's counts belong to its own GMG, so the bar is a band around them.
-   The default FP32 degree-3/5 V-cycles need more outer iterations at this tolerance; their counts
-   are only required to converge.
+   One degree-5 V-cycle per block (FP32 up to Q = 5, FP64 above, the default) stays within +2 of
+   the same column on 64^3 cells.
 3. The directly diagonalised variant with one V-cycle on each coupled 2x2 block (the paper's
    IRK-GMG column) needs at most the paper's iterations.
 """
@@ -63,11 +63,16 @@ def test_lu_preconditioner_iteration_counts_match_the_paper(Q):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("Q", [2, 8])
-def test_default_vcycle_converges_on_the_paper_setup(Q):
-    err, its = _steps(3, 32, 1, Q, 0.1, 2, rtol=1e-12, cheb_degree=5, max_it=400)
+@pytest.mark.parametrize("Q", [2, 4, 6, 8])
+def test_degree5_vcycle_iteration_counts_match_the_paper(Q):
+    """One V-cycle of Chebyshev degree 5 per block (the paper's solver setup, Sec. 5) on 64^3 cells,
+    default options otherwise: FP32 V-cycle up to Q = 5, FP64 from Q = 6 (where the basis change S~
+    of Eq. irk:P would magnify FP32 rounding).  The outer iterations stay within +2 of the paper's
+    IRK column (and not far below it)."""
+    err, its = _steps(3, 64, 1, Q, 0.1, 2, rtol=1e-12, cheb_degree=5, max_it=400)
     assert err <= 1e-9, (err, its)
-    assert max(its) < 60, its
+    paper = PAPER_ITS[Q]
+    assert paper - 3 <= np.mean(its) <= paper + 2, (Q, its, paper)
 
 
 @pytest.mark.slow

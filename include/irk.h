@@ -142,6 +142,7 @@ irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau,
  * IRK_EINVAL for a NULL y.  On IRK_ENOTCONV / IRK_ENUMERIC y is unchanged. */
 irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load,
                     irk_stats* stats);
+/* (irk_step refuses a group handle with IRK_EINVAL: groups step with irk_step_group.) */
 
 /* Advance `count` independent problems by one step each.  hs[i], ys[i],
  * t_ns[i] as in irk_step (built-in source).  Distinct handles run concurrently
@@ -154,6 +155,44 @@ irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_loa
  * their y unchanged as in irk_step. */
 irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int count,
                            irk_status* per_item);
+
+/* ---- groups of requests: shared launches across requests ----
+ * Not in the paper: the paper batches the Q stages of one problem into the same operator and
+ * multigrid sweeps (Sec. 3.4, Sec. 5.4); a group extends that batch across requests.  R independent
+ * heat problems of the same shape (dim, cells, degree, Q), each with its own step tau_r, live in one
+ * handle: their stage vectors are [R][Q][stride], every stage-operator launch, K y_n launch and
+ * V-cycle launch covers all R Q stage vectors or blocks, and each request keeps its own FGMRES
+ * (Krylov basis, Hessenberg matrix, convergence test) in lockstep with the others, one device->host
+ * read-back per iteration for all of them.  Every launch takes the launch shape of a single
+ * request's stage count and every per-stage or per-block result is computed as for that request
+ * alone, so each request's y_{n+1} equals the result of a one-request handle (to rounding, 1e-12
+ * relative).  Groups use the LU variant on the Cartesian mesh; R Q <= 16. */
+
+/* Create a group handle for R requests (taus: host, R steps > 0) of the shape given as in
+ * irk_create.  The multigrid hierarchy holds R Q blocks (lambda~_i M + tau_r K), the Krylov space
+ * R interleaved bases.  IRK_EINVAL as irk_create, and for NULL taus, R < 1, R Q > 16, a
+ * non-positive tau, the DIAG variant or a curved mesh. */
+irk_status irk_create_group(const irk_mesh* mesh, int degree, int Q, int R, const double* taus,
+                            const irk_options* opt, void* cuda_stream, irk_handle* out);
+
+/* One Radau IIA step of every request of a group (or one-request) handle from t_ns[r] (host, R
+ * values): ys (host array of R device pointers, irk_ndofs doubles each) y_n in, y_{n+1} out.  The
+ * built-in source.  stats (host, R entries) and per_item (host, R statuses) may be NULL.  Returns
+ * IRK_OK when every request succeeded, else the first failing status; a failed request (IRK_ENOTCONV,
+ * IRK_ENUMERIC) leaves its y unchanged while the others complete.  IRK_EINVAL for NULL ys or t_ns,
+ * a NULL entry of ys, or a handle of the DIAG variant or curved mesh. */
+irk_status irk_step_group(irk_handle h, double* const* ys, const double* t_ns, irk_stats* stats,
+                          irk_status* per_item);
+
+/* New steps for the requests of a handle (taus: host, irk_group_size(h) values > 0), so that a
+ * handle can serve a later request of the same shape: only what depends on tau is rebuilt, on the
+ * handle's memory (Chebyshev intervals by Lanczos, coarse inverses, fused-cycle parameters; the
+ * captured V-cycle graph is recaptured at the next step).  IRK_EINVAL for NULL taus, a
+ * non-positive tau or the DIAG variant. */
+irk_status irk_set_tau(irk_handle h, const double* taus);
+
+/* Requests in the handle (1 for irk_create), -1 for NULL. */
+int irk_group_size(irk_handle h);
 
 /* ---- serving: continuous batching of single-step requests ---- */
 typedef struct {
@@ -283,16 +322,18 @@ irk_status irk_get_cheb_interval(irk_handle h, int level, int block, double* out
 irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns,
                         const double* Cm_host, const double* Ck_host);
 
-/* v = calA u with calA = A^{-1} (x) M + tau I (x) K (Eq. irk:A), [Q][stride] FP64.
+/* v = calA u with calA = A^{-1} (x) M + tau I (x) K (Eq. irk:A), [Q][stride] FP64; on a group
+ * handle every request's [Q][stride] block with its own tau, u and v [R][Q][stride].
  * IRK_EINVAL for NULL u or v. */
 irk_status irk_apply(irk_handle h, const double* u, double* v);
 
 /* rhs = (A^{-1} (x) I)(gbar - 1 (x) K y_n) (Eq. irk:A right-hand side) with the
- * built-in source; rhs is [Q][stride] FP64.  IRK_EINVAL for NULL y or rhs. */
+ * built-in source; rhs is [Q][stride] FP64.  IRK_EINVAL for NULL y or rhs and for a group handle. */
 irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs);
 
 /* z = P^{-1} r (Eq. irk:P): basis change S~^{-1}, one V-cycle per block in the
- * configured MG precision, basis change S~.  [Q][stride] FP64 in and out.
+ * configured MG precision, basis change S~.  [Q][stride] FP64 in and out ([R][Q][stride] on a
+ * group handle, one V-cycle launch sequence over all R Q blocks).
  * IRK_EINVAL for NULL r or z. */
 irk_status irk_precondition(irk_handle h, const double* r, double* z);
 

@@ -243,3 +243,51 @@ class Solver:
 
     def synchronize(self):
         check(lib().irk_synchronize(self.h), self.h)
+
+
+class Group(Solver):
+    """R requests of one shape (dim, N cells, degree k, Q stages), each with its own step taus[r], in
+    one handle: shared operator and V-cycle launches, one FGMRES per request (irk_create_group)."""
+
+    def __init__(self, dim, cells, degree, Q, taus, stream=None, **opts):
+        import torch
+        self.dim, self.cells, self.degree, self.Q = dim, cells, degree, Q
+        self.taus = [float(t) for t in taus]
+        self.R = len(self.taus)
+        self.tau = self.taus[0]
+        self.opts = options(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        mesh = IrkMesh(dim, cells)
+        h = ctypes.c_void_p()
+        tv = (ctypes.c_double * self.R)(*self.taus)
+        check(lib().irk_create_group(ctypes.byref(mesh), degree, Q, self.R, tv, ctypes.byref(self.opts),
+                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        self.n = lib().irk_ndofs(h)
+        self.n_interior = lib().irk_ninterior(h)
+        self.stride = lib().irk_stage_stride(h)
+        self.levels = lib().irk_num_levels(h)
+
+    def step_group(self, ys, t_ns):
+        """One step of every request (ys: R device vectors, t_ns: R start times); returns
+        (per-request statuses, per-request IrkStats)."""
+        R = lib().irk_group_size(self.h)
+        if len(ys) != R or len(t_ns) != R:
+            raise ValueError("one vector and one time per request")
+        ptrs = (ctypes.c_void_p * R)(*[y.data_ptr() for y in ys])
+        tn = (ctypes.c_double * R)(*[float(t) for t in t_ns])
+        stats = (IrkStats * R)()
+        per = (ctypes.c_int * R)()
+        code = lib().irk_step_group(self.h, ptrs, tn, stats, per)
+        if code != _capi.IRK_OK and all(p == _capi.IRK_OK for p in per):
+            check(code, self.h)
+        return list(per), list(stats)
+
+    def set_tau(self, taus):
+        R = lib().irk_group_size(self.h)
+        tv = (ctypes.c_double * R)(*[float(t) for t in taus])
+        check(lib().irk_set_tau(self.h, tv), self.h)
+        self.taus = list(tv)
+        self.tau = self.taus[0]

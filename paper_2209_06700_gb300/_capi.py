@@ -67,6 +67,11 @@ SIGNATURES = {
     "irk_step": (_I, [_H, _P, _D, _P, ctypes.POINTER(IrkStats)]),
     "irk_solve_batch": (_I, [ctypes.POINTER(_H), ctypes.POINTER(_P), ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
     "irk_destroy": (_I, [_H]),
+    "irk_create_group": (_I, [ctypes.POINTER(IrkMesh), _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(IrkOptions), _P,
+                             ctypes.POINTER(_H)]),
+    "irk_step_group": (_I, [_H, ctypes.POINTER(_P), ctypes.POINTER(_D), ctypes.POINTER(IrkStats), ctypes.POINTER(_I)]),
+    "irk_set_tau": (_I, [_H, ctypes.POINTER(_D)]),
+    "irk_group_size": (_I, [_H]),
     "irk_default_serve_options": (None, [ctypes.POINTER(IrkServeOptions)]),
     "irk_serve": (_I, [ctypes.POINTER(IrkRequest), _I, ctypes.POINTER(IrkServeOptions), ctypes.POINTER(IrkResult),
                        ctypes.POINTER(ctypes.POINTER(ctypes.c_double))]),

@@ -47,6 +47,12 @@ struct irk_problem {
   double *Ky = nullptr, *rhs = nullptr, *kst = nullptr, *Mu = nullptr, *Ku = nullptr, *G1 = nullptr,
          *x1d = nullptr, *tq = nullptr;
   int nslots = 0;                                   // stage slots of Mu/Ku
+  // requests batched in this handle (irk_create_group): R problems of the same shape, each with its
+  // own tau; stage vectors [R][Q][stride], hierarchy blocks [R][Q], Krylov vectors interleaved
+  int R = 1;
+  std::vector<double> taus;                         // tau of each request
+  double* Yg = nullptr;                             // y_n of the requests side by side [R][stride]
+  GroupScalars gsc;                                 // per-request Krylov scalars of group steps
   int mg_sel = 0;                                   // hierarchy of the irk_mg_* entry points (irk_mg_select)
   // curved mesh (opt.deform > 0): mapping data, cell-wise buffers, full load vector
   bool deformed = false;
@@ -56,6 +62,7 @@ struct irk_problem {
   Profiler prof;
   std::string last_err;
   ~irk_problem() {
+    group_scalars_release(gsc);
     pinned_block_release(fw.hvals);
     if (fwd.hvals != fw.hvals) pinned_block_release(fwd.hvals);
   }
@@ -106,6 +113,8 @@ Status launch_apply64(irk_problem* h, const S* u, int ns, const double* cm, cons
   }
   using T = typename std::conditional<std::is_same<S, ff>::value, ff, double>::type;
   OpParams<T> P = make_op_params<T>(h->fine, ns, cm, ck);
+  // a launch over the stage vectors of several requests takes the launch shape of one request's
+  P.shape_ns = (h->R > 1 && ns % h->R == 0) ? ns / h->R : 0;
   EpiParams<S> E;
   std::memset(&E, 0, sizeof(E));
   E.out = out;
@@ -326,6 +335,107 @@ Status step_diag(irk_problem* h, double* y, double t_n, const double* loads, irk
   return Status::Ok();
 }
 
+// ---- groups of requests (irk_create_group): shared launches, one FGMRES per request ----
+
+// v_r = (A^{-1} (x) M + tau_r I (x) K) u_r for every request r: M and K of all R Q stage vectors in
+// one launch, then each request's combination with its own tau
+template <typename S>
+Status apply_calA_group(irk_problem* h, const S* u, S* v) {
+  const int Q = h->Q, R = h->R;
+  const LevelGeom& g = h->fine;
+  const long long len = (long long)Q * g.ld;
+  S* Mu = as<S>(h->Mu);
+  S* Ku = as<S>(h->Ku);
+  IRK_TRY(launch_apply64<S>(h, u, R * Q, nullptr, nullptr, EPI_DUAL, Mu, Ku));
+  std::vector<double> Ck((size_t)Q * Q, 0.0);
+  for (int r = 0; r < R; ++r) {
+    for (int i = 0; i < Q; ++i) Ck[(size_t)i * Q + i] = h->taus[r];
+    CombineParams C = combine_params(Q, Q, h->tab.Ainv.data(), Ck.data(), Q);
+    IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, S>(Mu + r * len, Ku + r * len, v + r * len, g.n, g.ld, C, h->st));
+  }
+  return Status::Ok();
+}
+
+// z_r = P^{-1} r_r (Eq. irk:P) for every request: basis changes per request, one V-cycle over all
+// R Q blocks
+template <typename S>
+Status precondition_group(irk_problem* h, const S* r_all, S* z_all) {
+  const int Q = h->Q, R = h->R;
+  const LevelGeom& g = h->fine;
+  const long long len = (long long)Q * g.ld;
+  MGBase* mg = h->mg.get();
+  CombineParams Cin = combine_params(Q, Q, h->tab.Sinv.data());
+  CombineParams Cout = combine_params(Q, Q, h->tab.S.data());
+  for (int r = 0; r < R; ++r) {
+    if (mg->elem_size() == 4)
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, float>(r_all + r * len, nullptr, (float*)mg->fine_b() + r * len,
+                                                         g.n, g.ld, Cin, h->st));
+    else
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<S, S, double>(r_all + r * len, nullptr, (double*)mg->fine_b() + r * len,
+                                                          g.n, g.ld, Cin, h->st));
+  }
+  IRK_TRY(mg->vcycle_top(h->st, h->opt.use_graph != 0));
+  for (int r = 0; r < R; ++r) {
+    if (mg->elem_size() == 4)
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<float, S, S>((const float*)mg->fine_x() + r * len, nullptr, z_all + r * len,
+                                                         g.n, g.ld, Cout, h->st));
+    else
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<double, S, S>((const double*)mg->fine_x() + r * len, nullptr,
+                                                          z_all + r * len, g.n, g.ld, Cout, h->st));
+  }
+  return Status::Ok();
+}
+
+// One step of every request: ys[r] (device) y_n -> y_{n+1} from t_ns[r].  Per-request results in
+// stats / sts; a request that fails keeps its y.
+template <typename S>
+Status step_group_t(irk_problem* h, double* const* ys, const double* t_ns, std::vector<FGMRESResult>& res,
+                    std::vector<Status>& sts) {
+  const int Q = h->Q, R = h->R;
+  const LevelGeom& g = h->fine;
+  const long long len = (long long)Q * g.ld;
+  double* Y = (R > 1) ? h->Yg : ys[0];
+  if (R > 1)
+    for (int r = 0; r < R; ++r)
+      IRK_CUDA(cudaMemcpyAsync(Y + (size_t)r * g.ld, ys[r], (size_t)g.n * sizeof(double), cudaMemcpyDeviceToDevice,
+                               h->st));
+  // K y_n of every request in one launch
+  const S* yin;
+  if constexpr (std::is_same<S, ff>::value) {
+    IRK_LAUNCH(PROF_RHS, launch_to_ff(Y, as<ff>(h->Mu), (long long)R * g.ld, h->st));
+    yin = as<ff>(h->Mu);
+  } else {
+    yin = Y;
+  }
+  std::vector<double> zero(R, 0.0), one(R, 1.0);
+  IRK_TRY(launch_apply64<S>(h, yin, R, zero.data(), one.data(), EPI_STORE, as<S>(h->Ky), nullptr, PROF_RHS));
+  S* rhs = as<S>(h->rhs);
+  S* kst = as<S>(h->kst);
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r < R; ++r) {
+    RhsParams Rp;
+    std::memset(&Rp, 0, sizeof(Rp));
+    Rp.Q = Q;
+    for (int i = 0; i < Q; ++i)
+      for (int j = 0; j < Q; ++j) Rp.Ainv[i * kMaxQ + j] = h->tab.Ainv[i * Q + j];
+    for (int j = 0; j < Q; ++j) {
+      const double t = t_ns[r] + h->tab.c[j] * h->taus[r];
+      Rp.phi[j] = h->dim * pi * pi * std::cos(t) - std::sin(t);
+    }
+    IRK_LAUNCH(PROF_RHS, launch_stage_rhs<S>(g.grid(), Rp, as<S>(h->Ky) + r * g.ld, h->G1, h->Gv, nullptr,
+                                             rhs + r * len, h->st));
+  }
+  ApplyFn<S> op = [h](const S* in, S* out) { return apply_calA_group<S>(h, in, out); };
+  ApplyFn<S> prec = [h](const S* in, S* out) { return precondition_group<S>(h, in, out); };
+  IRK_TRY(fgmres_solve_group<S>(h->fw, R, h->gsc, op, prec, rhs, kst, h->opt.rtol, h->opt.max_it, h->st, res, sts));
+  for (int r = 0; r < R; ++r) {
+    if (sts[r].ok() && !res[r].converged) sts[r] = Status::Err(IRK_ENOTCONV, "FGMRES did not converge");
+    if (sts[r].ok())
+      IRK_LAUNCH(PROF_RHS, launch_update<S>(g.grid(), Q, kst + r * len, h->tab.b.data(), h->taus[r], ys[r], h->st));
+  }
+  return Status::Ok();
+}
+
 Status step(irk_problem* h, double* y, double t_n, const double* loads, irk_stats* stats) {
   const bool diag = (h->opt.variant == IRK_VARIANT_DIAG);
   if (h->opt.op_ff) return diag ? step_diag<ff>(h, y, t_n, loads, stats) : step_lu<ff>(h, y, t_n, loads, stats);
@@ -388,7 +498,7 @@ int auto_mg_precision(const Tableau& t, int variant) {
 }
 
 Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt, void* stream,
-              irk_problem* h) {
+              irk_problem* h, int R = 1, const double* taus = nullptr) {
   if (!mesh) return Status::Err(IRK_EINVAL, "mesh is NULL");
   if (mesh->dim != 2 && mesh->dim != 3) return Status::Err(IRK_EINVAL, "dim must be 2 or 3");
   if (mesh->cells_per_axis < 1 || mesh->cells_per_axis > 4096) return Status::Err(IRK_EINVAL, "cells_per_axis out of range");
@@ -406,6 +516,17 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
       (o.deform > 0 && !deform_valid(mesh->dim, o.deform)))
     return Status::Err(IRK_EINVAL, "invalid options");
   if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
+  if (R < 1 || R * Q > kMaxStages) return Status::Err(IRK_EINVAL, "a group holds 1..16/Q requests");
+  if (R > 1 && (o.variant != IRK_VARIANT_LU || o.deform > 0))
+    return Status::Err(IRK_EINVAL, "groups of requests use the LU variant on the Cartesian mesh");
+  h->R = R;
+  h->taus.assign(R, tau);
+  if (taus)
+    for (int r = 0; r < R; ++r) {
+      if (!(taus[r] > 0) || !std::isfinite(taus[r])) return Status::Err(IRK_EINVAL, "tau must be positive");
+      h->taus[r] = taus[r];
+    }
+  tau = h->taus[0];
   // curved mesh: FP64 stage vectors; op_ff picks the operator's arithmetic (float-float or FP64)
   const int deform_ff = o.op_ff;
   if (o.deform > 0) h->opt.op_ff = 0;
@@ -424,9 +545,10 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   if (!build_element1d(degree, h->el, err)) return Status::Err(IRK_EINVAL, err);
   h->fine = make_level(h->dim, degree, h->N, h->el);
   const LevelGeom& g = h->fine;
-  h->nslots = std::max(Q, 2);
+  h->nslots = std::max(R * Q, 2);
   const size_t vq = (size_t)h->nslots * g.ld * sizeof(double);
-  IRK_TRY(h->arena.alloc((void**)&h->Ky, g.ld * sizeof(double)));
+  IRK_TRY(h->arena.alloc((void**)&h->Ky, (size_t)R * g.ld * sizeof(double)));
+  if (R > 1) IRK_TRY(h->arena.alloc((void**)&h->Yg, (size_t)R * g.ld * sizeof(double)));
   IRK_TRY(h->arena.alloc((void**)&h->rhs, vq));
   IRK_TRY(h->arena.alloc((void**)&h->kst, vq));
   IRK_TRY(h->arena.alloc((void**)&h->Mu, vq));
@@ -512,14 +634,20 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   mc.smoothing_range = o.smoothing_range; mc.eig_safety = o.eig_safety;
   mc.shared_cheb = o.shared_cheb; mc.batched = o.batched; mc.precision = o.mg_precision;
   mc.autotune = o.autotune;
-  // LU blocks (also used by the per-step entry points of the C ABI)
-  mc.nb = Q;
-  mc.cm = h->tab.lam;
+  // LU blocks (also used by the per-step entry points of the C ABI); a group's blocks are [R][Q]
+  mc.nb = R * Q;
+  mc.cm.clear();
+  for (int r = 0; r < R; ++r) mc.cm.insert(mc.cm.end(), h->tab.lam.begin(), h->tab.lam.end());
+  if (R > 1)
+    for (int r = 0; r < R; ++r) mc.taus.insert(mc.taus.end(), Q, h->taus[r]);
+  mc.shape_ns = Q;
   IRK_TRY(make_mg(mc, h->el, h->arena, h->st, h->mg));
-  IRK_TRY(fgmres_alloc(h->fw, Q, g.ld, o.restart, h->arena, h->st));
+  IRK_TRY(fgmres_alloc(h->fw, R * Q, g.ld, o.restart, h->arena, h->st));
+  IRK_TRY(group_scalars_alloc(h->gsc, R, h->arena, h->st));
   if (o.variant == IRK_VARIANT_DIAG) {
     for (const auto& blk : h->tab.blocks) {
       MGConfig md = mc;
+      md.shape_ns = 0;
       md.nb = 1;
       md.shared_cheb = 0;
       md.cm = {blk.pair ? blk.alpha + blk.beta : blk.alpha};
@@ -632,9 +760,86 @@ irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const
   return IRK_OK;
 }
 
+irk_status irk_create_group(const irk_mesh* mesh, int degree, int Q, int R, const double* taus,
+                            const irk_options* opt, void* cuda_stream, irk_handle* out) {
+  if (!out) return IRK_EINVAL;
+  *out = nullptr;
+  if (!taus || R < 1) return IRK_EINVAL;
+  irk_problem* h = nullptr;
+  try {
+    h = new irk_problem();
+  } catch (...) {
+    return IRK_ENOMEM;
+  }
+  Status s;
+  try {
+    s = create(mesh, degree, Q, taus[0], opt, cuda_stream, h, R, taus);
+  } catch (const std::bad_alloc&) {
+    s = Status::Err(IRK_ENOMEM, "host allocation failed");
+  } catch (...) {
+    s = Status::Err(IRK_ECUDA, "unexpected exception");
+  }
+  if (!s.ok()) {
+    cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    delete h;
+    return s.code;
+  }
+  *out = h;
+  return IRK_OK;
+}
+
+int irk_group_size(irk_handle h) { return h ? h->R : -1; }
+
+irk_status irk_step_group(irk_handle h, double* const* ys, const double* t_ns, irk_stats* stats,
+                          irk_status* per_item) {
+  return guarded(h, [&]() -> Status {
+    if (!ys || !t_ns) return Status::Err(IRK_EINVAL, "ys or t_ns is NULL");
+    for (int r = 0; r < h->R; ++r)
+      if (!ys[r]) return Status::Err(IRK_EINVAL, "ys holds a NULL vector");
+    if (h->opt.variant != IRK_VARIANT_LU || h->deformed)
+      return Status::Err(IRK_EINVAL, "group steps use the LU variant on the Cartesian mesh");
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<FGMRESResult> res;
+    std::vector<Status> sts;
+    Status s = h->opt.op_ff ? step_group_t<ff>(h, ys, t_ns, res, sts) : step_group_t<double>(h, ys, t_ns, res, sts);
+    IRK_CUDA(cudaStreamSynchronize(h->st));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (!s.ok()) return s;
+    Status first = Status::Ok();
+    for (int r = 0; r < h->R; ++r) {
+      if (stats) {
+        stats[r].iterations = res[r].iterations;
+        stats[r].vcycles = res[r].iterations;
+        stats[r].rel_residual = res[r].rel_residual;
+        stats[r].reorth_passes = res[r].reorth;
+        stats[r].ms_total = ms;
+      }
+      if (per_item) per_item[r] = sts[r].code;
+      if (!sts[r].ok() && first.ok()) first = sts[r];
+    }
+    return first;
+  });
+}
+
+irk_status irk_set_tau(irk_handle h, const double* taus) {
+  return guarded(h, [&]() -> Status {
+    if (!taus) return Status::Err(IRK_EINVAL, "taus is NULL");
+    if (h->opt.variant != IRK_VARIANT_LU) return Status::Err(IRK_EINVAL, "irk_set_tau needs the LU variant");
+    for (int r = 0; r < h->R; ++r)
+      if (!(taus[r] > 0) || !std::isfinite(taus[r])) return Status::Err(IRK_EINVAL, "tau must be positive");
+    std::vector<double> blocks;
+    for (int r = 0; r < h->R; ++r) blocks.insert(blocks.end(), h->Q, taus[r]);
+    IRK_TRY(h->mg->retau(blocks, h->st));
+    for (int r = 0; r < h->R; ++r) h->taus[r] = taus[r];
+    h->tau = taus[0];
+    return Status::Ok();
+  });
+}
+
 irk_status irk_step(irk_handle h, double* y, double t_n, const double* stage_load, irk_stats* stats) {
   return guarded(h, [&]() -> Status {
     if (!y) return Status::Err(IRK_EINVAL, "y is NULL");
+    if (h->R > 1) return Status::Err(IRK_EINVAL, "a group handle steps with irk_step_group");
     auto t0 = std::chrono::steady_clock::now();
     Status s = step(h, y, t_n, stage_load, stats);
     IRK_CUDA(cudaStreamSynchronize(h->st));
@@ -858,6 +1063,11 @@ irk_status irk_apply_op(irk_handle h, const double* u, double* v, int ns, const 
 irk_status irk_apply(irk_handle h, const double* u, double* v) {
   return guarded(h, [&]() -> Status {
     if (!u || !v) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (h->R > 1) {  // every request's stage vectors, [R][Q][stride]
+      if (!h->opt.op_ff) return apply_calA_group<double>(h, u, v);
+      const long long len = (long long)h->R * h->Q * h->fine.ld;
+      return with_ff_io(h, u, len, v, len, [&](const ff* a, ff* b) { return apply_calA_group<ff>(h, a, b); });
+    }
     if (!h->opt.op_ff) return apply_calA<double>(h, u, v);
     const long long len = (long long)h->Q * h->fine.ld;
     return with_ff_io(h, u, len, v, len, [&](const ff* a, ff* b) { return apply_calA<ff>(h, a, b); });
@@ -867,6 +1077,7 @@ irk_status irk_apply(irk_handle h, const double* u, double* v) {
 irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs) {
   return guarded(h, [&]() -> Status {
     if (!y || !rhs) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (h->R > 1) return Status::Err(IRK_EINVAL, "a group handle forms its right-hand sides in irk_step_group");
     if (!h->opt.op_ff) return stage_rhs<double>(h, y, t_n, nullptr, rhs);
     IRK_TRY(stage_rhs<ff>(h, y, t_n, nullptr, as<ff>(h->kst)));
     IRK_LAUNCH(PROF_RHS, launch_from_ff(as<ff>(h->kst), rhs, (long long)h->Q * h->fine.ld, h->st));
@@ -877,6 +1088,11 @@ irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs)
 irk_status irk_precondition(irk_handle h, const double* r, double* z) {
   return guarded(h, [&]() -> Status {
     if (!r || !z) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (h->R > 1) {  // every request's stage vectors, [R][Q][stride]
+      if (!h->opt.op_ff) return precondition_group<double>(h, r, z);
+      const long long len = (long long)h->R * h->Q * h->fine.ld;
+      return with_ff_io(h, r, len, z, len, [&](const ff* a, ff* b) { return precondition_group<ff>(h, a, b); });
+    }
     if (!h->opt.op_ff) return precondition_lu<double>(h, r, z);
     const long long len = (long long)h->Q * h->fine.ld;
     return with_ff_io(h, r, len, z, len, [&](const ff* a, ff* b) { return precondition_lu<ff>(h, a, b); });

@@ -179,7 +179,7 @@ __device__ __forceinline__ int dslot(int ix, int iy, int iz) {
 template <typename T, int K, int DIM>
 __device__ void smooth(const CoarseLevel& L, const CoarseParams& P, int s, T* x, T* xo, const T* b, T* t1, T* t2,
                        T* t3, T* t4, const T* invd, bool from_zero) {
-  const T cm = (T)P.cm[s], ck = (T)P.tau;
+  const T cm = (T)P.cm[s], ck = (T)P.taus[s];
   const int n = L.n;
   int j0 = 0;
   if (from_zero) {
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kCT) coarse_cycle_kernel(const CoarseParams P)
   for (int i = threadIdx.x; i < nlev * KD; i += blockDim.x) {
     const int l = i / KD, t = i - l * KD;
     const int rx = t % K, ry = (t / K) % K, rz = (DIM == 3) ? t / (K * K) : 0;
-    sinv[l][t] = inv_diag<T, K, DIM>(P.lv[l], (T)P.cm[s], (T)P.tau, rx, ry, rz);
+    sinv[l][t] = inv_diag<T, K, DIM>(P.lv[l], (T)P.cm[s], (T)P.taus[s], rx, ry, rz);
   }
   __syncthreads();
   const T* bin = reinterpret_cast<const T*>(P.b_in) + (long long)s * P.ld;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kCT) coarse_cycle_kernel(const CoarseParams P)
     smooth<T, K, DIM>(L, P, s, x[l], xo[l], b[l], t1, t2, t3, t4, sinv[l], true);
     T* rl = r[l];
     const T* bl = b[l];
-    apply_level<T, K, DIM>(L, (T)P.cm[s], (T)P.tau, x[l], t1, t2, t3, t4,
+    apply_level<T, K, DIM>(L, (T)P.cm[s], (T)P.taus[s], x[l], t1, t2, t3, t4,
                            [&](int q, int, int, int, T av) { rl[q] = bl[q] - av; });
     const int nf = L.n1, nc = P.lv[l + 1].n1, Nc = P.lv[l + 1].N;
     if (DIM == 3) {

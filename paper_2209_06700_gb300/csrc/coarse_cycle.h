@@ -20,13 +20,13 @@ struct CoarseLevel {
   unsigned magic;                       // coarse_cycle_magic(n1): q / n1 by a high multiply
   float me[5][5], ke[5][5];             // element matrices scaled by h and 1/h
   float dmr[kMaxDeg], dkr[kMaxDeg];     // 1D diagonals by node position mod k
-  float c1[kMaxChebDegree][kMaxQ], c2[kMaxChebDegree][kMaxQ];  // Chebyshev recurrence per step, block
+  float c1[kMaxChebDegree][kMaxStages], c2[kMaxChebDegree][kMaxStages];  // Chebyshev recurrence per step, block
 };
 
 struct CoarseParams {
   int nlev, nb, m, nci;
-  float cm[kMaxQ];
-  float tau;
+  float cm[kMaxStages];
+  float taus[kMaxStages];                // stiffness coefficient tau of each block
   CoarseLevel lv[kMaxFusedLevels];      // lv[0] = the finest fused level
   float pc[(2 * kMaxDeg + 1) * (kMaxDeg + 1)];
   const float* ainv;                    // [nb][nci][nci] dense coarse inverse (FP32 copy)

@@ -9,6 +9,7 @@
 // Gram-Schmidt kernel by its last block, and the Hessenberg/Givens update runs
 // on the host with one device->host transfer per iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -236,6 +237,251 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
   res.iterations = total;
   return Status::Ok();
 }
+
+Status group_scalars_alloc(GroupScalars& g, int R, DeviceArena& arena, cudaStream_t st) {
+  IRK_TRY(arena.alloc((void**)&g.dvals, (size_t)R * 256 * sizeof(double)));
+  IRK_TRY(arena.alloc((void**)&g.fvals, (size_t)R * 256 * sizeof(ff)));
+  IRK_TRY(arena.alloc((void**)&g.count, (size_t)R * 64 * sizeof(unsigned)));
+  IRK_CUDA(cudaMemsetAsync(g.count, 0, (size_t)R * 64 * sizeof(unsigned), st));
+  const ff one{1.0f, 0.0f};
+  for (int r = 0; r < R; ++r) {
+    double* hv = pinned_block_acquire();
+    if (!hv) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
+    g.hvals.push_back(hv);
+    hv[kOne] = 1.0;
+    std::memcpy(&hv[kOne - 1], &one, sizeof(ff));
+    IRK_CUDA(cudaMemcpyAsync(g.dvals + (size_t)r * 256 + kOne, hv + kOne, sizeof(double), cudaMemcpyHostToDevice, st));
+    IRK_CUDA(cudaMemcpyAsync(g.fvals + (size_t)r * 256 + kOne, hv + kOne - 1, sizeof(ff), cudaMemcpyHostToDevice, st));
+  }
+  IRK_CUDA(cudaStreamSynchronize(st));
+  return Status::Ok();
+}
+
+void group_scalars_release(GroupScalars& g) {
+  for (double* p : g.hvals) pinned_block_release(p);
+  g.hvals.clear();
+}
+
+namespace {
+
+// One request's view of the group scalars in the layout of FGMRESWork (coefficients, norms, counter).
+FGMRESWork request_view(const FGMRESWork& w, const GroupScalars& gs, int r, int R) {
+  FGMRESWork v = w;
+  v.len = w.len / R;
+  v.nb = reduction_blocks(v.len);
+  v.dvals = gs.dvals + (size_t)r * 256;
+  v.fvals = gs.fvals + (size_t)r * 256;
+  v.hvals = gs.hvals[r];
+  v.count = gs.count + (size_t)r * 64;
+  return v;
+}
+
+}  // namespace
+
+template <typename S>
+Status fgmres_solve_group(FGMRESWork& w, int R, GroupScalars& gs, const ApplyFn<S>& op, const ApplyFn<S>& prec,
+                          const S* b, S* x, double rtol, int max_it, cudaStream_t st,
+                          std::vector<FGMRESResult>& res, std::vector<Status>& st_out) {
+  const long long all = w.len, len = w.len / R;
+  const int m = w.m;
+  S* V = reinterpret_cast<S*>(w.V);
+  S* Z = reinterpret_cast<S*>(w.Z);
+  S* tmp = reinterpret_cast<S*>(w.tmp);
+  res.assign(R, FGMRESResult());
+  st_out.assign(R, Status::Ok());
+  std::vector<FGMRESWork> wv(R);
+  for (int r = 0; r < R; ++r) wv[r] = request_view(w, gs, r, R);
+  auto cf = [&](int r) { return coefs<S>(wv[r]); };
+  IRK_CUDA(cudaMemsetAsync(x, 0, (size_t)all * sizeof(S), st));
+  IRK_CUDA(cudaMemsetAsync(gs.count, 0, (size_t)R * 64 * sizeof(unsigned), st));
+  // norms of every request's vector at once (one read-back): out[r] = |v_r|
+  auto norms = [&](const S* v, const std::vector<bool>& which, std::vector<double>& out) -> Status {
+    for (int r = 0; r < R; ++r) {
+      if (!which[r]) continue;
+      int nb = wv[r].nb;
+      RowSink Rk;
+      Rk.out = wv[r].dvals + kNrm;
+      Rk.count = wv[r].count;
+      Rk.take_sqrt = 1;
+      IRK_LAUNCH(PROF_KRYLOV, launch_norm2_partial<S>(v + (size_t)r * len, len, w.partial, nb, Rk, st));
+      IRK_CUDA(cudaMemcpyAsync(wv[r].hvals + kNrm, wv[r].dvals + kNrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    IRK_CUDA(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r)
+      if (which[r]) out[r] = wv[r].hvals[kNrm];
+    return Status::Ok();
+  };
+  std::vector<bool> live(R, true);     // still iterating
+  std::vector<double> bnorm(R, 0.0), beta(R, 0.0), target(R, 0.0);
+  IRK_TRY(norms(b, live, bnorm));
+  for (int r = 0; r < R; ++r) {
+    if (!std::isfinite(bnorm[r])) {
+      st_out[r] = Status::Err(IRK_ENUMERIC, "non-finite right-hand side");
+      live[r] = false;
+    } else if (bnorm[r] == 0.0) {
+      res[r].converged = true;
+      live[r] = false;
+    }
+    target[r] = rtol * bnorm[r];
+    beta[r] = bnorm[r];
+  }
+  // first cycle: r = b (x0 = 0); stopped requests get zero slices
+  for (int r = 0; r < R; ++r) {
+    if (live[r]) IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(b + (size_t)r * len, 1.0 / beta[r], V + (size_t)r * len, len, st));
+    else IRK_CUDA(cudaMemsetAsync(V + (size_t)r * len, 0, (size_t)len * sizeof(S), st));
+  }
+  std::vector<std::vector<double>> H(R, std::vector<double>((size_t)(m + 1) * m)), cs(R, std::vector<double>(m)),
+      sn(R, std::vector<double>(m)), g(R, std::vector<double>(m + 1)), y(R, std::vector<double>(m));
+  std::vector<int> total(R, 0), jlast(R, -1);
+  while (true) {
+    std::vector<bool> cyc = live;  // requests iterating in this cycle
+    for (int r = 0; r < R; ++r) {
+      std::fill(g[r].begin(), g[r].end(), 0.0);
+      g[r][0] = beta[r];
+      jlast[r] = -1;
+    }
+    for (int j = 0; j < m; ++j) {
+      if (std::none_of(cyc.begin(), cyc.end(), [](bool v) { return v; })) break;
+      S* Vj = V + (size_t)j * all;
+      S* Zj = Z + (size_t)j * all;
+      S* W = V + (size_t)(j + 1) * all;
+      IRK_TRY(prec(Vj, Zj));
+      IRK_TRY(op(Zj, W));
+      const int nv = j + 1;
+      for (int r = 0; r < R; ++r) {
+        if (!cyc[r]) continue;
+        FGMRESWork& q = wv[r];
+        const S* Vr = V + (size_t)r * len;
+        S* wr = W + (size_t)r * len;
+        S* tr = tmp + (size_t)r * len;
+        RowSink r1;
+        r1.out = q.dvals + kH1;
+        r1.count = q.count;
+        r1.X.out_ff = q.fvals + kH1;
+        r1.X.copy_out = q.dvals + kN0;
+        r1.X.copy_row = nv;
+        int nb = q.nb;
+        IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(Vr, all, nv, wr, len, w.partial, nb, r1, st));
+        RowSink r2;
+        r2.out = q.dvals + kH2;
+        r2.count = q.count;
+        r2.X.out_ff = q.fvals + kH2;
+        r2.X.decide_flag = q.dvals + kRedo;
+        r2.X.decide_ref = q.dvals + kN0;
+        r2.X.decide_row = nv;
+        r2.X.eta2 = kEta * kEta;
+        nb = q.nb;
+        IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(Vr, all, nv, cf(r) + kH1, wr, tr, len, w.partial, nb, r2, st));
+        RowSink r3;
+        r3.out = q.dvals + kNrm;
+        r3.count = q.count;
+        r3.take_sqrt = 1;
+        r3.X.inv = q.dvals + kInv;
+        r3.X.inv_ff = q.fvals + kInv;
+        nb = q.nb;
+        IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(Vr, all, nv, cf(r) + kH2, q.dvals + kRedo, tr, wr, len, w.partial,
+                                                    nb, r3, st));
+        IRK_CUDA(cudaMemcpyAsync(q.hvals, q.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      }
+      IRK_CUDA(cudaStreamSynchronize(st));
+      for (int r = 0; r < R; ++r) {
+        if (!cyc[r]) continue;
+        FGMRESWork& q = wv[r];
+        const double hn = q.hvals[kNrm];
+        S* wr = W + (size_t)r * len;
+        if (!std::isfinite(hn)) {
+          st_out[r] = Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
+          cyc[r] = live[r] = false;
+          jlast[r] = -1;  // no update of x
+          IRK_CUDA(cudaMemsetAsync(wr, 0, (size_t)len * sizeof(S), st));
+          continue;
+        }
+        const bool redo = q.hvals[kRedo] != 0.0;
+        res[r].reorth += redo ? 1 : 0;
+        std::vector<double>& Hr = H[r];
+        for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = q.hvals[kH1 + i] + (redo ? q.hvals[kH2 + i] : 0.0);
+        Hr[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hr[(size_t)i * m + j], bb = Hr[(size_t)(i + 1) * m + j];
+          Hr[(size_t)i * m + j] = cs[r][i] * a + sn[r][i] * bb;
+          Hr[(size_t)(i + 1) * m + j] = -sn[r][i] * a + cs[r][i] * bb;
+        }
+        const double a = Hr[(size_t)j * m + j], bb = Hr[(size_t)(j + 1) * m + j];
+        const double rr = std::hypot(a, bb);
+        cs[r][j] = (rr == 0.0) ? 1.0 : a / rr;
+        sn[r][j] = (rr == 0.0) ? 0.0 : bb / rr;
+        Hr[(size_t)j * m + j] = rr;
+        Hr[(size_t)(j + 1) * m + j] = 0.0;
+        g[r][j + 1] = -sn[r][j] * g[r][j];
+        g[r][j] = cs[r][j] * g[r][j];
+        ++total[r];
+        jlast[r] = j;
+        const double resid = std::fabs(g[r][j + 1]);
+        res[r].rel_residual = resid / bnorm[r];
+        bool stop = false;
+        if (resid <= target[r]) { res[r].converged = true; stop = true; }
+        if (total[r] >= max_it || hn == 0.0) stop = true;
+        if (stop) {
+          cyc[r] = live[r] = false;
+          IRK_CUDA(cudaMemsetAsync(wr, 0, (size_t)len * sizeof(S), st));  // later shared launches see zeros
+        } else if (hn > 0.0) {
+          IRK_LAUNCH(PROF_KRYLOV, launch_scale_dev<S>(wr, cf(r) + kInv, wr, len, st));
+        }
+      }
+    }
+    // y = H^{-1} g, x += Z y for every request that iterated in this cycle
+    for (int r = 0; r < R; ++r) {
+      const int kk = jlast[r] + 1;
+      if (kk <= 0) continue;
+      for (int i = kk - 1; i >= 0; --i) {
+        double t = g[r][i];
+        for (int c = i + 1; c < kk; ++c) t -= H[r][(size_t)i * m + c] * y[r][c];
+        y[r][i] = t / H[r][(size_t)i * m + i];
+      }
+      IRK_TRY(upload_y<S>(wv[r], y[r], kk, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy<S>(Z + (size_t)r * len, all, kk, cf(r) + kY, 1.0, x + (size_t)r * len, len, st));
+    }
+    if (std::none_of(live.begin(), live.end(), [](bool v) { return v; })) break;
+    // restart the live requests with their explicit residuals (one shared operator launch)
+    IRK_TRY(op(x, tmp));
+    for (int r = 0; r < R; ++r) {
+      if (!live[r]) continue;
+      S* tr = tmp + (size_t)r * len;
+      IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(tr, -1.0, tr, len, st));
+      IRK_LAUNCH(PROF_KRYLOV, launch_multi_axpy<S>(b + (size_t)r * len, 0, 1, cf(r) + kOne, 1.0, tr, len, st));
+    }
+    std::vector<double> nb(R, 0.0);
+    IRK_TRY(norms(tmp, live, nb));
+    for (int r = 0; r < R; ++r) {
+      if (!live[r]) {
+        IRK_CUDA(cudaMemsetAsync(V + (size_t)r * len, 0, (size_t)len * sizeof(S), st));
+        continue;
+      }
+      beta[r] = nb[r];
+      if (!std::isfinite(beta[r])) {
+        st_out[r] = Status::Err(IRK_ENUMERIC, "non-finite restart residual");
+        live[r] = false;
+      } else if (beta[r] <= target[r]) {
+        res[r].converged = true;
+        res[r].rel_residual = beta[r] / bnorm[r];
+        live[r] = false;
+      }
+      if (live[r]) IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(tmp + (size_t)r * len, 1.0 / beta[r], V + (size_t)r * len, len, st));
+      else IRK_CUDA(cudaMemsetAsync(V + (size_t)r * len, 0, (size_t)len * sizeof(S), st));
+    }
+    if (std::none_of(live.begin(), live.end(), [](bool v) { return v; })) break;
+  }
+  IRK_CUDA(cudaStreamSynchronize(st));
+  for (int r = 0; r < R; ++r) res[r].iterations = total[r];
+  return Status::Ok();
+}
+
+template Status fgmres_solve_group<double>(FGMRESWork&, int, GroupScalars&, const ApplyFn<double>&,
+                                           const ApplyFn<double>&, const double*, double*, double, int, cudaStream_t,
+                                           std::vector<FGMRESResult>&, std::vector<Status>&);
+template Status fgmres_solve_group<ff>(FGMRESWork&, int, GroupScalars&, const ApplyFn<ff>&, const ApplyFn<ff>&,
+                                       const ff*, ff*, double, int, cudaStream_t, std::vector<FGMRESResult>&,
+                                       std::vector<Status>&);
 
 template Status fgmres_solve<double>(FGMRESWork&, const ApplyFn<double>&, const ApplyFn<double>&, const double*,
                                      double*, double, int, cudaStream_t, FGMRESResult&);

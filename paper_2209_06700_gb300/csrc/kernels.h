@@ -30,6 +30,9 @@ struct OpParams {
   int ntile_y;         // 3D: number of y tiles (grid.y = ntile_y * nch, chunk index fastest)
   int nch;             // 3D: number of z chunks (set by the launcher)
   int cluster;         // 3D: 1 = the nch chunks of a tile form a thread-block cluster (set by the launcher)
+  int shape_ns;        // 3D: stage count whose launch shape this launch takes (0: nstage).  Launches that
+                       // batch the stages of several requests use the shape of one request's stages, so
+                       // each stage's arithmetic (chunk-boundary summation order) is the same as alone
   T me[kMaxDeg + 1][kMaxDeg + 1];
   T ke[kMaxDeg + 1][kMaxDeg + 1];
   T yvm[2 * kMaxDeg + 1], yvk[2 * kMaxDeg + 1];  // banded taps of a vertex row, offsets -k..k
@@ -245,11 +248,11 @@ cudaError_t launch_transfer_axis(const T* in, T* out, int nstage, long long ld_i
                                  const int din[3], const int dout[3], int axis, int restrict_mode,
                                  int accumulate, const TransferParams& P, cudaStream_t st);
 
-// Exact coarse solve by fast diagonalisation: (cm_s M + tau K)^{-1} = W diag(1/(cm_s + tau mu)) W^T,
+// Exact coarse solve by fast diagonalisation: (cm_s M + tau_s K)^{-1} = W diag(1/(cm_s + tau_s mu)) W^T,
 // W = V (x) V (x) V with V^T M1 V = I, V^T K1 V = diag(mu1) on the interior 1D nodes.
 struct FdParams {
   int ni;                   // interior nodes per axis
-  double tau;
+  double taus[kMaxStages];  // stiffness coefficient tau of each block
   double cm[kMaxStages];
   double beta;              // coupled 2x2 systems (launch_fd_scale_coupled): coupling coefficient
 };
@@ -257,7 +260,7 @@ struct FdParams {
 template <typename Tin, typename Tout>
 cudaError_t launch_fd_axis(const Tin* in, Tout* out, int nstage, long long ld, int n1, int dim, int axis,
                            const double* Mt, int ni, cudaStream_t st);
-// t[interior] *= 1 / (cm_s + tau (mu_a + mu_b (+ mu_c)))
+// t[interior] *= 1 / (cm_s + tau_s (mu_a + mu_b (+ mu_c)))
 cudaError_t launch_fd_scale(double* t, int nstage, long long ld, int n1, int dim, const double* mu,
                             const FdParams& P, cudaStream_t st);
 // The coupled 2x2 system [[A, -beta M], [beta M, A]], A = cm[0] M + tau K, in modal coordinates:

@@ -244,6 +244,14 @@ class MG final : public MGBase {
 
   MG(const MGConfig& c, const Element1D& e, DeviceArena& a) : cfg_(c), el_(e), arena_(a) {}
 
+  // level-operator parameters with the launch-shape key of one request's blocks
+  template <typename U>
+  OpParams<U> opp(const LevelGeom& g, int nstage, const double* cm, const double* ck) const {
+    OpParams<U> P = make_op_params<U>(g, nstage, cm, ck);
+    P.shape_ns = (cfg_.shape_ns > 0 && nstage == cfg_.nb) ? cfg_.shape_ns : 0;
+    return P;
+  }
+
   // Coupled mode: the two blocks are the components of [[A, -beta M], [beta M, A]] (a 2x2 block of
   // the real form of Eq. irk:Ainv, Sec. 6) and one V-cycle acts on the coupled system.
   bool coupled() const { return cfg_.coupled_beta != 0.0; }
@@ -257,7 +265,9 @@ class MG final : public MGBase {
     const int nmin = (cfg_.k == 1) ? 2 : 1;
     while (sizes.back() % 2 == 0 && sizes.back() / 2 >= nmin) sizes.push_back(sizes.back() / 2);
     const int nb = cfg_.nb;
+    if (!cfg_.taus.empty() && (int)cfg_.taus.size() != nb) return Status::Err(IRK_EINVAL, "one tau per block");
     ck_.assign(nb, cfg_.tau);
+    if (!cfg_.taus.empty()) ck_ = cfg_.taus;
     for (size_t l = 0; l < sizes.size(); ++l) {
       Lvl L;
       L.g = make_level(cfg_.dim, cfg_.k, sizes[l], el_);
@@ -298,7 +308,7 @@ class MG final : public MGBase {
     const int last = fused_ ? lc_ : levels() - 1;
     for (int l = 0; l < last; ++l) {
       Lvl& L = lv_[l];
-      OpParams<T> P = make_op_params<T>(L.g, nb, cfg_.cm.data(), ck_.data());
+      OpParams<T> P = opp<T>(L.g, nb, cfg_.cm.data(), ck_.data());
       EpiParams<T> E;
       std::memset(&E, 0, sizeof(E));
       E.out = L.xb;
@@ -344,6 +354,29 @@ class MG final : public MGBase {
     IRK_TRY(vcycle(l + 1, st));
     IRK_TRY(prolongate_add(l, lv_[l + 1].cur, L.cur, st));
     IRK_TRY(cheb(l, L.b, /*from_zero=*/false, st));
+    return Status::Ok();
+  }
+
+  Status retau(const std::vector<double>& taus, cudaStream_t st) override {
+    if ((int)taus.size() != cfg_.nb) return Status::Err(IRK_EINVAL, "one tau per block");
+    for (double t : taus)
+      if (!(t > 0) || !std::isfinite(t)) return Status::Err(IRK_EINVAL, "tau must be positive");
+    if (coupled()) return Status::Err(IRK_EINVAL, "the coupled hierarchy keeps its tau");
+    st_ = st;
+    ck_ = taus;
+    cfg_.taus = taus;
+    if (use_fd_) {
+      for (int s = 0; s < cfg_.nb && s < kMaxStages; ++s) fd_params_.taus[s] = ck_[s];
+    } else {
+      IRK_TRY(setup_coarse());
+    }
+    IRK_TRY(setup_chebyshev(st));
+    IRK_TRY(setup_fused());
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    if (graph_) cudaGraphDestroy(graph_);
+    gexec_ = nullptr;
+    graph_ = nullptr;
+    IRK_CUDA(cudaStreamSynchronize(st));
     return Status::Ok();
   }
 
@@ -411,13 +444,13 @@ class MG final : public MGBase {
     std::memset(&E, 0, sizeof(E));
     E.out = L.mx;
     E.out2 = L.kx;
-    OpParams<T> P = make_op_params<T>(L.g, 2, cfg_.cm.data(), ck_.data());
+    OpParams<T> P = opp<T>(L.g, 2, cfg_.cm.data(), ck_.data());
     if (cheb != 2)
       IRK_LAUNCH(l == 0 ? PROF_MG_OP_FINE : PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, 2, x, P, EPI_DUAL, E, st));
     CoupledParams C;
     std::memset(&C, 0, sizeof(C));
     C.cm = cfg_.cm[0];
-    C.ck = cfg_.tau;
+    C.ck = ck_[0];
     C.beta = cfg_.coupled_beta;
     C.cheb = cheb;
     C.xold_zero = xold_zero ? 1 : 0;
@@ -532,7 +565,7 @@ class MG final : public MGBase {
     EpiParams<T> E;
     std::memset(&E, 0, sizeof(E));
     E.out = (T*)y;
-    OpParams<T> P = make_op_params<T>(lv_[l].g, cfg_.nb, cm.data(), ck.data());
+    OpParams<T> P = opp<T>(lv_[l].g, cfg_.nb, cm.data(), ck.data());
     IRK_LAUNCH(PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, cfg_.nb, (const T*)x, P, EPI_STORE, E, st));
     return Status::Ok();
   }
@@ -555,12 +588,12 @@ class MG final : public MGBase {
     Lvl& L = lv_[l];
     const int nb = cfg_.nb;
     if (cfg_.batched) {
-      OpParams<T> P = make_op_params<T>(L.g, nb, cfg_.cm.data(), ck_.data());
+      OpParams<T> P = opp<T>(L.g, nb, cfg_.cm.data(), ck_.data());
       IRK_LAUNCH(l == 0 ? PROF_MG_OP_FINE : PROF_MG_OP, launch_op<T>(cfg_.dim, cfg_.k, nb, u, P, epi, E, st));
       return Status::Ok();
     }
     for (int s = 0; s < nb; ++s) {
-      OpParams<T> P = make_op_params<T>(L.g, 1, &cfg_.cm[s], &ck_[s]);
+      OpParams<T> P = opp<T>(L.g, 1, &cfg_.cm[s], &ck_[s]);
       EpiParams<T> Es = E;
       const long long off = (long long)s * L.g.ld;
       Es.out = E.out ? E.out + off : nullptr;
@@ -659,14 +692,14 @@ class MG final : public MGBase {
             for (int b = 0; b < dim; ++b) if (b != a) t *= mv[b];
             kterm += t;
           }
-          A[(size_t)q * nci_ + r] = cfg_.cm[s] * mprod + cfg_.tau * kterm;
+          A[(size_t)q * nci_ + r] = cfg_.cm[s] * mprod + ck_[s] * kterm;
         }
       if (!spd_inverse(nci_, A)) return Status::Err(IRK_ENUMERIC, "coarse operator not SPD");
       std::copy(A.begin(), A.end(), Ainv_all.begin() + (size_t)s * nci_ * nci_);
     }
     ainv_host_ = Ainv_all;
-    IRK_TRY(arena_.alloc((void**)&dAinv_, Ainv_all.size() * sizeof(double)));
-    IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
+    if (!dAinv_) IRK_TRY(arena_.alloc((void**)&dAinv_, Ainv_all.size() * sizeof(double)));
+    if (!dmap_) IRK_TRY(arena_.alloc((void**)&dmap_, map.size() * sizeof(int)));
     IRK_CUDA(cudaMemcpyAsync(dAinv_, Ainv_all.data(), Ainv_all.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
     IRK_CUDA(cudaMemcpyAsync(dmap_, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
     return Status::Ok();
@@ -677,7 +710,7 @@ class MG final : public MGBase {
   Status setup_fused() {
     fused_ = false;
     if (sizeof(T) != 4 || !cfg_.batched || use_fd_ || coupled() || cfg_.cheb_degree > kMaxChebDegree ||
-        cfg_.nb > kMaxQ)
+        cfg_.nb > kMaxStages)
       return Status::Ok();
     int lc = levels() - 1;
     const long long maxn = (cfg_.dim == 3) ? kFusedMaxNodes3D : kFusedMaxNodes2D;
@@ -690,8 +723,10 @@ class MG final : public MGBase {
     P.nb = cfg_.nb;
     P.m = cfg_.cheb_degree;
     P.nci = nci_;
-    P.tau = (float)cfg_.tau;
-    for (int s = 0; s < cfg_.nb; ++s) P.cm[s] = (float)cfg_.cm[s];
+    for (int s = 0; s < cfg_.nb; ++s) {
+      P.cm[s] = (float)cfg_.cm[s];
+      P.taus[s] = (float)ck_[s];
+    }
     for (int i = 0; i < nlev; ++i) {
       const Lvl& L = lv_[lc + i];
       CoarseLevel& C = P.lv[i];
@@ -709,10 +744,9 @@ class MG final : public MGBase {
     for (size_t i = 0; i < el_.Pc.size(); ++i) P.pc[i] = (float)el_.Pc[i];
     if (coarse_cycle_smem(P, sizeof(float)) > kCoarseCycleMaxSmem) return Status::Ok();
     std::vector<float> af(ainv_host_.begin(), ainv_host_.end());
-    float* dA = nullptr;
-    IRK_TRY(arena_.alloc((void**)&dA, af.size() * sizeof(float)));
-    IRK_CUDA(cudaMemcpyAsync(dA, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice, st_));
-    P.ainv = dA;
+    if (!dAinvf_) IRK_TRY(arena_.alloc((void**)&dAinvf_, af.size() * sizeof(float)));
+    IRK_CUDA(cudaMemcpyAsync(dAinvf_, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice, st_));
+    P.ainv = dAinvf_;
     P.map = dmap_;
     P.ld = lv_[lc].g.ld;
     lc_ = lc;
@@ -792,8 +826,10 @@ class MG final : public MGBase {
     IRK_CUDA(cudaMemcpyAsync(fd_mu_, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice, st_));
     std::memset(&fd_params_, 0, sizeof(fd_params_));
     fd_params_.ni = ni;
-    fd_params_.tau = cfg_.tau;
-    for (int s = 0; s < cfg_.nb && s < kMaxStages; ++s) fd_params_.cm[s] = cfg_.cm[s];
+    for (int s = 0; s < cfg_.nb && s < kMaxStages; ++s) {
+      fd_params_.cm[s] = cfg_.cm[s];
+      fd_params_.taus[s] = ck_[s];
+    }
     fd_params_.beta = cfg_.coupled_beta;
     return Status::Ok();
   }
@@ -839,7 +875,7 @@ class MG final : public MGBase {
       IRK_CUDA(launch_block_shift(nullptr, v1, w, nrm0, nb, n, ldl, st));
       std::vector<double> one(nb, 1.0);
       DiagParams<double> D = make_diag_params<double>(g, nb, cfg_.cm.data(), ck_.data(), one.data());
-      OpParams<LT> P = make_op_params<LT>(g, nb, cfg_.cm.data(), ck_.data());
+      OpParams<LT> P = opp<LT>(g, nb, cfg_.cm.data(), ck_.data());
       EpiParams<LT> E;
       std::memset(&E, 0, sizeof(E));
       E.out = wf;
@@ -910,6 +946,7 @@ class MG final : public MGBase {
   std::vector<double> ck_;
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
+  float* dAinvf_ = nullptr;  // FP32 copy of the coarse inverses for the fused cycle
   int nci_ = 0;
   cudaStream_t st_ = nullptr;
   std::vector<double> ainv_host_;

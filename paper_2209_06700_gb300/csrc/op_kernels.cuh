@@ -854,8 +854,9 @@ cudaError_t launch_op_k(int dim, int nstage, const typename Storage<T>::type* u,
         }
         if (fit <= 0) return cudaErrorInvalidConfiguration;
       }
-    } else if (!OpTuned<T, K, EPI>::find(P.N, nstage, sh)) {
-      sh = default_shape<T, K, EPI>(P.N, nstage);
+    } else {
+      const int key = P.shape_ns > 0 ? P.shape_ns : nstage;
+      if (!OpTuned<T, K, EPI>::find(P.N, key, sh)) sh = default_shape<T, K, EPI>(P.N, key);
     }
     return launch_by_shape<T, K, EPI>(nstage, u, P, E, st, sh);
   }
@@ -885,12 +886,13 @@ template <typename T, int K, int EPI>
 cudaError_t tune_op_k(int dim, int nstage, const typename Storage<T>::type* u, const OpParams<T>& P,
                       const EpiParams<typename Storage<T>::type>& E, cudaStream_t st) {
   if (dim != 3) return cudaSuccess;
+  const int key = P.shape_ns > 0 ? P.shape_ns : nstage;  // the shape is kept per stage count of a request
   OpShape known;
-  if (OpTuned<T, K, EPI>::find(P.N, nstage, known)) return cudaSuccess;
+  if (OpTuned<T, K, EPI>::find(P.N, key, known)) return cudaSuccess;
   const long long nodes = (long long)P.n1 * P.n1 * P.n1 * nstage;
-  const OpShape model = default_shape<T, K, EPI>(P.N, nstage);
+  const OpShape model = default_shape<T, K, EPI>(P.N, key);
   if (nodes < kTuneMinNodes) {
-    OpTuned<T, K, EPI>::put(P.N, nstage, model);
+    OpTuned<T, K, EPI>::put(P.N, key, model);
     return cudaSuccess;
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -898,7 +900,7 @@ cudaError_t tune_op_k(int dim, int nstage, const typename Storage<T>::type* u, c
   // one tuning at a time per kernel: a second thread waits, then finds the shape cached
   static std::mutex tune_mu;
   std::lock_guard<std::mutex> tune_lock(tune_mu);
-  if (OpTuned<T, K, EPI>::find(P.N, nstage, known)) return cudaSuccess;
+  if (OpTuned<T, K, EPI>::find(P.N, key, known)) return cudaSuccess;
   // candidates: the model's segment width (and 32 for FP32 levels), every distinct chunk count,
   // with and without a cluster where one fits
   std::vector<OpShape> cands;
@@ -990,8 +992,8 @@ cudaError_t tune_op_k(int dim, int nstage, const typename Storage<T>::type* u, c
   }
   const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  OpTuned<T, K, EPI>::put(P.N, nstage, best);
-  tune_record(tune_kernel_name<T>(), K, EPI, P.N, nstage, best.cxs, best.zc, best.cluster, 1e3 * best_ms,
+  OpTuned<T, K, EPI>::put(P.N, key, best);
+  tune_record(tune_kernel_name<T>(), K, EPI, P.N, key, best.cxs, best.zc, best.cluster, 1e3 * best_ms,
               model_ms < 0.f ? -1.0 : 1e3 * model_ms, model.cxs, model.zc, model.cluster);
   return cudaSuccess;
 }

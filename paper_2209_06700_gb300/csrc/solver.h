@@ -93,6 +93,10 @@ class MGBase {
   virtual Status coarse_solve(const void* b, void* x, cudaStream_t st) = 0;
   virtual Status apply_mass(int level, const void* x, void* y, double scale, cudaStream_t st) = 0;
   virtual const LevelGeom& geom(int level) const = 0;
+  // New per-block stiffness coefficients (nb values): rebuilds what depends on them (level operator
+  // coefficients, Chebyshev intervals, coarse inverses, fused-cycle parameters) on the existing buffers
+  // and drops the captured V-cycle graph.
+  virtual Status retau(const std::vector<double>& taus, cudaStream_t st) = 0;
   virtual void interval(int level, int block, double* lo, double* hi) const = 0;
 };
 
@@ -109,6 +113,8 @@ struct MGConfig {
   int precision;             // 32 or 64
   int autotune = 1;          // time the level operators' launch shapes at setup
   double coupled_beta = 0.0; // != 0: nb = 2 components of [[A, -beta M], [beta M, A]], A = cm M + tau K
+  std::vector<double> taus;  // per-block stiffness coefficient (blocks of several requests); empty: tau for all
+  int shape_ns = 0;          // blocks per request: level-operator launches take that count's launch shape
 };
 
 Status make_mg(const MGConfig& cfg, const Element1D& e, DeviceArena& arena, cudaStream_t st,
@@ -143,5 +149,25 @@ using ApplyFn = std::function<Status(const S* in, S* out)>;
 template <typename S>
 Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec, const S* b, S* x, double rtol,
                     int max_it, cudaStream_t st, FGMRESResult& res);
+
+// Lockstep flexible GMRES for R independent systems (one per request of a group handle), stored
+// interleaved in w's arrays: vector j of request r at base + (j R + r) len, len = w.len / R.  op and
+// prec act on the R requests' vectors at once (shared launches); the Gram-Schmidt passes, norms,
+// Hessenberg matrices, Givens rotations and convergence tests are per request, with one device->host
+// transfer per iteration for all of them.  A request that has stopped (converged, failed or out of
+// iterations) keeps its result; its later slices are zero.  Scalars: per-request blocks of 256
+// values in dvals / fvals and one pinned host block per request; status per request in st_out.
+struct GroupScalars {
+  double* dvals = nullptr;     // R x 256 device FP64 scalars
+  ff* fvals = nullptr;         // R x 256 device ff scalars
+  std::vector<double*> hvals;  // R pinned host blocks of 256 (from the process-wide pool)
+  unsigned* count = nullptr;   // R arrival counters of the fused reductions
+};
+Status group_scalars_alloc(GroupScalars& g, int R, DeviceArena& arena, cudaStream_t st);
+void group_scalars_release(GroupScalars& g);
+template <typename S>
+Status fgmres_solve_group(FGMRESWork& w, int R, GroupScalars& gs, const ApplyFn<S>& op, const ApplyFn<S>& prec,
+                          const S* b, S* x, double rtol, int max_it, cudaStream_t st,
+                          std::vector<FGMRESResult>& res, std::vector<Status>& st_out);
 
 }  // namespace irk

@@ -443,7 +443,7 @@ __global__ void fd_scale_kernel(double* __restrict__ t, long long ld, int n1, in
     double m = mu[a0] + mu[a1];
     int idx = (a0 + 1) + (a1 + 1) * n1;
     if (dim == 3) { m += mu[a2]; idx += (a2 + 1) * n1 * n1; }
-    t[s * ld + idx] /= (P.cm[s] + P.tau * m);
+    t[s * ld + idx] /= (P.cm[s] + P.taus[s] * m);
   }
 }
 
@@ -457,7 +457,7 @@ __global__ void fd_scale_coupled_kernel(double* __restrict__ t, long long ld, in
     double m = mu[a0] + mu[a1];
     int idx = (a0 + 1) + (a1 + 1) * n1;
     if (dim == 3) { m += mu[a2]; idx += (a2 + 1) * n1 * n1; }
-    const double a = P.cm[0] + P.tau * m, bt = P.beta;
+    const double a = P.cm[0] + P.taus[0] * m, bt = P.beta;
     const double den = a * a + bt * bt;
     const double t0 = t[idx], t1 = t[ld + idx];
     t[idx] = (a * t0 + bt * t1) / den;

@@ -40,9 +40,11 @@ def test_null_handle_is_refused_by_every_call(capi):
         "irk_synchronize": (N,),
         "irk_profile": (N, 0),
         "irk_profile_read": (N, 0, d, ctypes.byref(ll), ctypes.byref(ll)),
+        "irk_step_group": (N, N, d, N, N),
+        "irk_set_tau": (N, d),
     }
     size_calls = {"irk_ndofs": (N,), "irk_ninterior": (N,), "irk_stage_stride": (N,), "irk_num_levels": (N,),
-                  "irk_level_ndofs": (N, 0), "irk_level_stride": (N, 0)}
+                  "irk_level_ndofs": (N, 0), "irk_level_stride": (N, 0), "irk_group_size": (N,)}
     for name, args in status_calls.items():
         assert getattr(lib, name)(*args) == capi.IRK_EINVAL, name
     for name, args in size_calls.items():
@@ -53,6 +55,19 @@ def test_null_handle_is_refused_by_every_call(capi):
     takes_handle = {n for n, (_, args) in capi.SIGNATURES.items() if args and args[0] is ctypes.c_void_p
                     and n not in ("irk_create",)}
     assert takes_handle == set(status_calls) | set(size_calls) | {"irk_last_error", "irk_destroy"}
+
+
+def test_create_group_refuses_bad_arguments_on_the_host(capi):
+    """irk_create_group checks R, the taus and the variant before any device work."""
+    lib = capi.lib()
+    out = ctypes.c_void_p()
+    mesh = capi.IrkMesh(3, 8)
+    taus = (ctypes.c_double * 8)(*([1e-3] * 8))
+    E = capi.IRK_EINVAL
+    assert lib.irk_create_group(ctypes.byref(mesh), 2, 3, 2, taus, None, None, None) == E      # NULL out
+    assert lib.irk_create_group(ctypes.byref(mesh), 2, 3, 2, None, None, None, ctypes.byref(out)) == E
+    assert lib.irk_create_group(ctypes.byref(mesh), 2, 3, 0, taus, None, None, ctypes.byref(out)) == E
+    assert out.value is None
 
 
 def test_batch_checks_its_arrays(capi):

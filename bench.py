@@ -247,7 +247,8 @@ def cpu_baseline_one_thread(w, timeout_s=300):
 
 
 def serving_measure(n_requests, realtime=True, **solver_opts):
-    """Serve the seeded request stream (Poisson arrivals at 200/s) through irk_serve."""
+    """Serve the seeded request stream (Poisson arrivals at 200/s) through irk_serve: groups of waiting
+    same-shape requests share launches and idle handles are reused unless the options say otherwise."""
     import paper_2209_06700_gb300 as pkg
     from synthetic import serving_stream
     reqs = serving_stream(512)[:n_requests]
@@ -265,6 +266,9 @@ def serving_measure(n_requests, realtime=True, **solver_opts):
             "mean_solve_ms": sum(r.solve_ms for r in ok) / max(1, len(ok)),
             "mean_queue_ms": sum(r.queue_ms for r in ok) / max(1, len(ok)),
             "mean_iterations": sum(r.iterations for r in ok) / max(1, len(ok)),
+            "mean_group_size": sum(r.group_size for r in ok) / max(1, len(ok)),
+            "requests_in_shared_launches": sum(1 for r in ok if r.group_size > 1),
+            "handles_reused_fraction": sum(r.handle_reused for r in ok) / max(1, len(ok)),
             "slots": 16, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0"}
 
 
@@ -704,7 +708,7 @@ def main():
             line["serving"] = serving_measure(args.serve_requests)
             # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)
             line["serving_fp64_per_stage_baseline"] = serving_measure(
-                args.serve_baseline_requests, op_ff=0, mg_precision=64, batched=0)
+                args.serve_baseline_requests, op_ff=0, mg_precision=64, batched=0, max_group=1, reuse_handles=0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
             line["cpu_baseline"]["one_thread"] = cpu_baseline_one_thread(w)

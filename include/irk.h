@@ -211,6 +211,8 @@ typedef struct {
   double solve_ms;            /* irk_step */
   long long ndofs, ninterior;
   double mem_bytes;           /* device memory reserved for the request at admission */
+  int group_size;             /* requests that shared this request's launches (irk_create_group) */
+  int handle_reused;          /* 1: the group's handle came from the cache (irk_set_tau), 0: created */
 } irk_result;
 
 typedef struct {
@@ -218,23 +220,32 @@ typedef struct {
   double mem_budget_bytes;    /* device memory for resident requests; <= 0: 80% of the free memory */
   int realtime;               /* 1: honour arrival_s; 0: every request arrives at time 0 */
   irk_options solver;         /* solver options of every request */
+  int max_group;              /* requests of one shape that share launches (1 = none; 0 = up to 16/Q) */
+  int reuse_handles;          /* 1: keep idle handles per shape and group size and reuse them for later
+                                 requests (irk_set_tau), evicted least recently used when memory is
+                                 needed; 0: create and destroy a handle per group */
 } irk_serve_options;
 
-/* Default serving options: 16 slots, automatic budget, real time, solver defaults with restart 16
- * and autotune 0 (concurrent requests would time each other's kernels; the cost model's launch
- * shapes, or shapes tuned earlier in the process, are used). */
+/* Default serving options: 16 slots, automatic budget, real time, groups up to 16/Q requests,
+ * handle reuse on, solver defaults with restart 16 and autotune 0 (concurrent requests would time
+ * each other's kernels; the cost model's launch shapes, or shapes tuned earlier in the process,
+ * are used). */
 void irk_default_serve_options(irk_serve_options* opt);
 
 /* Serve `count` requests with continuous batching (not in the paper: the serving form of this
- * library).  Requests are admitted in arrival order as soon as a slot and enough of the memory
- * budget are free; each admitted request builds its own handle on its own CUDA stream, takes one
- * step from the interpolant of u(., t0) and releases its memory, so requests arriving while others
- * are on the GPU join without waiting for them and their kernels overlap on the device.  Every
- * request's result is independent of the mix (same kernels, same launch shapes, deterministic
- * reductions).  results (host, count entries) receive per-request timing and status; out_host
- * (optional, count pointers, each NULL or a host array of irk_ndofs doubles) receives y_{n+1}.
- * A request larger than the whole budget fails with IRK_EBUSY.  Returns IRK_OK if every request
- * succeeded, else the first failing status. */
+ * library).  Arrived requests wait in arrival order; a free slot (a host worker) takes the oldest
+ * one together with the other waiting requests of the same shape (dim, cells, degree, Q), up to
+ * max_group, as one group whose operator and V-cycle launches they share (irk_create_group), on a
+ * handle taken from the cache of idle handles of that shape and size (irk_set_tau) or created when
+ * the memory budget allows (evicting idle handles if needed), each handle on its own CUDA stream.
+ * Each request takes one step from the interpolant of u(., t0); groups run concurrently, so
+ * requests arriving while others are on the GPU start as soon as a slot and memory are free.
+ * Every request's result is independent of the mix (a group member's result equals its result
+ * alone; same launch shapes, deterministic reductions).  results (host, count entries) receive
+ * per-request timing, status and group size; out_host (optional, count pointers, each NULL or a
+ * host array of irk_ndofs doubles) receives y_{n+1}.  A request larger than the whole budget fails
+ * with IRK_EBUSY.  Every cached handle is destroyed before the call returns.  Returns IRK_OK if
+ * every request succeeded, else the first failing status. */
 irk_status irk_serve(const irk_request* reqs, int count, const irk_serve_options* opt, irk_result* results,
                      double** out_host);
 

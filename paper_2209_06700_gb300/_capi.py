@@ -41,7 +41,8 @@ class IrkRequest(ctypes.Structure):
 class IrkResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("latency_ms", ctypes.c_double),
                 ("queue_ms", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("ndofs", ctypes.c_longlong), ("ninterior", ctypes.c_longlong), ("mem_bytes", ctypes.c_double)]
+                ("ndofs", ctypes.c_longlong), ("ninterior", ctypes.c_longlong), ("mem_bytes", ctypes.c_double),
+                ("group_size", ctypes.c_int), ("handle_reused", ctypes.c_int)]
 
 
 class IrkStats(ctypes.Structure):
@@ -51,7 +52,7 @@ class IrkStats(ctypes.Structure):
 
 class IrkServeOptions(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("realtime", ctypes.c_int),
-                ("solver", IrkOptions)]
+                ("solver", IrkOptions), ("max_group", ctypes.c_int), ("reuse_handles", ctypes.c_int)]
 
 
 _H = ctypes.c_void_p

@@ -38,6 +38,40 @@ def test_alone_equals_mix_and_oracle():
         assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
 
 
+# two shapes, several steps each: waiting requests of one shape run as a group with shared launches
+SAME = [(3, 8, 2, 3, tau, t0, 0.0) for tau, t0 in ((1e-3, 0.0), (2e-3, 0.1), (5e-4, 0.2), (3e-3, 0.0))] + \
+       [(2, 16, 3, 2, tau, 0.0, 0.0) for tau in (1e-2, 2e-3, 4e-4)]
+
+
+def test_groups_share_launches_and_each_result_equals_alone():
+    st, res, ys = pkg.serve(SAME, max_active=1, realtime=False, outputs=True)
+    assert st == 0
+    assert max(r.group_size for r in res) > 1, [r.group_size for r in res]
+    for i, req in enumerate(SAME):
+        st1, res1, ys1 = pkg.serve([req], max_active=1, realtime=False, outputs=True)
+        assert st1 == 0 and res1[0].group_size == 1
+        assert np.abs(ys[i] - ys1[0]).max() <= 1e-12 * np.abs(ys1[0]).max(), i
+        assert res1[0].iterations == res[i].iterations
+    # without groups and without handle reuse the results are the same
+    st2, res2, ys2 = pkg.serve(SAME, max_active=2, realtime=False, outputs=True, max_group=1, reuse_handles=0)
+    assert st2 == 0 and all(r.group_size == 1 and r.handle_reused == 0 for r in res2)
+    for i in range(len(SAME)):
+        assert np.abs(ys[i] - ys2[i]).max() <= 1e-12 * np.abs(ys2[i]).max(), i
+
+
+def test_idle_handles_are_reused_for_later_requests():
+    """One slot, groups of one: the second request of a shape takes the first one's handle (new
+    tau set with irk_set_tau) and still matches the oracle."""
+    reqs = [(3, 6, 3, 2, 1e-3, 0.0, 0.0), (3, 6, 3, 2, 4e-3, 0.0, 0.0), (3, 6, 3, 2, 2e-4, 0.0, 0.0)]
+    st, res, ys = pkg.serve(reqs, max_active=1, realtime=False, outputs=True, max_group=1)
+    assert st == 0
+    assert res[0].handle_reused == 0 and res[1].handle_reused == 1 and res[2].handle_reused == 1
+    for i, (d, N, k, Q, tau, t0, _) in enumerate(reqs):
+        prob = Problem(d, N, k, Q, tau)
+        ref = step_fastdiag(prob, prob.y0(), 0.0)
+        assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
+
+
 def test_realtime_arrivals_and_latency_accounting():
     reqs = [(2, 16, 2, 2, 1e-2, 0.0, 0.01 * i) for i in range(6)]
     st, res, _ = pkg.serve(reqs, max_active=2, realtime=True)

@@ -63,8 +63,8 @@ struct irk_problem {
   std::string last_err;
   ~irk_problem() {
     group_scalars_release(gsc);
-    pinned_block_release(fw.hvals);
-    if (fwd.hvals != fw.hvals) pinned_block_release(fwd.hvals);
+    fgmres_release(fw);
+    fgmres_release(fwd);
   }
 };
 

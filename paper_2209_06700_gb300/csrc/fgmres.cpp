@@ -65,6 +65,12 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
     w.hvals = pinned_block_acquire();
     if (!w.hvals) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
   }
+  if (!w.hvals2) {
+    w.hvals2 = pinned_block_acquire();
+    if (!w.hvals2) return Status::Err(IRK_ENOMEM, "pinned host allocation failed");
+  }
+  for (int i = 0; i < 2; ++i)
+    if (!w.ev[i]) IRK_CUDA(cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming));
   // the constant 1 (restart residual b - A x) in both forms
   const ff one{1.0f, 0.0f};
   w.hvals[255] = 1.0;
@@ -73,6 +79,15 @@ Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& are
   IRK_CUDA(cudaMemcpyAsync(w.fvals + 255, w.hvals + 254, sizeof(ff), cudaMemcpyHostToDevice, stream));
   IRK_CUDA(cudaStreamSynchronize(stream));
   return Status::Ok();
+}
+
+void fgmres_release(FGMRESWork& w) {
+  pinned_block_release(w.hvals);
+  pinned_block_release(w.hvals2);
+  w.hvals = w.hvals2 = nullptr;
+  for (int i = 0; i < 2; ++i)
+    if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+  w.ev[0] = w.ev[1] = nullptr;
 }
 
 namespace {
@@ -140,58 +155,85 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
   IRK_LAUNCH(PROF_KRYLOV, launch_scale<S>(b, 1.0 / beta, V, len, st));
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   int total = 0;
+  // One Arnoldi step j: preconditioner, operator, the Gram-Schmidt passes, the read-back of their
+  // scalars into pinned block j % 2 (event ev[j % 2]) and the normalisation by the device-computed
+  // 1/|w''| (0 when |w''| = 0).  Nothing in step j + 1 needs the host's Givens update of step j,
+  // so step j + 1 is enqueued before the host waits for step j: the GPU does not idle while the
+  // host reads the scalars, updates the Hessenberg matrix and tests convergence.  Near the
+  // expected convergence the host waits first, so that no step is computed in vain.
+  auto launch_step = [&](int j) -> Status {
+    S* Vj = V + (size_t)j * len;
+    S* Zj = Z + (size_t)j * len;
+    S* wv = V + (size_t)(j + 1) * len;
+    IRK_TRY(prec(Vj, Zj));
+    IRK_TRY(op(Zj, wv));
+    // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
+    const int nv = j + 1;
+    // pass 1: h1 = V^T w and |w|^2 (row nv, kept aside in kN0 before pass 2 overwrites row nv)
+    RowSink r1;
+    r1.out = w.dvals + kH1;
+    r1.count = w.count;
+    r1.X.out_ff = w.fvals + kH1;
+    r1.X.copy_out = w.dvals + kN0;
+    r1.X.copy_row = nv;
+    int nb = w.nb;  // row capacity of w.partial in, blocks used out
+    IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, nb, r1, st));
+    // w' = w - V h1, h2 = V^T w', |w'|^2; second pass when |w'|^2 < eta^2 |w|^2
+    RowSink r2;
+    r2.out = w.dvals + kH2;
+    r2.count = w.count;
+    r2.X.out_ff = w.fvals + kH2;
+    r2.X.decide_flag = w.dvals + kRedo;
+    r2.X.decide_ref = w.dvals + kN0;
+    r2.X.decide_row = nv;
+    r2.X.eta2 = kEta * kEta;
+    nb = w.nb;
+    IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, nb, r2, st));
+    // w'' = w' - V h2 (if decided), |w''| and 1 / |w''|
+    RowSink r3;
+    r3.out = w.dvals + kNrm;
+    r3.count = w.count;
+    r3.take_sqrt = 1;
+    r3.X.inv = w.dvals + kInv;
+    r3.X.inv_ff = w.fvals + kInv;
+    nb = w.nb;
+    IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, tmp, wv, len, w.partial,
+                                                nb, r3, st));
+    double* hb = (j % 2 == 0) ? w.hvals : w.hvals2;
+    IRK_CUDA(cudaMemcpyAsync(hb, w.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IRK_CUDA(cudaEventRecord(w.ev[j % 2], st));
+    IRK_LAUNCH(PROF_KRYLOV, launch_scale_dev<S>(wv, cf + kInv, wv, len, st));
+    return Status::Ok();
+  };
   while (true) {
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jlast = -1;
     bool stop = false;
+    double prev_resid = -1.0, prev2_resid = -1.0;
+    IRK_TRY(launch_step(0));
     for (int j = 0; j < m; ++j) {
-      S* Vj = V + (size_t)j * len;
-      S* Zj = Z + (size_t)j * len;
-      S* wv = V + (size_t)(j + 1) * len;
-      IRK_TRY(prec(Vj, Zj));
-      IRK_TRY(op(Zj, wv));
-      // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
-      const int nv = j + 1;
-      // pass 1: h1 = V^T w and |w|^2 (row nv, kept aside in kN0 before pass 2 overwrites row nv)
-      RowSink r1;
-      r1.out = w.dvals + kH1;
-      r1.count = w.count;
-      r1.X.out_ff = w.fvals + kH1;
-      r1.X.copy_out = w.dvals + kN0;
-      r1.X.copy_row = nv;
-      int nb = w.nb;  // row capacity of w.partial in, blocks used out
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, nb, r1, st));
-      // w' = w - V h1, h2 = V^T w', |w'|^2; second pass when |w'|^2 < eta^2 |w|^2
-      RowSink r2;
-      r2.out = w.dvals + kH2;
-      r2.count = w.count;
-      r2.X.out_ff = w.fvals + kH2;
-      r2.X.decide_flag = w.dvals + kRedo;
-      r2.X.decide_ref = w.dvals + kN0;
-      r2.X.decide_row = nv;
-      r2.X.eta2 = kEta * kEta;
-      nb = w.nb;
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, nb, r2, st));
-      // w'' = w' - V h2 (if decided), |w''| and 1 / |w''|
-      RowSink r3;
-      r3.out = w.dvals + kNrm;
-      r3.count = w.count;
-      r3.take_sqrt = 1;
-      r3.X.inv = w.dvals + kInv;
-      r3.X.inv_ff = w.fvals + kInv;
-      nb = w.nb;
-      IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, tmp, wv, len, w.partial,
-                                                  nb, r3, st));
-      IRK_CUDA(cudaMemcpyAsync(w.hvals, w.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      IRK_CUDA(cudaStreamSynchronize(st));
-      const double hn = w.hvals[kNrm];
-      if (!std::isfinite(hn)) return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
-      const bool redo = w.hvals[kRedo] != 0.0;
+      // enqueue step j + 1 ahead unless step j is expected to be the last one
+      bool ahead = false;
+      if (j + 1 < m && total + 1 < max_it) {
+        const bool expect_last = prev_resid > 0.0 && prev2_resid > 0.0 &&
+                                 prev_resid * (prev_resid / prev2_resid) <= 2.0 * target;
+        if (!expect_last) {
+          IRK_TRY(launch_step(j + 1));
+          ahead = true;
+        }
+      }
+      IRK_CUDA(cudaEventSynchronize(w.ev[j % 2]));
+      const double* hv = (j % 2 == 0) ? w.hvals : w.hvals2;
+      const double hn = hv[kNrm];
+      if (!std::isfinite(hn)) {
+        IRK_CUDA(cudaStreamSynchronize(st));
+        return Status::Err(IRK_ENUMERIC, "non-finite value in the Arnoldi process");
+      }
+      const bool redo = hv[kRedo] != 0.0;
       res.reorth += redo ? 1 : 0;
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = w.hvals[kH1 + i] + (redo ? w.hvals[kH2 + i] : 0.0);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[kH1 + i] + (redo ? hv[kH2 + i] : 0.0);
       H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) IRK_LAUNCH(PROF_KRYLOV, launch_scale_dev<S>(wv, cf + kInv, wv, len, st));
       // Givens rotations
       for (int i = 0; i < j; ++i) {
         const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -210,8 +252,11 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
       jlast = j;
       const double resid = std::fabs(g[j + 1]);
       res.rel_residual = resid / bnorm;
+      prev2_resid = prev_resid;
+      prev_resid = resid;
       if (resid <= target) { res.converged = true; stop = true; break; }
       if (total >= max_it || hn == 0.0) { stop = true; break; }
+      if (!ahead && j + 1 < m) IRK_TRY(launch_step(j + 1));
     }
     // y = H^{-1} g, x += Z y
     const int kk = jlast + 1;

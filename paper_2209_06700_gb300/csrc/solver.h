@@ -133,9 +133,13 @@ struct FGMRESWork {
   double* dvals = nullptr;    // device scalars: h1[65], h2[65], norms, decision, y[64], 1
   ff* fvals = nullptr;        // the same scalars split into ff (the ff kernels' coefficients)
   double* hvals = nullptr;    // pinned host mirror
+  double* hvals2 = nullptr;   // second pinned block: iteration j's scalars land in block j % 2
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded after the read-back of iteration j into block j % 2
   unsigned* count = nullptr;  // arrival counter of the fused reductions (0 between kernels)
   int nb = 0;
 };
+// Releases the pinned blocks and events of fgmres_alloc.
+void fgmres_release(FGMRESWork& w);
 
 Status fgmres_alloc(FGMRESWork& w, int ns, long long ld, int m, DeviceArena& arena, cudaStream_t stream);
 double* pinned_block_acquire();

@@ -855,14 +855,17 @@ class MG final : public MGBase {
     IRK_TRY(tmp.alloc((void**)&wf, len * sizeof(LT)));
     const int nbred = std::min(reduction_blocks((long long)g0.ld), 1024);
     IRK_TRY(tmp.alloc((void**)&partial, (size_t)nbred * nb * sizeof(double)));
-    // alpha[step][block], beta[step][block], norm[block]
-    IRK_TRY(tmp.alloc((void**)&ab, (size_t)(2 * steps + 2) * nb * sizeof(double)));
-    double* alpha = ab;
-    double* beta = ab + (size_t)steps * nb;
-    double* nrm0 = ab + (size_t)2 * steps * nb;
-    double* zeros = nrm0 + nb;  // beta_0 = 0 (allocation is zero-initialised)
-    std::vector<double> hab((size_t)2 * steps * nb);
-    for (int l = 0; l + 1 < levels(); ++l) {
+    // per level: alpha[step][block], beta[step][block], norm[block], zeros[block]; every level's
+    // recurrence is enqueued back to back and read back once
+    const int nlev = levels() - 1;
+    const size_t per_level = (size_t)(2 * steps + 2) * nb;
+    IRK_TRY(tmp.alloc((void**)&ab, std::max<size_t>(1, nlev) * per_level * sizeof(double)));
+    std::vector<double> hab(std::max<size_t>(1, nlev) * per_level);
+    for (int l = 0; l < nlev; ++l) {
+      double* alpha = ab + (size_t)l * per_level;
+      double* beta = alpha + (size_t)steps * nb;
+      double* nrm0 = alpha + (size_t)2 * steps * nb;
+      double* zeros = nrm0 + nb;  // beta_0 = 0 (allocation is zero-initialised)
       Lvl& L = lv_[l];
       const LevelGeom& g = L.g;
       const long long n = g.n, ldl = g.ld;
@@ -894,12 +897,18 @@ class MG final : public MGBase {
         IRK_CUDA(launch_reduce_partials(partial, nb, nbl, b_it, st, 1));
         IRK_CUDA(launch_block_shift(v0, v1, w, b_it, nb, n, ldl, st));
       }
-      IRK_CUDA(cudaMemcpyAsync(hab.data(), ab, hab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (nlev > 0) {
+      IRK_CUDA(cudaMemcpyAsync(hab.data(), ab, (size_t)nlev * per_level * sizeof(double), cudaMemcpyDeviceToHost, st));
       IRK_CUDA(cudaStreamSynchronize(st));
+    }
+    for (int l = 0; l < nlev; ++l) {
+      Lvl& L = lv_[l];
+      const double* hl = hab.data() + (size_t)l * per_level;
       std::vector<std::vector<double>> alpha_h(nb), beta_h(nb);
       for (int s = 0; s < nb; ++s) {
         for (int it = 0; it < steps; ++it) {
-          const double a = hab[(size_t)it * nb + s], bb = hab[(size_t)(steps + it) * nb + s];
+          const double a = hl[(size_t)it * nb + s], bb = hl[(size_t)(steps + it) * nb + s];
           alpha_h[s].push_back(a);
           if (!(bb > 1e-12 * std::fabs(a))) break;  // invariant subspace found
           if (it + 1 < steps) beta_h[s].push_back(bb);

@@ -335,14 +335,15 @@ __global__ void __launch_bounds__(kCT) coarse_cycle_kernel(const CoarseParams P)
       tpass<T, K, 1, true>(t1, b[l + 1], d1, d2, Nc, P.pc, false);
     }
   }
-  // coarsest: dense inverse (float copy of the FP64 inverse)
+  // coarsest: the dense FP64 inverse applied in FP64 (the coarse-grid solve stays FP64 inside the
+  // FP32 V-cycle)
   {
     const int lc = nlev - 1;
-    const float* A = P.ainv + (long long)s * P.nci * P.nci;
+    const double* A = P.ainv + (long long)s * P.nci * P.nci;
     for (int rr = threadIdx.x; rr < P.nci; rr += blockDim.x) {
-      T acc = T(0);
-      for (int c = 0; c < P.nci; ++c) acc += (T)A[(long long)rr * P.nci + c] * b[lc][P.map[c]];
-      x[lc][P.map[rr]] = acc;
+      double acc = 0.0;
+      for (int c = 0; c < P.nci; ++c) acc += A[(long long)rr * P.nci + c] * (double)b[lc][P.map[c]];
+      x[lc][P.map[rr]] = (T)acc;
     }
     __syncthreads();
   }

@@ -29,7 +29,7 @@ struct CoarseParams {
   float taus[kMaxStages];                // stiffness coefficient tau of each block
   CoarseLevel lv[kMaxFusedLevels];      // lv[0] = the finest fused level
   float pc[(2 * kMaxDeg + 1) * (kMaxDeg + 1)];
-  const float* ainv;                    // [nb][nci][nci] dense coarse inverse (FP32 copy)
+  const double* ainv;                   // [nb][nci][nci] dense coarse inverse (FP64, applied in FP64)
   const int* map;                       // interior index -> node of the coarsest level
   const void* b_in;                     // level-lc right-hand sides [nb][ld]
   void* x_out;                          // level-lc result [nb][ld]

@@ -743,10 +743,7 @@ class MG final : public MGBase {
     }
     for (size_t i = 0; i < el_.Pc.size(); ++i) P.pc[i] = (float)el_.Pc[i];
     if (coarse_cycle_smem(P, sizeof(float)) > kCoarseCycleMaxSmem) return Status::Ok();
-    std::vector<float> af(ainv_host_.begin(), ainv_host_.end());
-    if (!dAinvf_) IRK_TRY(arena_.alloc((void**)&dAinvf_, af.size() * sizeof(float)));
-    IRK_CUDA(cudaMemcpyAsync(dAinvf_, af.data(), af.size() * sizeof(float), cudaMemcpyHostToDevice, st_));
-    P.ainv = dAinvf_;
+    P.ainv = dAinv_;  // the FP64 inverses of setup_coarse
     P.map = dmap_;
     P.ld = lv_[lc].g.ld;
     lc_ = lc;
@@ -955,7 +952,6 @@ class MG final : public MGBase {
   std::vector<double> ck_;
   double* dAinv_ = nullptr;
   int* dmap_ = nullptr;
-  float* dAinvf_ = nullptr;  // FP32 copy of the coarse inverses for the fused cycle
   int nci_ = 0;
   cudaStream_t st_ = nullptr;
   std::vector<double> ainv_host_;

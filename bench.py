@@ -269,7 +269,8 @@ def serving_measure(n_requests, realtime=True, **solver_opts):
             "mean_group_size": sum(r.group_size for r in ok) / max(1, len(ok)),
             "requests_in_shared_launches": sum(1 for r in ok if r.group_size > 1),
             "handles_reused_fraction": sum(r.handle_reused for r in ok) / max(1, len(ok)),
-            "slots": 16, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0"}
+            "slots": 16, "arrivals": "Poisson 200/s, seed 0" if realtime else "all at t=0",
+            "order": "arrival" if solver_opts.get("smallest_first", 1) == 0 else "smallest first"}
 
 
 def run_reference(args, w):
@@ -706,9 +707,11 @@ def main():
             line["accuracy_vs_oracle"] = accuracy_vs_oracle(w)
         if world == 1 and not args.no_serve:
             line["serving"] = serving_measure(args.serve_requests)
+            line["serving_arrival_order"] = serving_measure(args.serve_requests, smallest_first=0)
             # the plain per-stage FP64 GPU path (native FP64 operator, FP64 V-cycle, one launch per stage)
             line["serving_fp64_per_stage_baseline"] = serving_measure(
-                args.serve_baseline_requests, op_ff=0, mg_precision=64, batched=0, max_group=1, reuse_handles=0)
+                args.serve_baseline_requests, op_ff=0, mg_precision=64, batched=0, max_group=1, reuse_handles=0,
+                smallest_first=0)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
             line["cpu_baseline"]["one_thread"] = cpu_baseline_one_thread(w)

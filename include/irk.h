@@ -224,17 +224,20 @@ typedef struct {
   int reuse_handles;          /* 1: keep idle handles per shape and group size and reuse them for later
                                  requests (irk_set_tau), evicted least recently used when memory is
                                  needed; 0: create and destroy a handle per group */
+  int smallest_first;         /* 1 (default): a free slot takes the waiting request with the fewest
+                                 stage-DoFs (oldest among equals); 0: the oldest waiting request */
 } irk_serve_options;
 
 /* Default serving options: 16 slots, automatic budget, real time, groups up to 16/Q requests,
- * handle reuse on, solver defaults with restart 16 and autotune 0 (concurrent requests would time
+ * handle reuse on, smallest request first, solver defaults with restart 16 and autotune 0 (concurrent requests would time
  * each other's kernels; the cost model's launch shapes, or shapes tuned earlier in the process,
  * are used). */
 void irk_default_serve_options(irk_serve_options* opt);
 
 /* Serve `count` requests with continuous batching (not in the paper: the serving form of this
- * library).  Arrived requests wait in arrival order; a free slot (a host worker) takes the oldest
- * one together with the other waiting requests of the same shape (dim, cells, degree, Q), up to
+ * library).  Arrived requests wait; a free slot (a host worker) takes the smallest waiting request
+ * (fewest stage-DoFs, the oldest among equals; the oldest with smallest_first = 0) together with the
+ * other waiting requests of the same shape (dim, cells, degree, Q), up to
  * max_group, as one group whose operator and V-cycle launches they share (irk_create_group), on a
  * handle taken from the cache of idle handles of that shape and size (irk_set_tau) or created when
  * the memory budget allows (evicting idle handles if needed), each handle on its own CUDA stream.

@@ -15,7 +15,7 @@ __all__ = ["Solver", "IrkError", "IRK_VARIANT_LU", "IRK_VARIANT_DIAG", "autotune
 
 
 def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=False, max_group=0,
-          reuse_handles=1, **solver_opts):
+          reuse_handles=1, smallest_first=1, **solver_opts):
     """Run irk_serve on a list of (dim, cells, degree, Q, tau, t0, arrival_s) tuples or objects.
 
     Returns (status, results, ys): results are IrkResult structs, ys the host numpy arrays of
@@ -37,6 +37,7 @@ def serve(requests, max_active=8, mem_budget_bytes=0.0, realtime=True, outputs=F
     o.realtime = 1 if realtime else 0
     o.max_group = int(max_group)
     o.reuse_handles = int(reuse_handles)
+    o.smallest_first = int(smallest_first)
     for key, val in solver_opts.items():
         setattr(o.solver, key, val)
     res = (IrkResult * n)()

@@ -52,7 +52,8 @@ class IrkStats(ctypes.Structure):
 
 class IrkServeOptions(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("mem_budget_bytes", ctypes.c_double), ("realtime", ctypes.c_int),
-                ("solver", IrkOptions), ("max_group", ctypes.c_int), ("reuse_handles", ctypes.c_int)]
+                ("solver", IrkOptions), ("max_group", ctypes.c_int), ("reuse_handles", ctypes.c_int),
+                ("smallest_first", ctypes.c_int)]
 
 
 _H = ctypes.c_void_p

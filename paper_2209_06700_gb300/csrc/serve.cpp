@@ -1,8 +1,9 @@
 // Continuous-batching request loop of libirk (irk_serve, declared in include/irk.h).
 //
-// Arrived requests wait in arrival order.  A free slot (a host worker thread) takes the oldest
-// waiting request together with the other waiting requests of the same shape (dim, cells, degree,
-// Q), up to the group limit, and runs them as one group: one handle whose stage-operator and
+// Arrived requests wait.  A free slot (a host worker thread) takes the smallest waiting request
+// (fewest stage-DoFs, the oldest among equals; or the oldest, by option) together with the other
+// waiting requests of the same shape (dim, cells, degree, Q), up to the group limit, and runs them
+// as one group: one handle whose stage-operator and
 // V-cycle launches cover every member's stage vectors and blocks, with one FGMRES per member
 // (irk_create_group / irk_step_group).  Handles are kept per shape and group size when idle and
 // reused for later groups with irk_set_tau, which rebuilds only what depends on the step tau
@@ -94,6 +95,7 @@ extern "C" void irk_default_serve_options(irk_serve_options* o) {
   o->solver.autotune = 0;
   o->max_group = 0;
   o->reuse_handles = 1;
+  o->smallest_first = 1;
 }
 
 extern "C" irk_status irk_serve(const irk_request* reqs, int count, const irk_serve_options* opt_in,
@@ -115,8 +117,9 @@ extern "C" irk_status irk_serve(const irk_request* reqs, int count, const irk_se
   const bool groups_ok = opt.solver.variant == IRK_VARIANT_LU && !(opt.solver.deform > 0);
   const bool reuse = opt.reuse_handles != 0 && opt.solver.variant == IRK_VARIANT_LU;
 
-  std::vector<double> est(count);
+  std::vector<double> est(count), work(count);
   for (int i = 0; i < count; ++i) {
+    work[i] = reqs[i].Q * std::pow((double)reqs[i].degree * reqs[i].cells - 1.0, reqs[i].dim);
     results[i] = irk_result();
     results[i].status = IRK_OK;
     est[i] = estimate_bytes(reqs[i], opt.solver);
@@ -146,9 +149,14 @@ extern "C" irk_status irk_serve(const irk_request* reqs, int count, const irk_se
         std::unique_lock<std::mutex> lock(mu);
         cv.wait(lock, [&] { return closing || !pending.empty(); });
         if (pending.empty()) break;
-        // the oldest request and the waiting requests of its shape, up to the group limit
-        const int i0 = pending.front();
-        pending.pop_front();
+        // the oldest request (or the smallest, oldest among equals) and the waiting requests of its
+        // shape, up to the group limit
+        auto pick = pending.begin();
+        if (opt.smallest_first)
+          for (auto it = pending.begin(); it != pending.end(); ++it)
+            if (work[*it] < work[*pick]) pick = it;
+        const int i0 = *pick;
+        pending.erase(pick);
         members.push_back(i0);
         const irk_request& sh = reqs[i0];
         int rmax = groups_ok ? std::max(1, kMaxGroupStages / std::max(1, sh.Q)) : 1;

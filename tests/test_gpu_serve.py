@@ -59,6 +59,14 @@ def test_groups_share_launches_and_each_result_equals_alone():
         assert np.abs(ys[i] - ys2[i]).max() <= 1e-12 * np.abs(ys2[i]).max(), i
 
 
+def test_arrival_order_gives_the_same_results():
+    st, res, ys = pkg.serve(SAME + MIX[:3], max_active=2, realtime=False, outputs=True)
+    st2, res2, ys2 = pkg.serve(SAME + MIX[:3], max_active=2, realtime=False, outputs=True, smallest_first=0)
+    assert st == 0 and st2 == 0
+    for i in range(len(ys)):
+        assert np.abs(ys[i] - ys2[i]).max() <= 1e-12 * np.abs(ys[i]).max(), i
+
+
 def test_idle_handles_are_reused_for_later_requests():
     """One slot, groups of one: the second request of a shape takes the first one's handle (new
     tau set with irk_set_tau) and still matches the oracle."""

@@ -108,6 +108,26 @@ def test_one_failing_request_leaves_the_others_intact():
         assert np.abs(got[r] - alone).max() <= 1e-12 * np.abs(alone).max()
 
 
+def test_float_float_group_equals_alone():
+    """The float-float outer arithmetic (op_ff = 1) in a group: each request as alone."""
+    dim, N, k, Q = 3, 8, 3, 2
+    taus = [1e-3, 3e-3, 6e-4]
+    stream = torch.cuda.Stream()
+    y0 = Problem(dim, N, k, Q, 1e-3).y0()
+    with pkg.Group(dim, N, k, Q, taus, stream=stream, op_ff=1) as g:
+        ys = [torch.from_numpy(y0).cuda() for _ in taus]
+        per, _ = g.step_group(ys, [0.0] * 3)
+        assert per == [0, 0, 0]
+        got = [y.cpu().numpy() for y in ys]
+    for r, tau in enumerate(taus):
+        with pkg.Solver(dim, N, k, Q, tau, stream=stream, op_ff=1) as s:
+            y = torch.from_numpy(y0).cuda()
+            s.step(y, 0.0)
+            s.synchronize()
+            alone = y.cpu().numpy()
+        assert np.abs(got[r] - alone).max() <= 1e-12 * np.abs(alone).max(), r
+
+
 def test_group_arguments():
     with pytest.raises(pkg.IrkError):
         pkg.Group(3, 8, 2, 9, [1e-3, 1e-3])               # R Q > 16

@@ -80,6 +80,18 @@ def test_idle_handles_are_reused_for_later_requests():
         assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
 
 
+def test_diagonalised_variant_is_served_request_by_request():
+    """Groups need the LU variant: with the DIAG variant every request runs on its own handle and
+    still matches the oracle."""
+    reqs = [(3, 6, 2, 3, 1e-3, 0.0, 0.0), (3, 6, 2, 3, 2e-3, 0.0, 0.0), (2, 8, 3, 2, 5e-3, 0.0, 0.0)]
+    st, res, ys = pkg.serve(reqs, max_active=2, realtime=False, outputs=True, variant=pkg.IRK_VARIANT_DIAG)
+    assert st == 0 and all(r.group_size == 1 and r.handle_reused == 0 for r in res)
+    for i, (d, N, k, Q, tau, t0, _) in enumerate(reqs):
+        prob = Problem(d, N, k, Q, tau)
+        ref = step_fastdiag(prob, prob.y0(), 0.0)
+        assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
+
+
 def test_realtime_arrivals_and_latency_accounting():
     reqs = [(2, 16, 2, 2, 1e-2, 0.0, 0.01 * i) for i in range(6)]
     st, res, _ = pkg.serve(reqs, max_active=2, realtime=True)

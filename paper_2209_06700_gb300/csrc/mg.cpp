@@ -714,7 +714,9 @@ class MG final : public MGBase {
       return Status::Ok();
     int lc = levels() - 1;
     const long long maxn = (cfg_.dim == 3) ? kFusedMaxNodes3D : kFusedMaxNodes2D;
-    while (lc > 0 && lv_[lc - 1].g.n <= maxn) --lc;
+    // the lowest levels that fit, at most kMaxFusedLevels of them (a hierarchy with more small levels
+    // fuses its lowest ones and runs the others level by level)
+    while (lc > 0 && lv_[lc - 1].g.n <= maxn && levels() - (lc - 1) <= kMaxFusedLevels) --lc;
     const int nlev = levels() - lc;
     if (nlev < 2 || nlev > kMaxFusedLevels) return Status::Ok();
     CoarseParams& P = fparams_;

@@ -362,7 +362,8 @@ irk_status irk_precondition(irk_handle h, const double* r, double* z);
  *   vcycle:    x = V-cycle(b) starting from level `level`.
  * Vectors are [Q][level stride] of the level's (k N_l + 1)^d nodes; strides from
  * irk_level_stride.  The V-cycle of Sec. 5 (geometric multigrid, Chebyshev smoother around
- * point-Jacobi) taken apart.  IRK_EINVAL for NULL vectors or a level out of range: smooth,
+ * point-Jacobi) taken apart.  On a group handle the hierarchy holds R Q blocks (block r Q + i is
+ * block i of request r, with that request's tau).  IRK_EINVAL for NULL vectors or a level out of range: smooth,
  * restrict and prolongate need level < levels - 1, residual and vcycle level < levels;
  * irk_level_ndofs / irk_level_stride return -1 for a NULL handle or a bad level. */
 long long irk_level_ndofs(irk_handle h, int level);

@@ -177,24 +177,27 @@ def summarise_clocks(lines):
             "samples": len(sm)}
 
 
-def _oracle_replica(wd, steps, barrier, out_q):
-    """One host process: the oracle's problem and fast diagonalisation for workload ``wd``, one
-    untimed exact IRK step, then (after every replica is ready) ``steps`` timed steps of its own
-    replica; puts the elapsed seconds on ``out_q``."""
+def _oracle_replica(wd, steps, warmup, barrier, out_q):
+    """One host process: the oracle's problem and fast diagonalisation for workload ``wd``, ``warmup``
+    untimed exact IRK steps (at least one), then (after every replica is ready) ``steps`` timed steps
+    of its own replica; puts the elapsed seconds on ``out_q``."""
     from synthetic import Workload
     from oracle.irk import FastDiag, Problem, step_fastdiag
     w = Workload(**wd)
     prob = Problem(w.dim, w.cells, w.degree, w.Q, w.tau)
     fd = FastDiag(prob)
-    y = step_fastdiag(prob, prob.y0(), 0.0, fd)
+    y = prob.y0()
+    nw = max(1, warmup)
+    for i in range(nw):
+        y = step_fastdiag(prob, y, i * w.tau, fd)
     barrier.wait()
     t0 = time.perf_counter()
     for i in range(steps):
-        y = step_fastdiag(prob, y, (i + 1) * w.tau, fd)
+        y = step_fastdiag(prob, y, (i + nw) * w.tau, fd)
     out_q.put(time.perf_counter() - t0)
 
 
-def oracle_replicas(w, steps, nproc=None, timeout_s=900):
+def oracle_replicas(w, steps, nproc=None, timeout_s=900, warmup=1):
     """The oracle's exact IRK step (per-mode fast diagonalisation, numpy/scipy) on every host core:
     one single-threaded replica per process (spawned, so no GPU context is inherited), all timed
     together after a common start.  Returns (whole-host stage-DoF/s, processes, s per step)."""
@@ -212,7 +215,7 @@ def oracle_replicas(w, steps, nproc=None, timeout_s=900):
     try:
         ctx = mp.get_context("spawn")
         barrier, out_q = ctx.Barrier(nproc), ctx.Queue()
-        procs = [ctx.Process(target=_oracle_replica, args=(dataclasses.asdict(w), steps, barrier, out_q))
+        procs = [ctx.Process(target=_oracle_replica, args=(dataclasses.asdict(w), steps, warmup, barrier, out_q))
                  for _ in range(nproc)]
         for pr in procs:
             pr.start()
@@ -279,10 +282,10 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    value, nproc, per = oracle_replicas(w, steps=max(1, args.steps))
+    value, nproc, per = oracle_replicas(w, steps=max(1, args.steps), warmup=args.warmup)
     ms = 1e3 * per
     sample = (f"{args.steps} exact IRK steps of {w.name} on each of {nproc} single-threaded replica processes "
-              f"(per-mode fast diagonalisation), after one untimed step each")
+              f"(per-mode fast diagonalisation), after {max(1, args.warmup)} untimed steps each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -35,3 +35,19 @@ def test_degenerate_step_matches_oracle(dim, N, k, Q, tau):
         s.synchronize()
         got = y.cpu().numpy()
     assert rel_err(got, yref) <= 1e-9
+
+
+@pytest.mark.parametrize("dim,N,k,Q,tau,variant", [(2, 8, 2, 9, 1e-2, 0), (3, 4, 2, 9, 1e-3, 0),
+                                                   (2, 8, 2, 9, 1e-2, 1), (3, 6, 4, 7, 1e-3, 0)])
+def test_largest_stage_counts_match_oracle(dim, N, k, Q, tau, variant):
+    """Q up to the largest the library takes (9; the FP64 V-cycle the default picks from Q = 6 on),
+    in the LU and the directly diagonalised variant."""
+    prob = Problem(dim, N, k, Q, tau)
+    yref = step_fastdiag(prob, prob.y0(), 0.0, FastDiag(prob))
+    with pkg.Solver(dim, N, k, Q, tau, variant=variant) as s:
+        y = s.vector()
+        s.interpolate_initial(y, 0.0)
+        s.step(y, 0.0)
+        s.synchronize()
+        got = y.cpu().numpy()
+    assert rel_err(got, yref) <= 1e-9

@@ -92,6 +92,29 @@ def test_diagonalised_variant_is_served_request_by_request():
         assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
 
 
+def test_idle_handles_are_evicted_when_the_budget_needs_their_memory():
+    """A budget that holds one handle at a time: alternating shapes evict the idle handle of the other
+    shape (least recently used); every result still matches the oracle."""
+    A, B = (3, 8, 2, 3, 1e-3, 0.0, 0.0), (3, 6, 3, 2, 2e-3, 0.0, 0.0)
+    _, probe, _ = pkg.serve([A, B], max_active=1, realtime=False)
+    ea, eb = probe[0].mem_bytes, probe[1].mem_bytes
+    budget = 1.05 * max(ea, eb)
+    if ea + eb <= budget:
+        pytest.skip("the two requests fit together")
+    reqs = [A, B, (3, 8, 2, 3, 4e-3, 0.0, 0.0), (3, 6, 3, 2, 5e-4, 0.0, 0.0)]
+    # with room for both handles the last two requests reuse the first two's handles ...
+    st, res, _ = pkg.serve(reqs, max_active=1, realtime=False, max_group=1, smallest_first=0)
+    assert st == 0 and [r.handle_reused for r in res] == [0, 0, 1, 1]
+    # ... with room for one, each request evicts the other shape's idle handle and creates its own
+    st, res, ys = pkg.serve(reqs, max_active=1, realtime=False, outputs=True, mem_budget_bytes=budget,
+                            max_group=1, smallest_first=0)
+    assert st == 0 and [r.handle_reused for r in res] == [0, 0, 0, 0]
+    for i, (d, N, k, Q, tau, t0, _) in enumerate(reqs):
+        prob = Problem(d, N, k, Q, tau)
+        ref = step_fastdiag(prob, prob.y0(), 0.0)
+        assert np.abs(ys[i] - ref).max() <= 1e-9 * np.abs(ref).max(), i
+
+
 def test_realtime_arrivals_and_latency_accounting():
     reqs = [(2, 16, 2, 2, 1e-2, 0.0, 0.01 * i) for i in range(6)]
     st, res, _ = pkg.serve(reqs, max_active=2, realtime=True)

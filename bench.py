@@ -462,6 +462,8 @@ def main():
                     help="time the operator launch shapes at create (1) or keep the cost model's (0)")
     ap.add_argument("--cheb-degree", type=int, default=None)
     ap.add_argument("--smoothing-range", type=float, default=None)
+    ap.add_argument("--gs-reorth", type=int, default=0, choices=[0, 1],
+                    help="second Gram-Schmidt pass: 0 where needed (default), 1 at every step")
     ap.add_argument("--eig-safety", type=float, default=None)
     ap.add_argument("--curved-only", action="store_true",
                     help="run only the curved-mesh measurement (profiler captures of its operator)")
@@ -496,6 +498,8 @@ def main():
     extra = {}
     if args.smoothing_range is not None:
         extra["smoothing_range"] = args.smoothing_range
+    if args.gs_reorth:
+        extra["gs_reorth"] = 1
     if args.eig_safety is not None:
         extra["eig_safety"] = args.eig_safety
     cheb = w.cheb_degree if args.cheb_degree is None else args.cheb_degree
@@ -688,6 +692,7 @@ def main():
                            "variant": args.variant, "mg_precision": mg_bits,
                            "parallelism": f"replicas x{world}",
                            "smoothing_range": extra.get("smoothing_range", 10.0),
+                           "gs_second_pass": "every step" if args.gs_reorth else "where needed (semi-orthogonality)",
                            "l2": "inputs larger than L2: Krylov basis of several GB > 129 MB; no flush"},
                 "latency_ms": {"p50": statistics.median(lat),
                                "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},

@@ -100,6 +100,10 @@ typedef struct {
                          stage vectors; op_ff then picks the operator's arithmetic (1 float-float,
                          0 native FP64).  The preconditioner keeps the Cartesian blocks of
                          Eq. (irk:P) (flexible GMRES absorbs the difference) */
+  int gs_reorth;      /* second classical Gram-Schmidt pass of the outer FGMRES: 0 (default) where
+                         one pass would leave the Krylov basis less than semi-orthogonal (estimated
+                         loss of orthogonality above 2^-26; the residuals and stopping test are then
+                         those of an orthogonal basis to within 1e-6 relative); 1 at every step */
 } irk_options;
 
 typedef struct {
@@ -107,7 +111,7 @@ typedef struct {
   int vcycles;          /* V-cycles applied (per block, sequential count as in Sec. 5 tables) */
   double rel_residual;  /* final ||r|| / ||rhs|| (max over DIAG blocks) */
   double ms_total;      /* host wall time of the step, ms */
-  int reorth_passes;    /* Gram-Schmidt second passes taken (the first pass cancelled too much) */
+  int reorth_passes;    /* Gram-Schmidt second passes taken (see gs_reorth) */
 } irk_stats;
 
 typedef struct irk_problem* irk_handle;

@@ -30,7 +30,8 @@ class IrkOptions(ctypes.Structure):
                 ("batched", ctypes.c_int), ("use_graph", ctypes.c_int), ("eig_steps", ctypes.c_int),
                 ("smoothing_range", ctypes.c_double), ("eig_safety", ctypes.c_double),
                 ("shared_cheb", ctypes.c_int), ("op_ff", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("pair_precond", ctypes.c_int), ("deform", ctypes.c_double)]
+                ("pair_precond", ctypes.c_int), ("deform", ctypes.c_double),
+                ("gs_reorth", ctypes.c_int)]
 
 
 class IrkRequest(ctypes.Structure):

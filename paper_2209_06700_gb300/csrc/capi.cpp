@@ -512,7 +512,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   if (!(o.rtol > 0) || o.max_it < 1 || o.restart < 1 || o.restart > 60 || o.cheb_degree < 1 || o.cheb_degree > 16 ||
       (o.mg_precision != 0 && o.mg_precision != 32 && o.mg_precision != 64) || (o.variant != IRK_VARIANT_LU && o.variant != IRK_VARIANT_DIAG) ||
       o.eig_steps < 2 || !(o.smoothing_range > 1) || !(o.eig_safety >= 1) ||
-      (o.pair_precond != 0 && o.pair_precond != 1) || !(o.deform >= 0) ||
+      (o.pair_precond != 0 && o.pair_precond != 1) || !(o.deform >= 0) || (o.gs_reorth != 0 && o.gs_reorth != 1) ||
       (o.deform > 0 && !deform_valid(mesh->dim, o.deform)))
     return Status::Err(IRK_EINVAL, "invalid options");
   if (o.variant == IRK_VARIANT_DIAG && Q < 2) return Status::Err(IRK_EINVAL, "DIAG variant needs Q >= 2");
@@ -643,6 +643,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   mc.shape_ns = Q;
   IRK_TRY(make_mg(mc, h->el, h->arena, h->st, h->mg));
   IRK_TRY(fgmres_alloc(h->fw, R * Q, g.ld, o.restart, h->arena, h->st));
+  h->fw.always_two_passes = o.gs_reorth;
   IRK_TRY(group_scalars_alloc(h->gsc, R, h->arena, h->st));
   if (o.variant == IRK_VARIANT_DIAG) {
     for (const auto& blk : h->tab.blocks) {
@@ -662,6 +663,7 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
       h->mg_diag.push_back(std::move(m));
     }
     IRK_TRY(fgmres_alloc(h->fwd, 2, g.ld, o.restart, h->arena, h->st));
+    h->fwd.always_two_passes = o.gs_reorth;
   }
   if (o.autotune && !h->deformed) IRK_TRY(autotune_stage_operator(h));
   IRK_CUDA(cudaStreamSynchronize(h->st));
@@ -731,6 +733,7 @@ void irk_default_options(irk_options* o) {
   o->autotune = 1;
   o->pair_precond = 0;
   o->deform = 0.0;
+  o->gs_reorth = 0;
 }
 
 irk_status irk_create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_options* opt,

@@ -3,9 +3,10 @@
 // preconditioner of Eq. (irk:P)).  The flexible variant stores the
 // preconditioned vectors Z because the preconditioner (one mixed-precision
 // V-cycle per block) is not a fixed linear map in floating point.
-// Classical Gram-Schmidt with a conditional second pass (Kahan-Parlett "twice
-// is enough", decided on the device by the reduction that finishes |w'|^2);
-// the dot products are deterministic device reductions, finished inside each
+// Classical Gram-Schmidt with a second pass where one pass would leave the
+// basis less than semi-orthogonal (decided on the device by the reduction
+// that finishes the first pass's coefficients, from the cancellation
+// |w - V h| / |w| and the loss carried over from earlier steps); the dot products are deterministic device reductions, finished inside each
 // Gram-Schmidt kernel by its last block, and the Hessenberg/Givens update runs
 // on the host with one device->host transfer per iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
 #include <cmath>
@@ -93,8 +94,48 @@ void fgmres_release(FGMRESWork& w) {
 namespace {
 
 // layout of dvals / fvals / hvals
-constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kN0 = 131, kRedo = 132, kInv = 133, kY = 160, kOne = 255;
-constexpr double kEta = 0.7;  // Kahan-Parlett threshold of the conditional second pass
+constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kRedo = 132, kInv = 133, kDelta = 134, kY = 160, kOne = 255;
+
+// The second classical Gram-Schmidt pass is taken only where one pass would leave the basis less
+// than semi-orthogonal: estimated loss of orthogonality above 2^-26 (the square root of the FP64
+// unit roundoff).  With the Gram matrix of the m + 1 basis vectors within m 2^-26 of the identity
+// (m <= 60), the Hessenberg least-squares residual equals the true residual |b - A x| of the
+// computed x, and GMRES's residuals the optimal ones, to within a factor 1 +- 1e-6: the stopping
+// test and the iteration count are those of a fully orthogonal basis.  Rounding of one pass: about
+// 100 units of roundoff of the vectors' arithmetic (the blocked length-n dot products; ff: 2^-48).
+constexpr double kSemiOrth = 1.4901161193847656e-8;  // 2^-26
+template <typename S> constexpr double pass_rounding();
+template <> constexpr double pass_rounding<double>() { return 100.0 * 1.1102230246251565e-16; }
+template <> constexpr double pass_rounding<ff>() { return 100.0 * 3.552713678800501e-15; }
+
+// The extras of the three Gram-Schmidt reductions of Arnoldi step nv - 1 on the scalars dv / fv:
+// pass 1 decides the second pass (flag kRedo, loss estimate kDelta); pass 2 writes |w'| and 1/|w'|
+// when no second pass follows; pass 3 writes them after the second pass.
+// (always_two: the second pass at every step, classical Gram-Schmidt twice.)
+template <typename S>
+void gs_sinks(double* dv, ff* fv, unsigned* count, int nv, bool always_two, RowSink& r1, RowSink& r2, RowSink& r3) {
+  r1.out = dv + kH1;
+  r1.count = count;
+  r1.X.out_ff = fv + kH1;
+  r1.X.sel_flag = dv + kRedo;
+  r1.X.sel_delta = dv + kDelta;
+  r1.X.sel_nv = nv;
+  r1.X.sel_round = pass_rounding<S>();
+  r1.X.sel_tol = always_two ? -1.0 : kSemiOrth;
+  r2.out = dv + kH2;
+  r2.count = count;
+  r2.X.out_ff = fv + kH2;
+  r2.X.clear_flag = dv + kRedo;
+  r2.X.clear_row = nv;
+  r2.X.clear_norm = dv + kNrm;
+  r2.X.clear_inv = dv + kInv;
+  r2.X.clear_inv_ff = fv + kInv;
+  r3.out = dv + kNrm;
+  r3.count = count;
+  r3.take_sqrt = 1;
+  r3.X.inv = dv + kInv;
+  r3.X.inv_ff = fv + kInv;
+}
 
 template <typename S> typename Coef<S>::type* coefs(FGMRESWork& w);
 template <> double* coefs<double>(FGMRESWork& w) { return w.dvals; }
@@ -167,37 +208,21 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
     S* wv = V + (size_t)(j + 1) * len;
     IRK_TRY(prec(Vj, Zj));
     IRK_TRY(op(Zj, wv));
-    // classical Gram-Schmidt, second pass only when the first one cancelled ("twice is enough")
+    // classical Gram-Schmidt; the second pass only where one pass would lose semi-orthogonality
     const int nv = j + 1;
-    // pass 1: h1 = V^T w and |w|^2 (row nv, kept aside in kN0 before pass 2 overwrites row nv)
-    RowSink r1;
-    r1.out = w.dvals + kH1;
-    r1.count = w.count;
-    r1.X.out_ff = w.fvals + kH1;
-    r1.X.copy_out = w.dvals + kN0;
-    r1.X.copy_row = nv;
+    RowSink r1, r2, r3;
+    gs_sinks<S>(w.dvals, w.fvals, w.count, nv, w.always_two_passes != 0, r1, r2, r3);
+    // pass 1: h1 = V^T w and |w|^2; its last block decides on the second pass
     int nb = w.nb;  // row capacity of w.partial in, blocks used out
     IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(V, len, nv, wv, len, w.partial, nb, r1, st));
-    // w' = w - V h1, h2 = V^T w', |w'|^2; second pass when |w'|^2 < eta^2 |w|^2
-    RowSink r2;
-    r2.out = w.dvals + kH2;
-    r2.count = w.count;
-    r2.X.out_ff = w.fvals + kH2;
-    r2.X.decide_flag = w.dvals + kRedo;
-    r2.X.decide_ref = w.dvals + kN0;
-    r2.X.decide_row = nv;
-    r2.X.eta2 = kEta * kEta;
+    // w' = w - V h1 and |w'|^2 (in place up to 16 basis vectors), h2 = V^T w' for the second pass
+    S* w2 = (nv <= 16) ? wv : tmp;
     nb = w.nb;
-    IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, tmp, len, w.partial, nb, r2, st));
-    // w'' = w' - V h2 (if decided), |w''| and 1 / |w''|
-    RowSink r3;
-    r3.out = w.dvals + kNrm;
-    r3.count = w.count;
-    r3.take_sqrt = 1;
-    r3.X.inv = w.dvals + kInv;
-    r3.X.inv_ff = w.fvals + kInv;
+    IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(V, len, nv, cf + kH1, wv, w2, len, w.partial, nb, r2,
+                                                  w.dvals + kRedo, st));
+    // second pass w'' = w' - V h2, |w''| and 1 / |w''| (nothing to do in place without it)
     nb = w.nb;
-    IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, tmp, wv, len, w.partial,
+    IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(V, len, nv, cf + kH2, w.dvals + kRedo, w2, wv, len, w.partial,
                                                 nb, r3, st));
     double* hb = (j % 2 == 0) ? w.hvals : w.hvals2;
     IRK_CUDA(cudaMemcpyAsync(hb, w.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -399,32 +424,16 @@ Status fgmres_solve_group(FGMRESWork& w, int R, GroupScalars& gs, const ApplyFn<
         const S* Vr = V + (size_t)r * len;
         S* wr = W + (size_t)r * len;
         S* tr = tmp + (size_t)r * len;
-        RowSink r1;
-        r1.out = q.dvals + kH1;
-        r1.count = q.count;
-        r1.X.out_ff = q.fvals + kH1;
-        r1.X.copy_out = q.dvals + kN0;
-        r1.X.copy_row = nv;
+        RowSink r1, r2, r3;
+        gs_sinks<S>(q.dvals, q.fvals, q.count, nv, w.always_two_passes != 0, r1, r2, r3);
         int nb = q.nb;
         IRK_LAUNCH(PROF_KRYLOV, launch_gs_dot<S>(Vr, all, nv, wr, len, w.partial, nb, r1, st));
-        RowSink r2;
-        r2.out = q.dvals + kH2;
-        r2.count = q.count;
-        r2.X.out_ff = q.fvals + kH2;
-        r2.X.decide_flag = q.dvals + kRedo;
-        r2.X.decide_ref = q.dvals + kN0;
-        r2.X.decide_row = nv;
-        r2.X.eta2 = kEta * kEta;
+        S* w2 = (nv <= 16) ? wr : tr;
         nb = q.nb;
-        IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(Vr, all, nv, cf(r) + kH1, wr, tr, len, w.partial, nb, r2, st));
-        RowSink r3;
-        r3.out = q.dvals + kNrm;
-        r3.count = q.count;
-        r3.take_sqrt = 1;
-        r3.X.inv = q.dvals + kInv;
-        r3.X.inv_ff = q.fvals + kInv;
+        IRK_LAUNCH(PROF_KRYLOV, launch_gs_axpy_dot<S>(Vr, all, nv, cf(r) + kH1, wr, w2, len, w.partial, nb, r2,
+                                                      q.dvals + kRedo, st));
         nb = q.nb;
-        IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(Vr, all, nv, cf(r) + kH2, q.dvals + kRedo, tr, wr, len, w.partial,
+        IRK_LAUNCH(PROF_KRYLOV, launch_gs_reorth<S>(Vr, all, nv, cf(r) + kH2, q.dvals + kRedo, w2, wr, len, w.partial,
                                                     nb, r3, st));
         IRK_CUDA(cudaMemcpyAsync(q.hvals, q.dvals, (kRedo + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
       }

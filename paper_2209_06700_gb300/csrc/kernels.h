@@ -170,12 +170,22 @@ struct ReduceExtra {
   ff* out_ff = nullptr;               // ff copy of each row result
   double* inv = nullptr;              // 1 / (row 0 result), 0 when the result is 0
   ff* inv_ff = nullptr;               // the same in ff
-  double* decide_flag = nullptr;      // 1.0 when (row decide_row) < eta2 * decide_ref[0], else 0.0
-  const double* decide_ref = nullptr;
-  int decide_row = -1;
-  double eta2 = 0.0;
-  double* copy_out = nullptr;         // copy_out[0] = the result of row copy_row
-  int copy_row = -1;
+  // Second Gram-Schmidt pass or not, decided once every row is final (rows 0 .. sel_nv - 1: the
+  // coefficients h = V^T w; row sel_nv: |w|^2).  sel_flag[0] = 1.0 when the new basis vector would
+  // lose semi-orthogonality after one pass, else 0.0; sel_delta[0] carries the basis's estimated
+  // loss of orthogonality from one Arnoldi step to the next (taken as 0 when sel_nv == 1);
+  // sel_round is the rounding of one pass and sel_tol the loss allowed.
+  double* sel_flag = nullptr;
+  double* sel_delta = nullptr;
+  int sel_nv = -1;
+  double sel_round = 0.0, sel_tol = 0.0;
+  // Norm of a Gram-Schmidt result that gets no second pass (clear_flag[0] == 0): sqrt of row
+  // clear_row into clear_norm[0], its inverse (0 for 0) into clear_inv[0] and clear_inv_ff[0].
+  const double* clear_flag = nullptr;
+  int clear_row = -1;
+  double* clear_norm = nullptr;
+  double* clear_inv = nullptr;
+  ff* clear_inv_ff = nullptr;
 };
 // Rows finished inside the kernel that produced their partials: every block adds its partials,
 // and the block that arrives last on *count sums each row over the blocks in a fixed order, writes
@@ -198,10 +208,12 @@ cudaError_t launch_reduce_partials(const double* partial, int nv, int nb, double
 //  scale_dev    : out = inv[0] w                    (inv on the device, Coef<S>; out may alias w)
 //  scale        : out = a x                         (a from the host)
 //  gs_dot       : partial[i] = dot(V_i, w) (i < nv), partial[nv] = |w|^2
-//  gs_axpy_dot  : w_out = w_in - sum_i h[i] V_i; partial[i] = dot(V_i, w_out), partial[nv] = |w_out|^2
+//  gs_axpy_dot  : w_out = w_in - sum_i h[i] V_i; partial[i] = dot(V_i, w_out) when *dots_flag != 0
+//                 (or dots_flag is null; else 0), partial[nv] = |w_out|^2.  w_out may be w_in for
+//                 nv <= 16 (element-wise in place)
 //  gs_reorth    : w_out = w_in - sum_i h[i] V_i if *redo_flag != 0 (second pass of classical
-//                 Gram-Schmidt, "twice is enough" of Kahan and Parlett), else w_out = w_in;
-//                 partial[0] = |w_out|^2
+//                 Gram-Schmidt), else w_out = w_in; partial[0] = |w_out|^2.  w_out may be w_in;
+//                 then nothing runs when *redo_flag == 0 (the norm comes from gs_axpy_dot)
 template <typename S>
 cudaError_t launch_norm2_partial(const S* w, long long n, double* partial, int& nb, const RowSink& R,
                                  cudaStream_t st);
@@ -218,7 +230,7 @@ cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, lon
 template <typename S>
 cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
                                const S* w_in, S* w_out, long long n, double* partial, int& nb, const RowSink& R,
-                               cudaStream_t st);
+                               const double* dots_flag, cudaStream_t st);
 template <typename S>
 cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
                              const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int& nb,

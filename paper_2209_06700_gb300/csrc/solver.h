@@ -137,6 +137,7 @@ struct FGMRESWork {
   cudaEvent_t ev[2] = {nullptr, nullptr};  // recorded after the read-back of iteration j into block j % 2
   unsigned* count = nullptr;  // arrival counter of the fused reductions (0 between kernels)
   int nb = 0;
+  int always_two_passes = 0;  // 1: second Gram-Schmidt pass at every step (else where needed)
 };
 // Releases the pinned blocks and events of fgmres_alloc.
 void fgmres_release(FGMRESWork& w);

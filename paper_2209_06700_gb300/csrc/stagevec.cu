@@ -140,8 +140,41 @@ __device__ __forceinline__ void finish_row(int i, double v, double* __restrict__
     if (X.inv) X.inv[0] = r;
     if (X.inv_ff) X.inv_ff[0] = dev::from_double<ff>(r);
   }
-  if (X.decide_flag && i == X.decide_row) X.decide_flag[0] = (v < X.eta2 * X.decide_ref[0]) ? 1.0 : 0.0;
-  if (X.copy_out && i == X.copy_row) X.copy_out[0] = v;
+  if (X.clear_flag && i == X.clear_row && __double_as_longlong(X.clear_flag[0]) == 0) {
+    const double nrm = sqrt(v);
+    const double r = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+    X.clear_norm[0] = nrm;
+    if (X.clear_inv) X.clear_inv[0] = r;
+    if (X.clear_inv_ff) X.clear_inv_ff[0] = dev::from_double<ff>(r);
+  }
+}
+
+// Second Gram-Schmidt pass or not (thread 0 of the finishing block, rows final in out).  One
+// classical pass leaves w' = w - V h with |V^T w'| / |w'| about (delta + rho) |w| / |w'|: the
+// basis's own loss delta and the pass's rounding rho, both magnified by the cancellation |w| / |w'|
+// (the loss of orthogonality of classical Gram-Schmidt grows this way step after step).  |w'|^2 is
+// estimated before the second pass as |w|^2 - |h|^2 (exact for an orthonormal basis; with the basis
+// semi-orthogonal its error is far below the values that decide).  The pass is skipped while the
+// estimated loss stays within sel_tol, and taken otherwise (or when the estimate is not positive),
+// which brings the new vector's defect down to rounding level and leaves delta where it was.
+__device__ void decide_second_pass(const double* out, const ReduceExtra& X) {
+  const int nv = X.sel_nv;
+  double hh = 0.0;
+  for (int i = 0; i < nv; ++i) hh = fma(out[i], out[i], hh);
+  const double ww = out[nv];
+  const double d0 = (nv > 1) ? X.sel_delta[0] : 0.0;
+  const double rest = ww - hh;
+  bool redo = true;
+  double d1 = fmax(d0, X.sel_round);
+  if (rest > 0.0 && ww > 0.0) {  // false for NaN too: two passes, and the norm reports it
+    const double dn = (d0 + X.sel_round) * sqrt(ww / rest);
+    if (dn <= X.sel_tol) {
+      redo = false;
+      d1 = fmax(d0, dn);
+    }
+  }
+  X.sel_flag[0] = redo ? 1.0 : 0.0;
+  X.sel_delta[0] = d1;
 }
 
 // After the block's partials are written: the block that finishes last (of nblocks) sums every
@@ -162,6 +195,10 @@ __device__ void finish_rows(const double* partial, int rows, int nb, unsigned nb
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) finish_row(i, acc, R.out, R.take_sqrt, R.X);
+  }
+  if (R.X.sel_flag) {
+    __syncthreads();  // every row's result is in R.out
+    if (threadIdx.x == 0) decide_second_pass(R.out, R.X);
   }
   if (threadIdx.x == 0) *R.count = 0u;
 }
@@ -318,16 +355,20 @@ __global__ void from_ff_kernel(const ff* __restrict__ in, double* __restrict__ o
 
 // ------------------------------------------------------------ Gram-Schmidt
 // Basis vectors in groups of 8 (blockIdx.y) beyond 16; the last group also reduces |w|^2 into row nv.
+// MODE 1 without dots (*dots_flag == 0): group 0 alone computes w_out and its norm.
 template <typename S, int MODE>  // 0: dots of w_in;  1: w_out = w_in - V h, then dots of w_out
 __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, long long vstride, int nv,
                                                       const typename Coef<S>::type* __restrict__ h,
+                                                      const double* __restrict__ dots_flag,
                                                       const S* __restrict__ w_in, S* __restrict__ w_out, int n,
                                                       double* __restrict__ partial, int nb, const RowSink R) {
   dev::pdl_enter();
   using C = typename Coef<S>::type;
   constexpr int G = 8;
   const int i0 = blockIdx.y * G;
-  const bool last = (i0 + G >= nv);
+  const bool dots = (MODE == 0) || dots_flag == nullptr || __double_as_longlong(dots_flag[0]) != 0;
+  const bool last = dots ? (i0 + G >= nv) : (blockIdx.y == 0);  // the group that reduces |w|^2
+  const bool active = dots || blockIdx.y == 0;
   __shared__ C hs[64];
   if (MODE == 1) {
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = dev::neg(h[i]);
@@ -336,16 +377,18 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
   C acc[G + 1];
 #pragma unroll
   for (int g = 0; g <= G; ++g) acc[g] = dev::zero<C>();
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; active && e < n; e += gridDim.x * blockDim.x) {
     C we = dev::ldg<S>(w_in + e);
     if (MODE == 1) {
       for (int i = 0; i < nv; ++i) we = mad_acc(we, hs[i], dev::ldg<S>(V + i * vstride + e));
       we = fin(we);
       if (blockIdx.y == 0) w_out[e] = we;
     }
+    if (dots) {
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (i0 + g < nv) acc[g] = mad_acc(acc[g], dev::ldg<S>(V + (i0 + g) * vstride + e), we);
+      for (int g = 0; g < G; ++g)
+        if (i0 + g < nv) acc[g] = mad_acc(acc[g], dev::ldg<S>(V + (i0 + g) * vstride + e), we);
+    }
     acc[G] = mad_acc(acc[G], we, we);
   }
   const int cnt = min(G, nv - i0);
@@ -372,14 +415,17 @@ __global__ void __launch_bounds__(kThreads) gs_kernel(const S* __restrict__ V, l
 }
 
 // Basis sizes up to 16: fully unrolled, one pass over the basis per kernel; in MODE 1 the
-// basis values loaded for the update are reused for the dot products.
+// basis values loaded for the update are reused for the dot products (skipped when *dots_flag ==
+// 0), and w_out may be w_in (each element is read, then written, by the same thread).
 template <typename S, int MODE, int NV>
 __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict__ V, long long vstride,
                                                             const typename Coef<S>::type* __restrict__ h,
-                                                            const S* __restrict__ w_in, S* __restrict__ w_out, int n,
-                                                            double* __restrict__ partial, int nb, const RowSink R) {
+                                                            const double* __restrict__ dots_flag, const S* w_in,
+                                                            S* w_out, int n, double* __restrict__ partial, int nb,
+                                                            const RowSink R) {
   dev::pdl_enter();
   using C = typename Coef<S>::type;
+  const bool dots = (MODE == 0) || dots_flag == nullptr || __double_as_longlong(dots_flag[0]) != 0;
   C hr[NV];
   if (MODE == 1) {
 #pragma unroll
@@ -392,40 +438,47 @@ __global__ void __launch_bounds__(kThreads) gs_small_kernel(const S* __restrict_
     C vv[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) vv[i] = dev::ldg<S>(V + i * vstride + e);
-    C we = dev::ldg<S>(w_in + e);
-    if (MODE == 1) {
+    C we;
+    if constexpr (MODE == 1) {
+      we = w_in[e];  // a plain load: w_in may be w_out
 #pragma unroll
       for (int i = 0; i < NV; ++i) we = mad_acc(we, hr[i], vv[i]);
       we = fin(we);
       w_out[e] = we;
+    } else {
+      we = dev::ldg<S>(w_in + e);
     }
+    if (dots) {
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = mad_acc(acc[i], vv[i], we);
+      for (int i = 0; i < NV; ++i) acc[i] = mad_acc(acc[i], vv[i], we);
+    }
     acc[NV] = mad_acc(acc[NV], we, we);
   }
   block_partials<C, NV + 1>(acc, partial, nb, NV + 1);
   finish_rows(partial, NV + 1, nb, gridDim.x, R);
 }
 
-// w_out = w_in - V h when the device flag says the first pass cancelled too much ("twice is
-// enough"), else w_out = w_in; partial = |w_out|^2 per block.
+// w_out = w_in - V h when the device flag asks for the second pass, else w_out = w_in; partial =
+// |w_out|^2 per block.  In place (w_out == w_in) without the second pass there is nothing to do:
+// the whole grid returns at once and the first pass's kernel has written the norm.
 template <typename S, int NV>  // NV = 0: any basis size up to 64 (coefficients staged in shared memory)
 __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict__ V, long long vstride, int nv,
                                                              const typename Coef<S>::type* __restrict__ h,
                                                              const double* __restrict__ redo_flag,
-                                                             const S* __restrict__ w_in, S* __restrict__ w_out, int n,
+                                                             const S* w_in, S* w_out, int n,
                                                              double* __restrict__ partial, const RowSink R) {
   dev::pdl_enter();
   using C = typename Coef<S>::type;
   // the flag is 1.0 or 0.0: its bit pattern decides (no FP64 compare)
   const bool redo = __double_as_longlong(redo_flag[0]) != 0;
+  if (!redo && w_in == w_out) return;
   C acc[1] = {dev::zero<C>()};
   if constexpr (NV > 0) {
     C hr[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) hr[i] = redo ? dev::neg(h[i]) : dev::zero<C>();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-      C we = dev::ldg<S>(w_in + e);
+      C we = w_in[e];  // a plain load: w_in may be w_out
       if (redo) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) we = mad_acc(we, hr[i], dev::ldg<S>(V + i * vstride + e));
@@ -439,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) gs_reorth_kernel(const S* __restrict
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = redo ? dev::neg(h[i]) : dev::zero<C>();
     __syncthreads();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-      C we = dev::ldg<S>(w_in + e);
+      C we = w_in[e];
       if (redo)
         for (int i = 0; i < nv; ++i) we = mad_acc(we, hs[i], dev::ldg<S>(V + i * vstride + e));
       we = fin(we);
@@ -669,27 +722,31 @@ cudaError_t launch_gs_dot(const S* V, long long vstride, int nv, const S* w, lon
   if (nv < 1 || nv > 64 || !R.out || !R.count) return cudaErrorInvalidValue;
   using C = typename Coef<S>::type;
   if (nv <= 16) {
-    IRK_GS_SMALL(0, V, vstride, (const C*)nullptr, w, (S*)nullptr, (int)n, partial, nb, R);
+    IRK_GS_SMALL(0, V, vstride, (const C*)nullptr, (const double*)nullptr, w, (S*)nullptr, (int)n, partial, nb, R);
     return cudaGetLastError();
   }
   nb = wave_blocks((const void*)gs_kernel<S, 0>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  launch_pdl(gs_kernel<S, 0>, grid, kThreads, 0, st, V, vstride, nv, nullptr, w, nullptr, (int)n, partial, nb, R);
+  launch_pdl(gs_kernel<S, 0>, grid, kThreads, 0, st, V, vstride, nv, nullptr, (const double*)nullptr, w, nullptr,
+             (int)n, partial, nb, R);
   return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_gs_axpy_dot(const S* V, long long vstride, int nv, const typename Coef<S>::type* h, const S* w_in,
-                               S* w_out, long long n, double* partial, int& nb, const RowSink& R, cudaStream_t st) {
-  if (nv < 1 || nv > 64 || w_in == w_out || !R.out || !R.count) return cudaErrorInvalidValue;
+                               S* w_out, long long n, double* partial, int& nb, const RowSink& R,
+                               const double* dots_flag, cudaStream_t st) {
+  if (nv < 1 || nv > 64 || !R.out || !R.count) return cudaErrorInvalidValue;
   if (nv <= 16) {
-    IRK_GS_SMALL(1, V, vstride, h, w_in, w_out, (int)n, partial, nb, R);
+    IRK_GS_SMALL(1, V, vstride, h, dots_flag, w_in, w_out, (int)n, partial, nb, R);
     return cudaGetLastError();
   }
-  // group 0 writes w_out; the other groups recompute it for their dots
+  // group 0 writes w_out; the other groups recompute it for their dots (so not in place)
+  if (w_in == w_out) return cudaErrorInvalidValue;
   nb = wave_blocks((const void*)gs_kernel<S, 1>, nb);
   dim3 grid(nb, (nv + 7) / 8);
-  launch_pdl(gs_kernel<S, 1>, grid, kThreads, 0, st, V, vstride, nv, h, w_in, w_out, (int)n, partial, nb, R);
+  launch_pdl(gs_kernel<S, 1>, grid, kThreads, 0, st, V, vstride, nv, h, dots_flag, w_in, w_out, (int)n, partial, nb,
+             R);
   return cudaGetLastError();
 }
 #undef IRK_GS_SMALL
@@ -699,7 +756,7 @@ template <typename S>
 cudaError_t launch_gs_reorth(const S* V, long long vstride, int nv, const typename Coef<S>::type* h,
                              const double* redo_flag, const S* w_in, S* w_out, long long n, double* partial, int& nb,
                              const RowSink& R, cudaStream_t st) {
-  if (nv < 1 || nv > 64 || w_in == w_out || !R.out || !R.count) return cudaErrorInvalidValue;
+  if (nv < 1 || nv > 64 || !R.out || !R.count) return cudaErrorInvalidValue;
   switch (nv) {
 #define IRK_GSR(NVV)                                                                                            \
   case NVV:                                                                                                     \
@@ -750,7 +807,8 @@ cudaError_t launch_scale(const S* x, double a, S* out, long long n, cudaStream_t
   template cudaError_t launch_gs_dot<S>(const S*, long long, int, const S*, long long, double*, int&,              \
                                         const RowSink&, cudaStream_t);                                             \
   template cudaError_t launch_gs_axpy_dot<S>(const S*, long long, int, const Coef<S>::type*, const S*, S*,          \
-                                             long long, double*, int&, const RowSink&, cudaStream_t);             \
+                                             long long, double*, int&, const RowSink&, const double*,             \
+                                             cudaStream_t);                                                       \
   template cudaError_t launch_gs_reorth<S>(const S*, long long, int, const Coef<S>::type*, const double*,         \
                                            const S*, S*, long long, double*, int&, const RowSink&, cudaStream_t); \
   template cudaError_t launch_norm2_partial<S>(const S*, long long, double*, int&, const RowSink&, cudaStream_t);  \

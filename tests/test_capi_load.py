@@ -48,7 +48,7 @@ def test_host_only_calls():
     lib = capi.load()
     o = capi.IrkOptions()
     lib.irk_default_options(ctypes.byref(o))
-    assert o.rtol == 1e-10 and o.restart == 30 and o.mg_precision == 0 and o.op_ff == 0
+    assert o.rtol == 1e-10 and o.restart == 30 and o.mg_precision == 0 and o.op_ff == 0 and o.gs_reorth == 0
     assert lib.irk_strerror(capi.IRK_ENOTCONV) == b"FGMRES did not converge"
     assert lib.irk_ndofs(None) == -1
     assert lib.irk_destroy(None) == 0

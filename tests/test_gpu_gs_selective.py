@@ -1,0 +1,71 @@
+"""The outer FGMRES's second Gram-Schmidt pass, taken only where it is needed (gs_reorth = 0).
+
+One classical Gram-Schmidt pass magnifies the basis's loss of orthogonality by the cancellation
+|w| / |w - V h| of each Arnoldi step; the solver tracks that estimate on the device and takes the
+second pass where one pass would leave the basis less than semi-orthogonal (2^-26).  The steps
+taken with that rule (the default) and with the second pass at every step (gs_reorth = 1,
+classical Gram-Schmidt twice) must both match the oracle's exact IRK step to the standing 1e-9
+and each other to the same bar, in the same number of FGMRES iterations (the residuals of a
+semi-orthogonal basis are those of an orthogonal one to within 1e-6 relative); the default takes
+fewer second passes, but takes some once the estimated loss has grown.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2209_06700_gb300 as pkg
+from oracle.heat import initial_value
+from oracle.irk import Problem, step_fastdiag
+
+pytestmark = pytest.mark.gpu
+
+YTOL = 1e-9
+
+
+def _step(dim, N, k, Q, tau, y0, t0, **opt):
+    with pkg.Solver(dim, N, k, Q, tau, **opt) as s:
+        y = torch.from_numpy(y0).cuda()
+        st = s.step(y, t0)
+        s.synchronize()
+        return y.cpu().numpy(), st.iterations, st.reorth_passes
+
+
+@pytest.mark.parametrize("dim,N,k,Q,tau,extra", [
+    (3, 16, 3, 3, 1e-3, {}),
+    (3, 12, 2, 5, 1e-2, {}),
+    (2, 32, 4, 4, 1e-2, {"restart": 8}),            # restarts: the estimate starts again per cycle
+    (3, 8, 3, 3, 1e-3, {"op_ff": 1}),               # float-float vectors (coarser pass rounding)
+    (3, 10, 2, 4, 1e-3, {"variant": pkg.IRK_VARIANT_DIAG}),
+])
+def test_selective_second_pass_matches_two_passes_and_the_oracle(dim, N, k, Q, tau, extra):
+    prob = Problem(dim, N, k, Q, tau)
+    t0 = 0.2
+    y0 = initial_value(prob.mesh, t0)
+    ref = step_fastdiag(prob, y0, t0)
+    scale = np.abs(ref).max()
+    y_sel, it_sel, re_sel = _step(dim, N, k, Q, tau, y0, t0, **extra)
+    y_two, it_two, re_two = _step(dim, N, k, Q, tau, y0, t0, gs_reorth=1, **extra)
+    assert np.abs(y_sel - ref).max() <= YTOL * scale
+    assert np.abs(y_two - ref).max() <= YTOL * scale
+    assert np.abs(y_sel - y_two).max() <= YTOL * scale
+    assert it_sel == it_two, (it_sel, it_two)
+    assert re_two == it_two                      # every step took the second pass
+    assert re_sel < re_two, (re_sel, re_two)     # the early steps do without it
+
+
+def test_second_passes_return_once_the_loss_has_grown():
+    """A long Arnoldi cycle (tight tolerance, degree-1 smoothing): the estimate passes 2^-26 after a
+    few steps of strong cancellation, and from then on the second pass is taken."""
+    dim, N, k, Q, tau = 3, 16, 3, 3, 1e-3
+    prob = Problem(dim, N, k, Q, tau)
+    y0 = initial_value(prob.mesh, 0.0)
+    y, its, passes = _step(dim, N, k, Q, tau, y0, 0.0, cheb_degree=1, rtol=1e-12, restart=60)
+    assert its >= 12, its
+    assert 0 < passes < its, (passes, its)
+    ref = step_fastdiag(prob, y0, 0.0)
+    assert np.abs(y - ref).max() <= YTOL * np.abs(ref).max()
+
+
+def test_gs_reorth_option_is_checked():
+    with pytest.raises(pkg.IrkError):
+        pkg.Solver(3, 4, 2, 2, 1e-3, gs_reorth=2)

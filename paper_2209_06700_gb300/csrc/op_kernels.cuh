@@ -39,6 +39,7 @@
 
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ffmath.cuh"
@@ -74,6 +75,32 @@ __device__ __forceinline__ void epilogue(const EpiParams<typename Storage<T>::ty
     S upd = S(0);  // momentum c1 (x_j - x_{j-1}); x_{j-1} = 0 when xold_zero
     if (c1 != S(0)) upd = c1 * (xv - (E.xold_zero ? S(0) : E.out[o]));
     E.out[o] = xv + upd + E.c2[s] * (bv - to_storage(va)) * invD;
+  }
+}
+
+// The same epilogues with the operands' addresses already at the node (the streaming kernel keeps
+// per-thread pointers to its row, so no 64-bit index arithmetic runs per node); c1, c2: the
+// stage's Chebyshev coefficients.
+template <typename T, int EPI>
+__device__ __forceinline__ void epilogue_at(typename Storage<T>::type* out, typename Storage<T>::type* out2,
+                                            const typename Storage<T>::type* b, const typename Storage<T>::type* xj,
+                                            int xold_zero, typename Storage<T>::type c1,
+                                            typename Storage<T>::type c2, T va, T vb,
+                                            typename Storage<T>::type invD) {
+  using S = typename Storage<T>::type;
+  if constexpr (EPI == EPI_STORE) {
+    *out = to_storage(va);
+  } else if constexpr (EPI == EPI_DUAL) {
+    *out = to_storage(va);
+    *out2 = to_storage(vb);
+  } else if constexpr (EPI == EPI_RESID) {
+    *out = *b - to_storage(va);
+  } else {  // EPI_CHEB (float / double)
+    const S xv = *xj;
+    const S bv = *b;
+    S upd = S(0);  // momentum c1 (x_j - x_{j-1}); x_{j-1} = 0 when xold_zero
+    if (c1 != S(0)) upd = c1 * (xv - (xold_zero ? S(0) : *out));
+    *out = xv + upd + c2 * (bv - to_storage(va)) * invD;
   }
 }
 
@@ -117,6 +144,31 @@ __device__ __forceinline__ void ytaps(const T* col, int stride, const OpParams<T
       const T v = col[(m - R) * stride];
       mad2p<PK>(g, h, P.me[R][m], P.ke[R][m], v, v);
     }
+  }
+}
+
+// y pass of one tile row with output row position R (compile time): the row's SL staged columns,
+// 32 per step with this lane's column first (col, g, h point at it), every offset a constant;
+// only the last step, when SL is not a multiple of 32, checks the lane.
+template <typename T, int K, int R, bool PK, int SL>
+__device__ __forceinline__ void yrow(const T* col, T* g, T* h, int lane, const OpParams<T>& P) {
+  constexpr int IT = (SL + 31) / 32;
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    if ((i + 1) * 32 <= SL || lane + 32 * i < SL) {
+      T a = zero<T>(), b = zero<T>();
+      ytaps<T, K, R, PK>(col + 32 * i, SL, P, a, b);
+      g[32 * i] = a;
+      h[32 * i] = b;
+    }
+  }
+}
+
+template <typename T, int K, bool PK, int SL, int R = 0>
+__device__ __forceinline__ void yrow_dispatch(int r, const T* col, T* g, T* h, int lane, const OpParams<T>& P) {
+  if constexpr (R < K) {
+    if (r == R) yrow<T, K, R, PK, SL>(col, g, h, lane, P);
+    else yrow_dispatch<T, K, PK, SL, R + 1>(r, col, g, h, lane, P);
   }
 }
 
@@ -268,8 +320,12 @@ template <typename T, int K> struct Warps3D {
 template <typename T, int K, int CXS> struct Tile3D {
   static constexpr int CY = Warps3D<T, K>::value * (32 / CXS) / K;
 };
-// resident CTAs per SM requested from the register allocator (FP32: 3 -> 24 warps per SM)
-template <typename T> struct MinBlocks { static constexpr int value = (sizeof(T) == 4) ? 3 : 2; };
+// resident CTAs per SM requested from the register allocator: FP32 3 (24 warps per SM), at
+// degree 3 4 of 6 warps (the kernel waits on loads: 24 warps hide more of that than 18 at fewer
+// instructions; 0.156 -> 0.134 ms per smoothing step on 64^3 cells)
+template <typename T, int K> struct MinBlocks {
+  static constexpr int value = (sizeof(T) == 4) ? (K == 3 ? 4 : 3) : 2;
+};
 
 // Shared-memory layout of the 3D kernel (dynamic): two staged planes, two y-pass outputs (g, h),
 // the held bottom plane of a cluster chunk, and the 1/D table of the Chebyshev epilogue.
@@ -285,7 +341,7 @@ struct Op3dSmem {
 
 // ---------------------------------------------------------------- 3D kernel
 template <typename T, int K, int EPI, int CXS>
-__global__ void __launch_bounds__(32 * Warps3D<T, K>::value, MinBlocks<T>::value)
+__global__ void __launch_bounds__(32 * Warps3D<T, K>::value, MinBlocks<T, K>::value)
 op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P,
             const EpiParams<typename Storage<T>::type> E) {
   dev::pdl_enter();
@@ -360,22 +416,36 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     T* su = su2 + buf * L::SU;
 #pragma unroll
     for (int q = 0; q < PF; ++q)
-      if (soff[q] >= 0) su[soff[q]] = pf[q];
+      if ((q + 1) * NT <= NLD || soff[q] >= 0) su[soff[q]] = pf[q];  // only the last slot can be empty
   };
+  // the warp's rows (warp-uniform row position in the cell): this lane's first staged input
+  // column and output slot of each, fixed for the whole kernel
+  // FP32 levels up to degree 3 (F32): the warp's rows with every offset a constant (this lane's
+  // first output slot; the input column sits K rows lower)
+  constexpr bool F32 = std::is_same<T, float>::value && K <= 3;
+  const int yout0 = w * RPW * SL + lane;
   auto ypass = [&](int buf) {
     const T* su = su2 + buf * L::SU;
     T* sgb = sg2 + buf * L::SG;
     T* shb = sh2 + buf * L::SG;
+    if constexpr (F32) {
 #pragma unroll 1
-    for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows, one at a time (warp-uniform tap row)
-      const int yr = w * RPW + rr;
-      const int ro = yr % K;
-      const T* colbase = su + (yr + K) * SL;
-      for (int sl = lane; sl < SL; sl += 32) {
-        T g = dev::zero<T>(), h = dev::zero<T>();
-        dev::ytaps_dispatch<T, K, PK>(ro, colbase + sl, SL, P, g, h);
-        sgb[yr * SL + sl] = g;
-        shb[yr * SL + sl] = h;
+      for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows one at a time (warp-uniform tap row)
+        const int o = yout0 + rr * SL;
+        dev::yrow_dispatch<T, K, PK, SL>((w * RPW + rr) % K, su + K * SL + o, sgb + o, shb + o, lane, P);
+      }
+    } else {
+#pragma unroll 1
+      for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows, one at a time (warp-uniform tap row)
+        const int yr = w * RPW + rr;
+        const int ro = yr % K;
+        const T* colbase = su + (yr + K) * SL;
+        for (int sl = lane; sl < SL; sl += 32) {
+          T g = dev::zero<T>(), h = dev::zero<T>();
+          dev::ytaps_dispatch<T, K, PK>(ro, colbase + sl, SL, P, g, h);
+          sgb[yr * SL + sl] = g;
+          shb[yr * SL + sl] = h;
+        }
       }
     }
   };
@@ -411,15 +481,32 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     for (int mo = 0; mo <= K; ++mo) { accA[m][mo] = dev::zero<T>(); accB[m][mo] = dev::zero<T>(); }
 
   // the thread's output nodes (z, yrow, K cell + m) sit at rowbase + z * n1^2 + m in stage s
-  // (32-bit offsets within a stage vector; the stage offset is uniform across the CTA)
+  // (32-bit offsets within a stage vector; the stage offset is uniform across the CTA).  F32: the
+  // row start, the stage's Chebyshev coefficients and this row's part of the 1/D
+  // table are fixed for the kernel, and the operands' addresses are formed once per plane.
   const int rowbase = yrow * n1 + K * cell;
   const int plane32 = n1 * n1;
   const long long sbase = (long long)s * P.ld;
+  const long long rowstart = sbase + rowbase;
+  S ec1{}, ec2{};
+  if constexpr (F32 && EPI == EPI_CHEB) {
+    ec1 = E.c1[s];
+    ec2 = E.c2[s];
+  }
+  const int sinv_row = (yrow % K) * K;
   auto emit_node = [&](int z, int m, int mo, T va, T vb) {
     if (m == 0 && cell == 0) return;  // x = 0: boundary node
     S invD{};
-    if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
-    dev::epilogue<T, EPI>(E, sbase + (rowbase + z * plane32 + m), s, va, vb, invD);
+    if constexpr (F32) {
+      if constexpr (EPI == EPI_CHEB) invD = sinvd[sinv_row + mo * K * K + m];
+      const long long o = rowstart + (long long)(z * plane32);
+      dev::epilogue_at<T, EPI>((E.out + o) + m, EPI == EPI_DUAL ? (E.out2 + o) + m : nullptr,
+                               (EPI == EPI_RESID || EPI == EPI_CHEB) ? (E.b + o) + m : nullptr,
+                               EPI == EPI_CHEB ? (E.xj + o) + m : nullptr, E.xold_zero, ec1, ec2, va, vb, invD);
+    } else {
+      if constexpr (EPI == EPI_CHEB) invD = sinvd[(mo * K + (yrow % K)) * K + m];
+      dev::epilogue<T, EPI>(E, sbase + (rowbase + z * plane32 + m), s, va, vb, invD);
+    }
   };
   auto emit = [&](int cz) {
     if (!row_ok) return;

@@ -49,6 +49,14 @@
 namespace irk {
 namespace dev {
 
+// 4-byte asynchronous copy global -> shared (completes at cp_async_wait_all in the same thread)
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <typename A, typename B> __device__ __forceinline__ void cp_async4(A*, const B*) {}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // load from storage and store back (ff vectors are stored as ff pairs, 8 bytes per value)
 template <typename T> __device__ __forceinline__ T load(const typename Storage<T>::type* p) { return ldg<T>(p); }
 __device__ __forceinline__ float to_storage(float v) { return v; }
@@ -321,8 +329,7 @@ template <typename T, int K, int CXS> struct Tile3D {
   static constexpr int CY = Warps3D<T, K>::value * (32 / CXS) / K;
 };
 // resident CTAs per SM requested from the register allocator: FP32 3 (24 warps per SM), at
-// degree 3 4 of 6 warps (the kernel waits on loads: 24 warps hide more of that than 18 at fewer
-// instructions; 0.156 -> 0.134 ms per smoothing step on 64^3 cells)
+// degree 3 4 CTAs of 6 warps (the kernel waits on loads: 24 warps hide more of that than 18)
 template <typename T, int K> struct MinBlocks {
   static constexpr int value = (sizeof(T) == 4) ? (K == 3 ? 4 : 3) : 2;
 };
@@ -335,8 +342,15 @@ struct Op3dSmem {
   static constexpr int CW = CXS + 2, SL = K * CW, HY = TY + K + 1;
   static constexpr int SU = HY * SL, SG = TY * SL, SHOLD = (EPI == EPI_DUAL ? 2 : 1) * K * NT;
   static constexpr int SINV = (EPI == EPI_CHEB) ? K * K * K : 1;
-  static constexpr size_t bytes =
-      (size_t)(2 * SU + 4 * SG + SHOLD) * sizeof(T) + (size_t)SINV * sizeof(typename Storage<T>::type);
+  // FP32 Chebyshev step and residual at degrees 2..3: the epilogue's operands of a z-cell (b; x_j,
+  // x_{j-1}), fetched asynchronously while the cell streams (at degree 4 the extra shared memory
+  // would cost a resident CTA)
+  static constexpr bool PRE =
+      std::is_same<T, float>::value && K >= 2 && K <= 3 && (EPI == EPI_CHEB || EPI == EPI_RESID);
+  static constexpr int NPRE = (EPI == EPI_CHEB) ? 3 : 1;
+  static constexpr int SPRE = PRE ? NPRE * K * K * NT : 0;
+  static constexpr size_t bytes = (size_t)(2 * SU + 4 * SG + SHOLD) * sizeof(T) +
+                                  (size_t)(SINV + SPRE) * sizeof(typename Storage<T>::type);
 };
 
 // ---------------------------------------------------------------- 3D kernel
@@ -364,6 +378,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   T* const sh2 = sg2 + 2 * L::SG;                 // two y-pass outputs h
   T* const shold = sh2 + 2 * L::SG;               // bottom plane held for the cluster exchange
   S* const sinvd = reinterpret_cast<S*>(shold + L::SHOLD);  // 1/D by (x, y, z) mod k
+  S* const spre = sinvd + L::SINV;                          // prefetched epilogue operands
   T* const sg = sg2;  // buffer 0 doubles as the cluster exchange area
   T* const sh = sh2;
 
@@ -420,9 +435,9 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   };
   // the warp's rows (warp-uniform row position in the cell): this lane's first staged input
   // column and output slot of each, fixed for the whole kernel
-  // FP32 levels up to degree 3 (F32): the warp's rows with every offset a constant (this lane's
-  // first output slot; the input column sits K rows lower)
-  constexpr bool F32 = std::is_same<T, float>::value && K <= 3;
+  // FP32 levels (F32; not the dual products at degree 4, which would spill): the warp's rows with
+  // every offset a constant (this lane's first output slot; the input column sits K rows lower)
+  constexpr bool F32 = std::is_same<T, float>::value && (K <= 3 || EPI != EPI_DUAL);
   const int yout0 = w * RPW * SL + lane;
   auto ypass = [&](int buf) {
     const T* su = su2 + buf * L::SU;
@@ -494,9 +509,52 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     ec2 = E.c2[s];
   }
   const int sinv_row = (yrow % K) * K;
-  auto emit_node = [&](int z, int m, int mo, T va, T vb) {
+  // prefetch slots: operand a (b, x_j, x_{j-1}) of node (mo, m) of this thread at
+  // spre[((a K + mo) K + m) NT + tid]; x_{j-1} only when the momentum term reads it
+  constexpr bool PRE = L::PRE;
+  bool need_old = false;
+  if constexpr (PRE && EPI == EPI_CHEB) need_old = ec1 != 0.0f && !E.xold_zero;
+  auto prefetch = [&](int cz) {  // the operands of cell cz's emitted nodes (emit below)
+    if constexpr (PRE) {
+      if (!row_ok) return;
+#pragma unroll
+      for (int mo = 0; mo < K; ++mo) {
+        const int z = K * cz + mo;
+        if (z < 1 || (mo == 0 && hold_bottom && cz == c0)) continue;
+        const long long o = rowstart + (long long)(z * plane32);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          if (m == 0 && cell == 0) continue;
+          const int slot = (mo * K + m) * NT + tid;
+          dev::cp_async4(spre + slot, (E.b + o) + m);
+          if constexpr (EPI == EPI_CHEB) {
+            dev::cp_async4(spre + K * K * NT + slot, (E.xj + o) + m);
+            if (need_old) dev::cp_async4(spre + 2 * K * K * NT + slot, (E.out + o) + m);
+          }
+        }
+      }
+    }
+  };
+  auto emit_node = [&](int z, int m, int mo, T va, T vb, bool pre = false) {
     if (m == 0 && cell == 0) return;  // x = 0: boundary node
     S invD{};
+    if constexpr (PRE) {
+      if (pre) {
+        const int slot = (mo * K + m) * NT + tid;
+        const long long o = rowstart + (long long)(z * plane32);
+        const S bv = spre[slot];
+        if constexpr (EPI == EPI_RESID) {
+          (E.out + o)[m] = bv - dev::to_storage(va);
+        } else {
+          const S xv = spre[K * K * NT + slot];
+          S upd = S(0);
+          if (ec1 != S(0)) upd = ec1 * (xv - (need_old ? spre[2 * K * K * NT + slot] : S(0)));
+          invD = sinvd[sinv_row + mo * K * K + m];
+          (E.out + o)[m] = xv + upd + ec2 * (bv - dev::to_storage(va)) * invD;
+        }
+        return;
+      }
+    }
     if constexpr (F32) {
       if constexpr (EPI == EPI_CHEB) invD = sinvd[sinv_row + mo * K * K + m];
       const long long o = rowstart + (long long)(z * plane32);
@@ -510,6 +568,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
   };
   auto emit = [&](int cz) {
     if (!row_ok) return;
+    if constexpr (PRE) dev::cp_async_wait_all();  // this thread's prefetched operands of cell cz
 #pragma unroll
     for (int mo = 0; mo < K; ++mo) {
       const int z = K * cz + mo;
@@ -523,7 +582,7 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
         continue;
       }
 #pragma unroll
-      for (int m = 0; m < K; ++m) emit_node(z, m, mo, accA[m][mo], accB[m][mo]);
+      for (int m = 0; m < K; ++m) emit_node(z, m, mo, accA[m][mo], accB[m][mo], true);
     }
   };
 
@@ -549,6 +608,8 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
       T R[K], Pp[K];
       xpass(buf ^ 1, R, Pp);
       dev::zstep<T, K, DUAL, PK>(r, c, cstart, c0, P, cm, ck, R, Pp, accA, accB, emit);
+      // cell c's operands, one barrier after emit(c - 1) read the slots: K - 1 planes ahead
+      if (PRE && r == 1 && c >= c0) prefetch(c);
       if (zp + 1 <= zlast) {
         store_plane(buf ^ 1);
         if (zp + 2 <= zlast) load_plane(zp + 2);

@@ -355,6 +355,18 @@ irk_status irk_stage_rhs(irk_handle h, const double* y, double t_n, double* rhs)
  * IRK_EINVAL for NULL r or z. */
 irk_status irk_precondition(irk_handle h, const double* r, double* z);
 
+/* The two basis changes of Eq. (irk:P) around the block V-cycles, on their own (LU variant; the
+ * kernels irk_precondition runs, on the caller's buffers):
+ *   to_mg:   b = S~^{-1} r in FP64, rounded to the multigrid's element type (float for the FP32
+ *            hierarchy, round to nearest with ties to even; double for the FP64 one);
+ *            r [Q][stride] FP64, b [Q][stride] of that type;
+ *   from_mg: z = S~ x, x [Q][stride] in the multigrid's element type (widened exactly), z
+ *            [Q][stride] FP64.
+ * stride = irk_level_stride(h, 0).  Asynchronous on the handle's stream.
+ * IRK_EINVAL for NULL vectors, a DIAG-variant handle or a group handle. */
+irk_status irk_basis_to_mg(irk_handle h, const double* r, void* b);
+irk_status irk_basis_from_mg(irk_handle h, const void* x, double* z);
+
 /* Multigrid pieces on level `level` (0 = finest) for all Q LU blocks at once,
  * in the MG precision's element type (float for 32, double for 64):
  *   smooth:    x <- degree-m Chebyshev iteration on (lambda_i M + tau K) x = b

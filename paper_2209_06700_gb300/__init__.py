@@ -204,6 +204,12 @@ class Solver:
     def precondition(self, r, z):
         check(lib().irk_precondition(self.h, _ptr(r), _ptr(z)), self.h)
 
+    def basis_to_mg(self, r, b):
+        check(lib().irk_basis_to_mg(self.h, _ptr(r), _ptr(b)), self.h)
+
+    def basis_from_mg(self, x, z):
+        check(lib().irk_basis_from_mg(self.h, _ptr(x), _ptr(z)), self.h)
+
     def stage_combine(self, u, v, D):
         import numpy as np
         D = np.ascontiguousarray(D, dtype=np.float64)

@@ -96,6 +96,8 @@ SIGNATURES = {
     "irk_apply": (_I, [_H, _P, _P]),
     "irk_stage_rhs": (_I, [_H, _P, _D, _P]),
     "irk_precondition": (_I, [_H, _P, _P]),
+    "irk_basis_to_mg": (_I, [_H, _P, _P]),
+    "irk_basis_from_mg": (_I, [_H, _P, _P]),
     "irk_level_ndofs": (_LL, [_H, _I]),
     "irk_level_stride": (_LL, [_H, _I]),
     "irk_mg_smooth": (_I, [_H, _I, _P, _P, _I]),

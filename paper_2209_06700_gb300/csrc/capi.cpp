@@ -1102,6 +1102,38 @@ irk_status irk_precondition(irk_handle h, const double* r, double* z) {
   });
 }
 
+irk_status irk_basis_to_mg(irk_handle h, const double* r, void* b) {
+  return guarded(h, [&]() -> Status {
+    if (!r || !b) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (h->opt.variant != IRK_VARIANT_LU || h->R > 1)
+      return Status::Err(IRK_EINVAL, "the basis changes of the LU variant, one request per handle");
+    const LevelGeom& g = h->fine;
+    const CombineParams C = combine_params(h->Q, h->Q, h->tab.Sinv.data());
+    if (h->mg->elem_size() == 4)
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double, float>(r, nullptr, (float*)b, g.n, g.ld, C, h->st));
+    else
+      IRK_LAUNCH(PROF_COMBINE, launch_combine<double, double, double>(r, nullptr, (double*)b, g.n, g.ld, C, h->st));
+    return Status::Ok();
+  });
+}
+
+irk_status irk_basis_from_mg(irk_handle h, const void* x, double* z) {
+  return guarded(h, [&]() -> Status {
+    if (!x || !z) return Status::Err(IRK_EINVAL, "bad arguments");
+    if (h->opt.variant != IRK_VARIANT_LU || h->R > 1)
+      return Status::Err(IRK_EINVAL, "the basis changes of the LU variant, one request per handle");
+    const LevelGeom& g = h->fine;
+    const CombineParams C = combine_params(h->Q, h->Q, h->tab.S.data());
+    if (h->mg->elem_size() == 4)
+      IRK_LAUNCH(PROF_COMBINE,
+                 launch_combine<float, double, double>((const float*)x, nullptr, z, g.n, g.ld, C, h->st));
+    else
+      IRK_LAUNCH(PROF_COMBINE,
+                 launch_combine<double, double, double>((const double*)x, nullptr, z, g.n, g.ld, C, h->st));
+    return Status::Ok();
+  });
+}
+
 long long irk_level_ndofs(irk_handle h, int level) {
   if (!h || level < 0 || level >= h->mg->levels()) return -1;
   return h->mg->geom(level).n;

@@ -108,11 +108,62 @@ template <> __device__ __forceinline__ ff from_double<ff>(double d) {
   const float hi = __double2float_rn(d);
   return ff{hi, __double2float_rn(d - (double)hi)};
 }
-__device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(ff v) { return (double)v.hi + (double)v.lo; }
-// between vector element types: float <-> ff exact one way, rounded to FP32 the other
+// binary32 <-> binary64 on the integer pipe.  On a GPU whose FP64 pipe is a small fraction of its
+// FP32 and integer pipes, the conversion instructions (which run on the FP64 pipe) bound the basis
+// changes between the FP64 outer solver and the FP32 multigrid as much as their multiply-adds; the
+// IEEE 754 definitions below give the same results from bit operations.
+// float -> double is exact: sign kept, exponent rebiased by 1023 - 127 = 896, fraction moved up by
+// 29 bits; a subnormal float is normalised (its leading one becomes the implicit bit); infinities
+// keep the all-ones exponent, NaNs come out quiet.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, frac = u & 0x7FFFFFu;
+  unsigned hi, lo;
+  if (e - 1u < 0xFEu) {  // normal: 1 <= e <= 254
+    hi = sign | ((e + 896u) << 20) | (frac >> 3);
+    lo = frac << 29;
+  } else if (e == 0xFFu) {  // infinity (frac 0) or NaN (quiet bit set)
+    hi = sign | 0x7FF00000u | (frac >> 3) | (frac != 0u ? 0x80000u : 0u);
+    lo = frac << 29;
+  } else if (frac == 0u) {  // signed zero
+    hi = sign;
+    lo = 0u;
+  } else {  // subnormal: frac 2^-149 with its highest set bit p (0..22) as the implicit one
+    const int p = 31 - __clz(frac);
+    const unsigned long long f52 = ((unsigned long long)(frac ^ (1u << p))) << (52 - p);
+    hi = sign | ((unsigned)(p + 874) << 20) | (unsigned)(f52 >> 32);
+    lo = (unsigned)f52;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double to_double(float v) { return f32_to_f64(v); }
+// double -> float, rounded to nearest with ties to even: the top 23 of the 52 fraction bits are
+// kept and the 29 below decide; a carry out of the fraction moves into the exponent (and to
+// infinity above the largest float) by itself.  Results below the float's normal range (and
+// zeros' signs aside, which are kept directly) go through the hardware conversion: rare.
+__device__ __forceinline__ float f64_to_f32_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((((hi & 0xFFFFFu) | lo) != 0u) ? 0x400000u : 0u));
+  if (e == 0 && (hi & 0xFFFFFu) == 0u && lo == 0u) return __uint_as_float(sign);
+  const int fe = e - 896;
+  if (fe >= 0xFF) return __uint_as_float(sign | 0x7F800000u);
+  if (fe <= 0) return __double2float_rn(d);
+  const unsigned keep = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  unsigned r = sign | ((unsigned)fe << 23) | keep;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) r += 1u;
+  return __uint_as_float(r);
+}
+
+// between vector element types: float <-> ff exact one way, rounded to FP32 the other; float <->
+// double through the integer-pipe conversions above
 template <typename To, typename From> __device__ __forceinline__ To convert(From v) { return (To)v; }
+template <> __device__ __forceinline__ double convert<double, float>(float v) { return f32_to_f64(v); }
+template <> __device__ __forceinline__ float convert<float, double>(double v) { return f64_to_f32_rn(v); }
 template <> __device__ __forceinline__ ff convert<ff, float>(float v) { return ff{v, 0.f}; }
 template <> __device__ __forceinline__ float convert<float, ff>(ff v) { return __fadd_rn(v.hi, v.lo); }
 template <> __device__ __forceinline__ ff convert<ff, ff>(ff v) { return v; }

@@ -28,6 +28,8 @@ def test_null_handle_is_refused_by_every_call(capi):
         "irk_apply": (N, N, N),
         "irk_stage_rhs": (N, N, 0.0, N),
         "irk_precondition": (N, N, N),
+        "irk_basis_to_mg": (N, N, N),
+        "irk_basis_from_mg": (N, N, N),
         "irk_mg_smooth": (N, 0, N, N, 0),
         "irk_mg_residual": (N, 0, N, N, N),
         "irk_mg_restrict": (N, 0, N, N),

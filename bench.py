@@ -601,7 +601,7 @@ def main():
         return None
 
     def operator_roofline(avg_ms):
-        """The stage operator: algorithmic flops (the cell-matrix form of the apply, (14p^4 + 4p^3) per
+        """The stage operator: algorithmic flops (the DoF-space Kronecker form, (14p^4 + 4p^3) per
         cell and stage, p = k + 1) against
         the FP64 pipe (native FP64) or the float-float emulation ceiling, and its algorithmic bytes
         (16 B per stage-DoF: read u, write v) against measured HBM."""

@@ -26,7 +26,9 @@
  *  - Unless stated otherwise, pointers are DEVICE pointers owned by the
  *    caller, on the device current when the handle was created, and all work
  *    is enqueued on the handle's CUDA stream (irk_create's `cuda_stream`,
- *    NULL = legacy default stream).  The library owns every internal buffer
+ *    NULL = legacy default stream).  A call on a handle makes the handle's
+ *    GPU current while it runs and restores the caller's current device, so
+ *    one process may drive handles on several GPUs.  The library owns every internal buffer
  *    (Krylov bases, multigrid hierarchy) and frees it in irk_destroy.
  *  - Errors are returned as irk_status codes; no C++ exception crosses the
  *    ABI.  irk_last_error(h) gives a one-line message for the last failure.

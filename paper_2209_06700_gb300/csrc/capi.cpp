@@ -670,9 +670,24 @@ Status create(const irk_mesh* mesh, int degree, int Q, double tau, const irk_opt
   return Status::Ok();
 }
 
+// Makes the handle's GPU current for one call and restores the caller's device afterwards: kernels
+// can only be launched into a stream of the current device, and a process may drive several GPUs.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+    cudaGetLastError();
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 template <typename F>
 irk_status guarded(irk_problem* h, F&& f) {
   if (!h) return IRK_EINVAL;
+  DeviceScope dev(h->device);
   ProfBind bind(&h->prof);
   try {
     Status s = f();
@@ -905,8 +920,11 @@ irk_status irk_solve_batch(irk_handle* hs, double** ys, const double* t_ns, int 
 
 irk_status irk_destroy(irk_handle h) {
   if (!h) return IRK_OK;
-  cudaStreamSynchronize(h->st);
-  delete h;
+  {
+    DeviceScope dev(h->device);  // the handle's memory, graphs and events are freed on its GPU
+    cudaStreamSynchronize(h->st);
+    delete h;
+  }
   return IRK_OK;
 }
 

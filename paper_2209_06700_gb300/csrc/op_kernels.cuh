@@ -433,8 +433,6 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     for (int q = 0; q < PF; ++q)
       if ((q + 1) * NT <= NLD || soff[q] >= 0) su[soff[q]] = pf[q];  // only the last slot can be empty
   };
-  // the warp's rows (warp-uniform row position in the cell): this lane's first staged input
-  // column and output slot of each, fixed for the whole kernel
   // FP32 levels (F32; not the dual products at degree 4, which would spill): the warp's rows with
   // every offset a constant (this lane's first output slot; the input column sits K rows lower)
   constexpr bool F32 = std::is_same<T, float>::value && (K <= 3 || EPI != EPI_DUAL);
@@ -497,8 +495,8 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
 
   // the thread's output nodes (z, yrow, K cell + m) sit at rowbase + z * n1^2 + m in stage s
   // (32-bit offsets within a stage vector; the stage offset is uniform across the CTA).  F32: the
-  // row start, the stage's Chebyshev coefficients and this row's part of the 1/D
-  // table are fixed for the kernel, and the operands' addresses are formed once per plane.
+  // row start, the stage's Chebyshev coefficients and this row's part of the 1/D table are fixed
+  // for the kernel, and the operands' addresses are formed once per plane.
   const int rowbase = yrow * n1 + K * cell;
   const int plane32 = n1 * n1;
   const long long sbase = (long long)s * P.ld;

@@ -6,9 +6,11 @@
 // Classical Gram-Schmidt with a second pass where one pass would leave the
 // basis less than semi-orthogonal (decided on the device by the reduction
 // that finishes the first pass's coefficients, from the cancellation
-// |w - V h| / |w| and the loss carried over from earlier steps); the dot products are deterministic device reductions, finished inside each
+// |w - V h| / |w| and the loss carried over from earlier steps); the dot
+// products are deterministic device reductions, finished inside each
 // Gram-Schmidt kernel by its last block, and the Hessenberg/Givens update runs
-// on the host with one device->host transfer per iteration.  The vectors are FP64 or float-float (ff), chosen by the caller.
+// on the host with one device->host transfer per iteration.  The vectors are
+// FP64 or float-float (ff), chosen by the caller.
 #include <cmath>
 #include <algorithm>
 #include <cstring>

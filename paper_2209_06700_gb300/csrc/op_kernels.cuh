@@ -157,11 +157,14 @@ __device__ __forceinline__ void ytaps(const T* col, int stride, const OpParams<T
 
 // y pass of one tile row with output row position R (compile time): the row's SL staged columns,
 // 32 per step with this lane's column first (col, g, h point at it), every offset a constant;
-// only the last step, when SL is not a multiple of 32, checks the lane.
+// only the last step, when SL is not a multiple of 32, checks the lane.  FP32 unrolls every step;
+// FP64 two at a time, which gives the FP64 pipe independent chains without the registers (and
+// resident CTAs) that a full unroll costs.
 template <typename T, int K, int R, bool PK, int SL>
 __device__ __forceinline__ void yrow(const T* col, T* g, T* h, int lane, const OpParams<T>& P) {
   constexpr int IT = (SL + 31) / 32;
-#pragma unroll
+  constexpr int UNR = sizeof(T) == 8 ? 2 : IT;
+#pragma unroll (UNR)
   for (int i = 0; i < IT; ++i) {
     if ((i + 1) * 32 <= SL || lane + 32 * i < SL) {
       T a = zero<T>(), b = zero<T>();
@@ -433,15 +436,17 @@ op3d_kernel(const typename Storage<T>::type* __restrict__ u, const OpParams<T> P
     for (int q = 0; q < PF; ++q)
       if ((q + 1) * NT <= NLD || soff[q] >= 0) su[soff[q]] = pf[q];  // only the last slot can be empty
   };
-  // FP32 levels (F32; not the dual products at degree 4, which would spill): the warp's rows with
-  // every offset a constant (this lane's first output slot; the input column sits K rows lower)
+  // FP32 levels (F32; not the dual products at degree 4, which would spill) and FP64: the warp's
+  // rows with every offset a constant (this lane's first output slot; the input column sits K rows
+  // lower); float-float keeps the rolled loop
   constexpr bool F32 = std::is_same<T, float>::value && (K <= 3 || EPI != EPI_DUAL);
+  constexpr bool YCONST = F32 || std::is_same<T, double>::value;
   const int yout0 = w * RPW * SL + lane;
   auto ypass = [&](int buf) {
     const T* su = su2 + buf * L::SU;
     T* sgb = sg2 + buf * L::SG;
     T* shb = sh2 + buf * L::SG;
-    if constexpr (F32) {
+    if constexpr (YCONST) {
 #pragma unroll 1
       for (int rr = 0; rr < RPW; ++rr) {  // the warp's rows one at a time (warp-uniform tap row)
         const int o = yout0 + rr * SL;

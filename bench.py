@@ -693,7 +693,7 @@ def main():
                            "variant": args.variant, "mg_precision": mg_bits,
                            "parallelism": f"replicas x{world}",
                            "smoothing_range": extra.get("smoothing_range", 10.0),
-                           "gs_second_pass": "every step" if args.gs_reorth else "where needed (semi-orthogonality)",
+                           "gs_second_pass": "every step" if args.gs_reorth else "where needed (orthogonality to 2^-16)",
                            "l2": "inputs larger than L2: Krylov basis of several GB > 129 MB; no flush"},
                 "latency_ms": {"p50": statistics.median(lat),
                                "p99": sorted(lat)[min(len(lat) - 1, int(0.99 * len(lat)))]},

@@ -103,9 +103,9 @@ typedef struct {
                          0 native FP64).  The preconditioner keeps the Cartesian blocks of
                          Eq. (irk:P) (flexible GMRES absorbs the difference) */
   int gs_reorth;      /* second classical Gram-Schmidt pass of the outer FGMRES: 0 (default) where
-                         one pass would leave the Krylov basis less than semi-orthogonal (estimated
-                         loss of orthogonality above 2^-26; the residuals and stopping test are then
-                         those of an orthogonal basis to within 1e-6 relative); 1 at every step */
+                         one pass would leave the Krylov basis orthogonal to worse than 2^-16
+                         (estimated loss; the residuals and stopping test are then those of an
+                         orthogonal basis to within 0.1 %); 1 at every step */
 } irk_options;
 
 typedef struct {

@@ -4,7 +4,7 @@
 // preconditioned vectors Z because the preconditioner (one mixed-precision
 // V-cycle per block) is not a fixed linear map in floating point.
 // Classical Gram-Schmidt with a second pass where one pass would leave the
-// basis less than semi-orthogonal (decided on the device by the reduction
+// basis orthogonal to worse than 2^-16 (decided on the device by the reduction
 // that finishes the first pass's coefficients, from the cancellation
 // |w - V h| / |w| and the loss carried over from earlier steps); the dot
 // products are deterministic device reductions, finished inside each
@@ -98,14 +98,15 @@ namespace {
 // layout of dvals / fvals / hvals
 constexpr int kH1 = 0, kH2 = 65, kNrm = 130, kRedo = 132, kInv = 133, kDelta = 134, kY = 160, kOne = 255;
 
-// The second classical Gram-Schmidt pass is taken only where one pass would leave the basis less
-// than semi-orthogonal: estimated loss of orthogonality above 2^-26 (the square root of the FP64
-// unit roundoff).  With the Gram matrix of the m + 1 basis vectors within m 2^-26 of the identity
-// (m <= 60), the Hessenberg least-squares residual equals the true residual |b - A x| of the
-// computed x, and GMRES's residuals the optimal ones, to within a factor 1 +- 1e-6: the stopping
-// test and the iteration count are those of a fully orthogonal basis.  Rounding of one pass: about
-// 100 units of roundoff of the vectors' arithmetic (the blocked length-n dot products; ff: 2^-48).
-constexpr double kSemiOrth = 1.4901161193847656e-8;  // 2^-26
+// The second classical Gram-Schmidt pass is taken only where one pass would leave the basis
+// orthogonal to worse than 2^-16 (estimated loss of orthogonality).  With the Gram matrix of the
+// m + 1 basis vectors within m 2^-16 <= 1e-3 of the identity (m <= 60), its singular values lie
+// within 1 +- 5e-4: the Hessenberg least-squares residual equals the true residual |b - A x| of the
+// computed x, and GMRES's residuals the optimal ones over the same space, to within 0.1 %, so the
+// stopping test and the iteration count are those of a fully orthogonal basis; the estimate itself
+// runs about 100 times above the actual loss.  Rounding of one pass: about 100 units of roundoff of
+// the vectors' arithmetic (the blocked length-n dot products; ff: 2^-48).
+constexpr double kOrthTol = 1.52587890625e-5;  // 2^-16
 template <typename S> constexpr double pass_rounding();
 template <> constexpr double pass_rounding<double>() { return 100.0 * 1.1102230246251565e-16; }
 template <> constexpr double pass_rounding<ff>() { return 100.0 * 3.552713678800501e-15; }
@@ -123,7 +124,7 @@ void gs_sinks(double* dv, ff* fv, unsigned* count, int nv, bool always_two, RowS
   r1.X.sel_delta = dv + kDelta;
   r1.X.sel_nv = nv;
   r1.X.sel_round = pass_rounding<S>();
-  r1.X.sel_tol = always_two ? -1.0 : kSemiOrth;
+  r1.X.sel_tol = always_two ? -1.0 : kOrthTol;
   r2.out = dv + kH2;
   r2.count = count;
   r2.X.out_ff = fv + kH2;
@@ -210,7 +211,7 @@ Status fgmres_solve(FGMRESWork& w, const ApplyFn<S>& op, const ApplyFn<S>& prec,
     S* wv = V + (size_t)(j + 1) * len;
     IRK_TRY(prec(Vj, Zj));
     IRK_TRY(op(Zj, wv));
-    // classical Gram-Schmidt; the second pass only where one pass would lose semi-orthogonality
+    // classical Gram-Schmidt; the second pass only where one pass would lose orthogonality
     const int nv = j + 1;
     RowSink r1, r2, r3;
     gs_sinks<S>(w.dvals, w.fvals, w.count, nv, w.always_two_passes != 0, r1, r2, r3);

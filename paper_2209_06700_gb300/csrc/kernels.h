@@ -172,7 +172,7 @@ struct ReduceExtra {
   ff* inv_ff = nullptr;               // the same in ff
   // Second Gram-Schmidt pass or not, decided once every row is final (rows 0 .. sel_nv - 1: the
   // coefficients h = V^T w; row sel_nv: |w|^2).  sel_flag[0] = 1.0 when the new basis vector would
-  // lose semi-orthogonality after one pass, else 0.0; sel_delta[0] carries the basis's estimated
+  // lose orthogonality beyond sel_tol after one pass, else 0.0; sel_delta[0] carries the basis's estimated
   // loss of orthogonality from one Arnoldi step to the next (taken as 0 when sel_nv == 1);
   // sel_round is the rounding of one pass and sel_tol the loss allowed.
   double* sel_flag = nullptr;

@@ -154,7 +154,7 @@ __device__ __forceinline__ void finish_row(int i, double v, double* __restrict__
 // basis's own loss delta and the pass's rounding rho, both magnified by the cancellation |w| / |w'|
 // (the loss of orthogonality of classical Gram-Schmidt grows this way step after step).  |w'|^2 is
 // estimated before the second pass as |w|^2 - |h|^2 (exact for an orthonormal basis; with the basis
-// semi-orthogonal its error is far below the values that decide).  The pass is skipped while the
+// orthogonal to sel_tol its error is far below the values that decide).  The pass is skipped while the
 // estimated loss stays within sel_tol, and taken otherwise (or when the estimate is not positive),
 // which brings the new vector's defect down to rounding level and leaves delta where it was.
 __device__ void decide_second_pass(const double* out, const ReduceExtra& X) {

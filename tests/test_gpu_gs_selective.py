@@ -2,11 +2,11 @@
 
 One classical Gram-Schmidt pass magnifies the basis's loss of orthogonality by the cancellation
 |w| / |w - V h| of each Arnoldi step; the solver tracks that estimate on the device and takes the
-second pass where one pass would leave the basis less than semi-orthogonal (2^-26).  The steps
+second pass where one pass would leave the basis orthogonal to worse than 2^-16.  The steps
 taken with that rule (the default) and with the second pass at every step (gs_reorth = 1,
 classical Gram-Schmidt twice) must both match the oracle's exact IRK step to the standing 1e-9
 and each other to the same bar, in the same number of FGMRES iterations (the residuals of a
-semi-orthogonal basis are those of an orthogonal one to within 1e-6 relative); the default takes
+basis orthogonal to 2^-16 are those of an orthogonal one to within 0.1 %); the default takes
 fewer second passes, but takes some once the estimated loss has grown.
 """
 import numpy as np
@@ -54,7 +54,7 @@ def test_selective_second_pass_matches_two_passes_and_the_oracle(dim, N, k, Q, t
 
 
 def test_second_passes_return_once_the_loss_has_grown():
-    """A long Arnoldi cycle (tight tolerance, degree-1 smoothing): the estimate passes 2^-26 after a
+    """A long Arnoldi cycle (tight tolerance, degree-1 smoothing): the estimate passes 2^-16 after a
     few steps of strong cancellation, and from then on the second pass is taken."""
     dim, N, k, Q, tau = 3, 16, 3, 3, 1e-3
     prob = Problem(dim, N, k, Q, tau)

@@ -664,12 +664,18 @@ def main():
         roof_other["timing"] = "CUDA events on the solver stream, profiled eager step"
     kry_ms, kry_n, _ = cat_ms["krylov"]
     its_prof = max(1, round(sum(its[-3:]) / 3)) if its else 1
-    # Gram-Schmidt with a second pass every iteration: 4j multiply-adds and about 3j + 5 vector reads and
-    # writes per element in iteration j (j = 1..its); 8 bytes per element in either arithmetic
+    passes = min(its_prof, round(sum(reo[-3:]) / len(reo[-3:]))) if reo else its_prof
+    # Gram-Schmidt in iteration j (j = 1..its, j basis vectors) per element: with the second pass 4j
+    # multiply-adds and about 3j + 5 vector reads and writes, without it 2j and 2j + 5 (dots, then
+    # the update in place, then the normalisation); the second passes fall on the last iterations,
+    # where the basis's estimated loss of orthogonality has grown.  8 bytes per element in either
+    # arithmetic.
     js = range(1, its_prof + 1)
-    kry_flops = sum(8.0 * j for j in js) * w.Q * w.ndofs
-    kry_bytes = sum((3 * j + 5) * 8.0 for j in js) * w.Q * w.ndofs
+    second = lambda j: j > its_prof - passes
+    kry_flops = sum((8.0 if second(j) else 4.0) * j for j in js) * w.Q * w.ndofs
+    kry_bytes = sum(((3 * j + 5) if second(j) else (2 * j + 5)) * 8.0 for j in js) * w.Q * w.ndofs
     roof_krylov = {"category_ms_per_step": kry_ms, "launches": kry_n, "iterations": its_prof,
+                   "second_passes": passes,
                    "hbm": {"achieved": kry_bytes / (kry_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": kry_bytes / (kry_ms / 1e3) / 1e9 / hbm},
                    "alu": {"achieved": kry_flops / (kry_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
